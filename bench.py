@@ -1,0 +1,308 @@
+#!/usr/bin/env python
+"""Benchmark: Smolyak H|psi> applications/s on the D=12 L=10 workload.
+
+Workload: chained Henon-Heiles, D=12, L=10, nb(l)=l+1, nq(l)=l+2, omega_i ~
+U[0.8,1.2] (seeded), lambda = 0.111803; N_cs = 646,646 compact functions,
+646,646 Smolyak terms.  One step = one sg_apply_H on a block of `nvec` real
+vectors (the block of the block-Davidson solver); one application = one real
+vector.  Mixed precision (FP32 contractions, FP64 accumulation) is the headline;
+FP64 mode is measured beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun): every rank runs an independent replica (independent
+problems, no collective on the data path); value = all ranks' applications /
+the slowest rank's time ("scaling": "weak").
+--impl reference: the CPU oracle (the literal Alg. 1 in C) timed as it stands
+on the host cores, each step a random sample of the workload's terms.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Smolyak H|psi> applications/s and % roofline at D=12 L=10; mixed vs FP64; p50/p99"
+UNIT = "applications/s"
+WORKLOAD = "chained Henon-Heiles D=12 L=10 nb=l+1 nq=l+2 (N_cs=646646, 646646 terms)"
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.070 GHz (max SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# FP64: the nominal GB300 rate (1.25 TFLOP/s); the FMA microbenchmark is reported beside it
+FP64_PEAK_TFLOPS = 1.25
+
+
+def algorithmic_flops_per_vector(levels: np.ndarray, nbA=1, nbB=1, nqA=2, nqB=1) -> int:
+    """FLOPs of one real-vector apply by the route the kernel takes: per term,
+    forward and backward one-mode contractions over the modes with nb > 1
+    (2 flops per multiply-add), the kinetic matrices in the basis, one multiply
+    per grid point for the potential, and the weighted compress-add."""
+    l = levels.astype(np.int64)
+    nb = nbA + nbB * l
+    nq = nqA + nqB * l
+    act = nb > 1
+    a = np.where(act, nb, 1)
+    g = np.where(act, nq, 1)
+    # prefix product of g over j < i, suffix product of a over j > i
+    pre = np.cumprod(np.concatenate([np.ones((l.shape[0], 1), np.int64), g[:, :-1]], axis=1), axis=1)
+    suf = np.ones_like(a)
+    for i in range(l.shape[1] - 2, -1, -1):
+        suf[:, i] = suf[:, i + 1] * a[:, i + 1]
+    fwd = (np.where(act, a * g, 0) * pre * suf).sum(axis=1)
+    NB = a.prod(axis=1)
+    NG = g.prod(axis=1)
+    kin = NB * np.where(act, a, 0).sum(axis=1)
+    return int((2 * (2 * fwd + kin) + NG + 2 * NB).sum())
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0])); mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample_rate(problem, n_terms: int, seconds: float, seed: int, threads: int = 0):
+    """Time the literal oracle on a random sample of terms sized to ~`seconds`;
+    returns (applications/s estimate, sample description, threads used)."""
+    from oracle import oracle as orc
+    rng = np.random.default_rng(seed)
+    x = np.random.default_rng(seed).standard_normal((1, orc.n_compact(problem)))
+    pilot = rng.choice(n_terms, 64, replace=False)
+    t0 = time.perf_counter()
+    orc.apply_H(problem, x, pilot, threads)
+    tp = max(time.perf_counter() - t0, 1e-3)
+    n = int(min(n_terms, max(64, 64 * seconds / tp)))
+    sub = rng.choice(n_terms, n, replace=False)
+    t0 = time.perf_counter()
+    orc.apply_H(problem, x, sub, threads)
+    dt = time.perf_counter() - t0
+    est_apply_s = dt * n_terms / n
+    used = threads if threads > 0 else orc.max_threads()
+    return 1.0 / est_apply_s, f"{n} of {n_terms} terms drawn uniformly (1 vector), {dt:.1f} s; " \
+        f"full apply estimated as sample time x {n_terms}/{n}", used
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2111_13655_gb300 import synth
+    from oracle import oracle as orc
+    orc.build()
+    p = synth.workload_C3()
+    n_terms = orc.counts(12, 10)[0]
+    rates = []
+    desc = ""
+    cores = 0
+    for i in range(args.warmup + args.steps):
+        r, desc, cores = oracle_sample_rate(p, n_terms, args.ref_seconds, 1000 + i)
+        if i >= args.warmup:
+            rates.append(r)
+    value = statistics.mean(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "each step: " + desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_device(ctx, xd, yd, nvec, steps, warmup, flush, torch, sg):
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        sg.sg_apply_H(ctx, xd, yd, nvec, stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()                       # L2 flush, outside the timed interval
+        ev[i][0].record(stream)
+        sg.sg_apply_H(ctx, xd, yd, nvec, stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nvec", type=int, default=8)
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=5.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2111_13655_gb300 as sg
+    from paper_2111_13655_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # CPU baseline before any GPU work on rank 0 (the oracle's OpenMP pool
+    # starts in this process; no fork happens after CUDA initialisation).
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as orc
+        orc.build()
+        r, desc, cores = oracle_sample_rate(synth.workload_C3(), 646646, args.cpu_seconds, 7)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    p = synth.workload_C3()
+    nvec = args.nvec
+    results = {}
+    for prec in ("mixed", "fp64"):
+        ctx = sg.sg_create(p, prec)
+        n = ctx.n_cs
+        x = synth.random_vectors(n, nvec, 11 + rank)
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.empty_like(xd)
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+        steps = args.steps if prec == "mixed" else args.fp64_steps
+        warm = max(3, args.warmup if prec == "mixed" else 3)
+        barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            times = time_device(ctx, xd, yd, nvec, steps, warm, flush, torch, sg)
+        barrier()
+        torch.cuda.synchronize()
+        total_ms = sum(times)
+        if dist is not None:
+            t = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        assert sg.sg_device_error(ctx) == 0
+        lv, _ = sg.sg_term_levels(ctx)
+        f_alg = algorithmic_flops_per_vector(lv) * nvec
+        ms = total_ms / steps
+        peak = FP32_PEAK_TFLOPS if prec == "mixed" else FP64_PEAK_TFLOPS
+        achieved = f_alg / (statistics.mean(times) * 1e-3) / 1e12
+        results[prec] = {
+            "value": world * nvec * steps / (total_ms * 1e-3), "ms_per_step": ms, "steps": steps,
+            "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "flops_per_launch": f_alg,
+                         "peak_note": ("FP32 CUDA cores, derived: 152 SM x 128 lanes x 2 x 2.07 GHz"
+                                       if prec == "mixed" else "FP64, nominal GB300 rate")},
+            "clocks": clk.summary(),
+        }
+        if prec == "mixed":
+            # end to end through the host-buffer entry point: H2D + apply + D2H per step
+            xh = torch.from_numpy(x).pin_memory()
+            yh = torch.empty_like(xh).pin_memory()
+            for _ in range(2):
+                sg.sg_apply_H_host(ctx, xh, yh, nvec)
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                sg.sg_apply_H_host(ctx, xh, yh, nvec)
+            e2e_s = time.perf_counter() - t0
+            if dist is not None:
+                t = torch.tensor([e2e_s], device="cuda")
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                e2e_s = float(t.item())
+            results[prec]["e2e"] = {"value": world * nvec * args.steps / e2e_s, "unit": UNIT,
+                                    "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(x.nbytes)}
+        sg.sg_destroy(ctx)
+        del xd, yd, flush
+        torch.cuda.empty_cache()
+
+    if rank == 0:
+        m = results["mixed"]
+        f = results["fp64"]
+        line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": m["steps"],
+                "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "precision": "mixed (FP32 contractions, FP64 accumulation)",
+                           "vectors_per_step": nvec, "parallelism": f"replicas x{world}",
+                           "l2": "flushed between timed steps (256 MB write)"},
+                "latency_ms": m["latency_ms"], "roofline": m["roofline"], "clocks": m["clocks"],
+                "e2e": m["e2e"], "gpu_launches": m["steps"],
+                "fp64": {"value": f["value"], "unit": UNIT, "ms_per_step": f["ms_per_step"], "steps": f["steps"],
+                         "latency_ms": f["latency_ms"], "roofline": f["roofline"], "clocks": f["clocks"]},
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

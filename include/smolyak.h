@@ -1,0 +1,200 @@
+/*
+ * smolyak.h -- C ABI of the GB300 Smolyak operator-action library (libsmolyak.so).
+ *
+ * The library applies the Smolyak-represented Hamiltonian of arXiv 2111.13655
+ * to wavefunctions held in the compact Smolyak basis:
+ *
+ *     y = H_S x,   H_S = sum_{l in R(l)} D_l  P_l^T  A_l  P_l          (Sec. 2, Eq. (16))
+ *
+ * with R(l): L-n+1 <= |l| <= L and D_l = (-1)^{L-|l|} C(n-1, L-|l|) (Eq. (8)),
+ * P_l the restriction of the compact basis to term l (the mapping table M^B of
+ * Sec. 3, Table 2), and A_l the term action of Alg. 1: basis->grid (Eq. (15)),
+ * the operator on the term's direct-product grid, grid->basis (Eq. (14)).
+ *
+ * Conventions shared by every call
+ *   - Indices are 0-based.  Modes are numbered 0..D-1.
+ *   - Compact vectors have N_cs entries in lexicographic order of the
+ *     multi-index k = (k_0..k_{D-1}) with k_0 slowest and k_{D-1} fastest
+ *     (the compact ordering of Table 2).  A block of nvec vectors is stored
+ *     column after column: x[v*N_cs + i].
+ *   - Terms are numbered in the order of Table 2: l_0 varies fastest.
+ *   - Basis of every mode: orthonormal Hermite functions
+ *       b_k(Q) = sqrt(s) h_k(s (Q - q0))   (the "Hm" basis of Sec. 4),
+ *     grid: Gauss-Hermite nodes Q_u = q0 + x_u / s with weights chosen so that
+ *     sum_u w_u b_k(Q_u) b_k'(Q_u) = delta_kk' whenever nq >= nb.
+ *   - Hamiltonian: H = sum_i omega_i/2 (-d^2/dQ_i^2) + V(Q), V a sparse
+ *     polynomial (the Henon-Heiles form of Eq. (18) is one instance).
+ *   - Every call that takes a `stream` is enqueued on that CUDA stream
+ *     (cudaStream_t passed as void*, NULL = legacy default stream) and
+ *     returns before the GPU work ends, unless stated otherwise.
+ *   - Errors are returned as sg_status; nothing is thrown across the ABI, the
+ *     process is never terminated and no device trap is raised.  The text of
+ *     the last error of a context is available from sg_last_error(ctx); errors
+ *     of sg_create are reported by sg_last_error(NULL) (per calling thread).
+ *   - A context may be used by one host thread at a time.
+ */
+#ifndef SMOLYAK_GB300_H
+#define SMOLYAK_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sg_ctx sg_ctx;
+
+typedef enum {
+    SG_OK = 0,
+    SG_EINVAL = 1,       /* invalid argument (sizes, rules, pointers, precision)      */
+    SG_ENOMEM = 2,       /* host or device allocation failed                         */
+    SG_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed               */
+    SG_ENOCONV = 4,      /* an iterative solver did not converge in max_it            */
+    SG_ETIMEOUT = 5,     /* a bounded device wait ran out                             */
+    SG_EBUDGET = 6,      /* request exceeds the device-memory budget                  */
+    SG_EUNSUPPORTED = 7  /* valid request outside this build's limits (see below)     */
+} sg_status;
+
+typedef enum { SG_FP64 = 0, SG_MIXED = 1 } sg_precision;
+
+/* Primitive basis of one mode: nb(l) = nb_A + nb_B * l functions at level l
+ * (the level->size rule N_l = A + B l of Sec. 2), Hermite functions centred at
+ * q0 with scale factor `scale` (> 0).  Requires nb_A >= 1, nb_B >= 0. */
+typedef struct { int nb_A, nb_B; double q0, scale; } sg_basis;
+
+/* Grid of one mode: nq(l) = nq_A + nq_B * l Gauss-Hermite points at level l.
+ * Requires nq(l) >= nb(l) for every level (nq_A >= nb_A, nq_B >= nb_B). */
+typedef struct { int nq_A, nq_B; } sg_grid;
+
+/* Sparse polynomial potential.  Monomial m contributes
+ *     coef[m] * prod_{f = off_m}^{off_m + nfac[m] - 1} Q_{mode[f]}^{power[f]},
+ * off_m = nfac[0] + ... + nfac[m-1]: the factors of all monomials are stored
+ * back to back in mode/power.  nfac[m] = 0 is a constant.  power >= 1. */
+typedef struct {
+    int nterms;
+    const double *coef;
+    const int *nfac;
+    const int *mode;
+    const int *power;
+} sg_poly;
+
+/* H = sum_i omega[i]/2 (-d^2/dQ_i^2) + V(Q).  omega: D host doubles. */
+typedef struct {
+    const double *omega;
+    sg_poly V;
+} sg_hamiltonian;
+
+/*
+ * sg_create -- build a context for one Smolyak problem (Sec. 3: the three
+ * objects -- terms, compact basis, grid -- and the mapping table M^B).
+ *   D      number of modes, 1 <= D <= 32.
+ *   L      Smolyak level (L^B = L^G = L, Sec. 2), 0 <= L.
+ *   basis  D host structs; grids: D host structs.
+ *   H      Hamiltonian; all arrays are host memory, copied (caller keeps ownership).
+ *   prec   SG_FP64: every step in FP64.  SG_MIXED: per-term contractions and
+ *          the grid multiply in FP32, accumulation of the compact result in FP64.
+ *   out    receives the context (owned by the caller, release with sg_destroy).
+ * Setup runs on the host plus synchronous uploads on the current device.
+ * Limits of this build (SG_EUNSUPPORTED): nb(L), nq(L) <= 32, N_cs < 2^31,
+ * at most 256 monomials with at most 8 factors each, powers <= 16.
+ */
+sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
+                    const sg_hamiltonian *H, sg_precision prec, sg_ctx **out);
+
+/*
+ * sg_plan -- the host half of sg_create: validates the problem and builds the
+ * terms, the compact ranking and the 1D tables (Sec. 3's three objects) without
+ * touching any GPU.  The context answers sg_size, sg_term_levels,
+ * sg_compact_rank and sg_mode_tables (e.g. to size a problem before admitting
+ * it); calls that need device state return SG_EINVAL.  Release with sg_destroy.
+ */
+sg_status sg_plan(int D, int L, const sg_basis *basis, const sg_grid *grids,
+                  const sg_hamiltonian *H, sg_precision prec, sg_ctx **out);
+
+/* Sizes: n_cs = N_cs (compact basis), n_terms = N_st, n_s = N_s (sum of term
+ * basis sizes, Sec. 2, Eq. (11)), n_grid = sum of term grid sizes, bytes_device =
+ * device memory held by the context.  Any pointer may be NULL. */
+sg_status sg_size(const sg_ctx *ctx, int64_t *n_cs, int64_t *n_terms, int64_t *n_s,
+                  int64_t *n_grid, int64_t *bytes_device);
+
+/*
+ * sg_apply_H -- y = H_S x for nvec real vectors (Eq. (16), every term by Alg. 1).
+ *   x, y   DEVICE pointers, N_cs * nvec doubles each, column after column.
+ *          y is overwritten; x and y must not overlap.
+ *   nvec   >= 1.  A complex vector is passed as two real vectors.
+ * Enqueued on `stream`; the result is ready when the stream reaches it.
+ */
+sg_status sg_apply_H(sg_ctx *ctx, const double *x, double *y, int nvec, void *stream);
+
+/*
+ * sg_apply_H_host -- the same operation on HOST buffers: copies x to the
+ * device, applies H_S, copies y back, and returns when y is written.
+ *   x_host, y_host: N_cs * nvec doubles each (pinned memory gives the fastest copies).
+ * Device staging buffers are owned by the context and reused across calls.
+ */
+sg_status sg_apply_H_host(sg_ctx *ctx, const double *x_host, double *y_host, int nvec,
+                          void *stream);
+
+/*
+ * sg_term_levels -- levels l of terms [t0, t0+nt) in Table-2 order, D ints per
+ * term, into levels_host (nt*D ints), and their combination coefficients D_l
+ * (Eq. (8)) into coef_host (nt ints, may be NULL).
+ */
+sg_status sg_term_levels(const sg_ctx *ctx, int64_t t0, int64_t nt, int *levels_host,
+                         int *coef_host);
+
+/*
+ * sg_index_map -- the mapping table M^B (Sec. 3, Table 2) for terms
+ * [t0, t0+nt) in Table-2 order, computed on the device by the same index
+ * arithmetic the operator action uses.
+ *   offsets_host  nt+1 int64 (host, out): start of each term's list, relative
+ *                 to the first listed term (offsets_host[0] = 0).
+ *   cs_index_dev  DEVICE int64 array of offsets_host[nt] entries (out): compact
+ *                 index of each basis function of the term, k_0 fastest inside
+ *                 the term (Table 2's i^s order).  Call once with
+ *                 cs_index_dev = NULL to obtain the offsets (and the size).
+ * Synchronises `stream` before returning.
+ */
+sg_status sg_index_map(sg_ctx *ctx, int64_t t0, int64_t nt, int64_t *offsets_host,
+                       int64_t *cs_index_dev, void *stream);
+
+/*
+ * sg_compact_rank -- position of multi-indices in the compact basis (Table 2's
+ * compact ordering), computed on the host with the same partial-rank tables the
+ * GPU uses.  k: n*D host ints; rank: n host int64 (out), -1 for a k outside the
+ * compact basis.
+ */
+sg_status sg_compact_rank(const sg_ctx *ctx, const int *k, int64_t n, int64_t *rank);
+
+/*
+ * sg_mode_tables -- host copies of the 1D tables of one mode at one level:
+ *   B[u*nb+k]  = b_k(Q_u)                 (basis -> grid, Eq. (15))
+ *   BW[k*nq+u] = w_u b_k(Q_u)             (grid -> basis, Eq. (14))
+ *   K[k*nb+k'] = -omega/2 sum_u w_u b_k(Q_u) b_k''(Q_u)   (kinetic in the basis)
+ *   Q[u]       = Q_u                      (grid coordinates)
+ * nb, nq receive the sizes; any output pointer may be NULL.
+ */
+sg_status sg_mode_tables(const sg_ctx *ctx, int mode, int level, int *nb, int *nq,
+                         double *B, double *BW, double *K, double *Q);
+
+/*
+ * sg_device_error -- read and clear the context's device error word (0 when
+ * every kernel found its term within the capacities fixed at sg_create; a
+ * non-zero code names the capacity a kernel refused to exceed -- the kernel
+ * then skipped that term instead of touching memory out of bounds).
+ * Synchronous: waits for all work on the current device.
+ */
+sg_status sg_device_error(sg_ctx *ctx, int *code);
+
+/* Text of the last error of ctx (or of the calling thread's last sg_create
+ * when ctx is NULL).  Never NULL; valid until the next call on ctx. */
+const char *sg_last_error(const sg_ctx *ctx);
+
+/* Release the context and every device buffer it owns.  NULL is a no-op.
+ * The caller must ensure no work using ctx is still running on the GPU. */
+void sg_destroy(sg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMOLYAK_GB300_H */

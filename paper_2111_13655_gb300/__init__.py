@@ -1,0 +1,273 @@
+"""GB300 Smolyak operator action (arXiv 2111.13655) -- Python binding.
+
+A thin ctypes layer over libsmolyak.so (include/smolyak.h): every function has
+the C name and only marshals arguments; all arithmetic of the operator action
+runs in the library's CUDA kernels.  Device buffers are torch CUDA tensors
+(float64, contiguous); streams are torch.cuda.Stream objects or None (the
+current torch stream).
+
+If the library has not been built, every call raises: there is no CPU path.
+Build it with `python -m paper_2111_13655_gb300.build`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsmolyak.so")
+
+SG_OK, SG_EINVAL, SG_ENOMEM, SG_ECUDA, SG_ENOCONV, SG_ETIMEOUT, SG_EBUDGET, SG_EUNSUPPORTED = range(8)
+SG_FP64, SG_MIXED = 0, 1
+_STATUS = {0: "SG_OK", 1: "SG_EINVAL", 2: "SG_ENOMEM", 3: "SG_ECUDA", 4: "SG_ENOCONV",
+           5: "SG_ETIMEOUT", 6: "SG_EBUDGET", 7: "SG_EUNSUPPORTED"}
+
+
+class SgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Basis(ctypes.Structure):
+    _fields_ = [("nb_A", ctypes.c_int), ("nb_B", ctypes.c_int),
+                ("q0", ctypes.c_double), ("scale", ctypes.c_double)]
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nq_A", ctypes.c_int), ("nq_B", ctypes.c_int)]
+
+
+class _Poly(ctypes.Structure):
+    _fields_ = [("nterms", ctypes.c_int), ("coef", ctypes.c_void_p), ("nfac", ctypes.c_void_p),
+                ("mode", ctypes.c_void_p), ("power", ctypes.c_void_p)]
+
+
+class _Ham(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_void_p), ("V", _Poly)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp, _i64, _i32, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+_P64 = ctypes.POINTER(ctypes.c_int64)
+
+# name -> (restype, argtypes): every entry point declared in include/smolyak.h
+SIGNATURES = {
+    "sg_create": (_i32, [_i32, _i32, _vp, _vp, _vp, _i32, ctypes.POINTER(_vp)]),
+    "sg_plan": (_i32, [_i32, _i32, _vp, _vp, _vp, _i32, ctypes.POINTER(_vp)]),
+    "sg_size": (_i32, [_vp, _P64, _P64, _P64, _P64, _P64]),
+    "sg_apply_H": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "sg_apply_H_host": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "sg_term_levels": (_i32, [_vp, _i64, _i64, _vp, _vp]),
+    "sg_index_map": (_i32, [_vp, _i64, _i64, _vp, _vp, _vp]),
+    "sg_compact_rank": (_i32, [_vp, _vp, _i64, _vp]),
+    "sg_mode_tables": (_i32, [_vp, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                              _vp, _vp, _vp, _vp]),
+    "sg_device_error": (_i32, [_vp, ctypes.POINTER(_i32)]),
+    "sg_last_error": (ctypes.c_char_p, [_vp]),
+    "sg_destroy": (None, [_vp]),
+}
+
+
+def lib():
+    """Load libsmolyak.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -m paper_2111_13655_gb300.build` (there is no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib
+
+
+def _check(st: int, ctx=None):
+    if st != SG_OK:
+        msg = lib().sg_last_error(ctx.ptr if ctx is not None else None)
+        raise SgError(st, (msg or b"").decode(errors="replace"))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Ctx:
+    """Owner of one sg_ctx* (release with sg_destroy or a `with` block)."""
+
+    def __init__(self, ptr: int, problem, precision: int, device: bool):
+        self.ptr = ptr
+        self.problem = problem
+        self.precision = precision
+        self.device = device
+        n = sg_size(self)
+        self.n_cs, self.n_terms, self.n_s, self.n_grid = n["n_cs"], n["n_terms"], n["n_s"], n["n_grid"]
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        sg_destroy(self)
+
+    def __del__(self):
+        try:
+            sg_destroy(self)
+        except Exception:
+            pass
+
+
+def _marshal(p):
+    D = p.D
+    basis = (_Basis * D)(*[_Basis(int(p.nb_A[i]), int(p.nb_B[i]), float(p.q0[i]), float(p.scale[i]))
+                           for i in range(D)])
+    grids = (_Grid * D)(*[_Grid(int(p.nq_A[i]), int(p.nq_B[i])) for i in range(D)])
+    keep = [np.ascontiguousarray(p.omega, np.float64), np.ascontiguousarray(p.coef, np.float64),
+            np.ascontiguousarray(p.nfac, np.int32), np.ascontiguousarray(p.fmode, np.int32),
+            np.ascontiguousarray(p.fpow, np.int32)]
+    poly = _Poly(int(p.nmono), keep[1].ctypes.data, keep[2].ctypes.data,
+                 keep[3].ctypes.data if keep[3].size else None,
+                 keep[4].ctypes.data if keep[4].size else None)
+    ham = _Ham(keep[0].ctypes.data, poly)
+    return basis, grids, ham, keep
+
+
+def _precision(precision) -> int:
+    if precision in (SG_FP64, "fp64", "FP64"):
+        return SG_FP64
+    if precision in (SG_MIXED, "mixed", "MIXED", "fp32"):
+        return SG_MIXED
+    raise ValueError(f"unknown precision {precision!r}")
+
+
+def sg_create(problem, precision="fp64") -> Ctx:
+    """Context on the current CUDA device for a synth.Problem."""
+    prec = _precision(precision)
+    basis, grids, ham, keep = _marshal(problem)
+    out = _vp()
+    _check(lib().sg_create(problem.D, problem.L, ctypes.addressof(basis), ctypes.addressof(grids),
+                           ctypes.addressof(ham), prec, ctypes.byref(out)))
+    return Ctx(out.value, problem, prec, True)
+
+
+def sg_plan(problem, precision="fp64") -> Ctx:
+    """Host-only context (no GPU needed): sizes, terms, ranking, 1D tables."""
+    prec = _precision(precision)
+    basis, grids, ham, keep = _marshal(problem)
+    out = _vp()
+    _check(lib().sg_plan(problem.D, problem.L, ctypes.addressof(basis), ctypes.addressof(grids),
+                         ctypes.addressof(ham), prec, ctypes.byref(out)))
+    return Ctx(out.value, problem, prec, False)
+
+
+def sg_size(ctx: Ctx) -> dict:
+    v = [ctypes.c_int64() for _ in range(5)]
+    _check(lib().sg_size(ctx.ptr, *[ctypes.byref(a) for a in v]), ctx)
+    return dict(zip(["n_cs", "n_terms", "n_s", "n_grid", "bytes_device"], [a.value for a in v]))
+
+
+def _dev_ptr(t, n_expected: int, name: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if t.numel() != n_expected:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {n_expected}")
+    return t.data_ptr()
+
+
+def sg_apply_H(ctx: Ctx, x, y, nvec: int = None, stream=None) -> None:
+    """y = H_S x on the device (x, y: float64 CUDA tensors with nvec*N_cs elements)."""
+    if nvec is None:
+        nvec = x.numel() // ctx.n_cs
+    xp = _dev_ptr(x, nvec * ctx.n_cs, "x")
+    yp = _dev_ptr(y, nvec * ctx.n_cs, "y")
+    _check(lib().sg_apply_H(ctx.ptr, xp, yp, int(nvec), _stream_ptr(stream)), ctx)
+
+
+def sg_apply_H_host(ctx: Ctx, x_host, y_host, nvec: int = None, stream=None) -> None:
+    """Host-buffer form: copies in, applies, copies out; returns when y_host is written.
+    x_host, y_host: contiguous float64 numpy arrays or pinned CPU torch tensors."""
+    def ptr(a):
+        if isinstance(a, np.ndarray):
+            if a.dtype != np.float64 or not a.flags.c_contiguous:
+                raise TypeError("host buffers must be contiguous float64")
+            return a.ctypes.data, a.size
+        if a.dtype.is_floating_point and a.dtype.itemsize == 8 and not a.is_cuda and a.is_contiguous():
+            return a.data_ptr(), a.numel()
+        raise TypeError("host buffers must be contiguous float64")
+    xp, nx = ptr(x_host)
+    yp, ny = ptr(y_host)
+    if nvec is None:
+        nvec = nx // ctx.n_cs
+    if nx != nvec * ctx.n_cs or ny != nx:
+        raise ValueError("host buffer sizes do not match nvec * N_cs")
+    _check(lib().sg_apply_H_host(ctx.ptr, xp, yp, int(nvec), _stream_ptr(stream)), ctx)
+
+
+def sg_term_levels(ctx: Ctx, t0: int = 0, nt: int = None):
+    """(levels[nt, D] int32, coef[nt] int32) of terms [t0, t0+nt) in Table-2 order."""
+    if nt is None:
+        nt = ctx.n_terms - t0
+    lv = np.zeros((nt, ctx.problem.D), np.int32)
+    c = np.zeros(nt, np.int32)
+    _check(lib().sg_term_levels(ctx.ptr, t0, nt, lv.ctypes.data, c.ctypes.data), ctx)
+    return lv, c
+
+
+def sg_index_map(ctx: Ctx, t0: int = 0, nt: int = None, stream=None):
+    """(offsets[nt+1] int64 numpy, cs_index int64 CUDA tensor): M^B of Table 2."""
+    import torch
+    if nt is None:
+        nt = ctx.n_terms - t0
+    off = np.zeros(nt + 1, np.int64)
+    _check(lib().sg_index_map(ctx.ptr, t0, nt, off.ctypes.data, None, None), ctx)
+    out = torch.empty(int(off[-1]), dtype=torch.int64, device="cuda")
+    _check(lib().sg_index_map(ctx.ptr, t0, nt, off.ctypes.data,
+                              out.data_ptr() if out.numel() else None, _stream_ptr(stream)), ctx)
+    return off, out
+
+
+def sg_compact_rank(ctx: Ctx, k) -> np.ndarray:
+    k = np.ascontiguousarray(np.asarray(k, np.int32).reshape(-1, ctx.problem.D))
+    r = np.zeros(k.shape[0], np.int64)
+    _check(lib().sg_compact_rank(ctx.ptr, k.ctypes.data, k.shape[0], r.ctypes.data), ctx)
+    return r
+
+
+def sg_mode_tables(ctx: Ctx, mode: int, level: int) -> dict:
+    nb, nq = ctypes.c_int(), ctypes.c_int()
+    _check(lib().sg_mode_tables(ctx.ptr, mode, level, ctypes.byref(nb), ctypes.byref(nq),
+                                None, None, None, None), ctx)
+    nb, nq = nb.value, nq.value
+    B = np.zeros((nq, nb)); BW = np.zeros((nb, nq)); K = np.zeros((nb, nb)); Q = np.zeros(nq)
+    _check(lib().sg_mode_tables(ctx.ptr, mode, level, None, None, B.ctypes.data, BW.ctypes.data,
+                                K.ctypes.data, Q.ctypes.data), ctx)
+    return {"nb": nb, "nq": nq, "B": B, "BW": BW, "K": K, "Q": Q}
+
+
+def sg_device_error(ctx: Ctx) -> int:
+    c = ctypes.c_int()
+    _check(lib().sg_device_error(ctx.ptr, ctypes.byref(c)), ctx)
+    return c.value
+
+
+def sg_last_error(ctx: Ctx = None) -> str:
+    return (lib().sg_last_error(ctx.ptr if ctx is not None else None) or b"").decode(errors="replace")
+
+
+def sg_destroy(ctx: Ctx) -> None:
+    if ctx is not None and getattr(ctx, "ptr", None):
+        lib().sg_destroy(ctx.ptr)
+        ctx.ptr = None

@@ -1,0 +1,347 @@
+// C ABI of libsmolyak (declared in include/smolyak.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "sg_internal.h"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+sg_status fail(sg_ctx *ctx, sg_status st, const std::string &msg)
+{
+    if (ctx) ctx->last_error = msg; else g_create_error = msg;
+    return st;
+}
+
+sg_status cuda_fail(sg_ctx *ctx, cudaError_t e, const char *where)
+{
+    return fail(ctx, SG_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+sg_status upload(sg_ctx *ctx, const std::vector<T> &v, const T **dst)
+{
+    void *p = nullptr;
+    size_t bytes = std::max<size_t>(1, v.size()) * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return fail(ctx, SG_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    ctx->allocations.push_back(p);
+    ctx->bytes_device += (int64_t)bytes;
+    if (!v.empty()) {
+        e = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy");
+    }
+    *dst = static_cast<const T *>(p);
+    return SG_OK;
+}
+
+void free_all(sg_ctx *ctx)
+{
+    for (void *p : ctx->allocations) cudaFree(p);
+    ctx->allocations.clear();
+    if (ctx->stage_x) cudaFree(ctx->stage_x);
+    if (ctx->stage_y) cudaFree(ctx->stage_y);
+    ctx->stage_x = ctx->stage_y = nullptr;
+}
+
+// Device shared-memory opt-in limit of sm_100-class GPUs, used to size plans
+// made without a device (sg_plan).
+constexpr int kPlanSmemOptin = 232448;
+
+sg_status plan(int D, int L, const sg_basis *basis, const sg_grid *grids,
+                     const sg_hamiltonian *H, sg_precision prec, int smem_optin, sg_ctx **out)
+{
+    using namespace sg;
+    if (!out) return fail(nullptr, SG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (D < 1) return fail(nullptr, SG_EINVAL, "D must be >= 1");
+    if (D > kMaxD) return fail(nullptr, SG_EUNSUPPORTED, "D > 32");
+    if (L < 0) return fail(nullptr, SG_EINVAL, "L must be >= 0");
+    if (!basis || !grids || !H || !H->omega) return fail(nullptr, SG_EINVAL, "NULL basis/grids/H/omega");
+    if (prec != SG_FP64 && prec != SG_MIXED) return fail(nullptr, SG_EINVAL, "unknown precision");
+    for (int i = 0; i < D; i++) {
+        const sg_basis &b = basis[i];
+        const sg_grid &g = grids[i];
+        if (b.nb_A < 1 || b.nb_B < 0 || g.nq_A < b.nb_A || g.nq_B < b.nb_B)
+            return fail(nullptr, SG_EINVAL, "mode rules need nb_A>=1, nb_B>=0, nq_A>=nb_A, nq_B>=nb_B");
+        if (!(b.scale > 0) || !std::isfinite(b.scale) || !std::isfinite(b.q0))
+            return fail(nullptr, SG_EINVAL, "scale must be finite and > 0, q0 finite");
+        if ((int64_t)g.nq_A + (int64_t)g.nq_B * L > kMaxLevelSize)
+            return fail(nullptr, SG_EUNSUPPORTED, "nq(L) > 32");
+        if (!std::isfinite(H->omega[i])) return fail(nullptr, SG_EINVAL, "omega not finite");
+    }
+    const sg_poly &V = H->V;
+    if (V.nterms < 0) return fail(nullptr, SG_EINVAL, "V.nterms < 0");
+    if (V.nterms > kMaxMono) return fail(nullptr, SG_EUNSUPPORTED, "more than 256 monomials");
+    if (V.nterms > 0 && (!V.coef || !V.nfac)) return fail(nullptr, SG_EINVAL, "NULL V arrays");
+
+    sg_ctx *ctx = new (std::nothrow) sg_ctx();
+    if (!ctx) return fail(nullptr, SG_ENOMEM, "host allocation failed");
+    Problem &p = ctx->prob;
+    p.D = D; p.L = L; p.prec = prec;
+    p.basis.assign(basis, basis + D);
+    p.grids.assign(grids, grids + D);
+    p.omega.assign(H->omega, H->omega + D);
+    p.mfoff.push_back(0);
+    for (int m = 0; m < V.nterms; m++) {
+        if (V.nfac[m] < 0 || V.nfac[m] > kMaxFac) { delete ctx; return fail(nullptr, SG_EUNSUPPORTED, "monomial with more than 8 factors"); }
+        if (!std::isfinite(V.coef[m])) { delete ctx; return fail(nullptr, SG_EINVAL, "V coefficient not finite"); }
+        if (V.nfac[m] > 0 && (!V.mode || !V.power)) { delete ctx; return fail(nullptr, SG_EINVAL, "NULL V factor arrays"); }
+        p.mcoef.push_back(V.coef[m]);
+        p.mnfac.push_back(V.nfac[m]);
+        int tot[kMaxD] = {0};
+        for (int f = p.mfoff[m]; f < p.mfoff[m] + V.nfac[m]; f++) {
+            if (V.mode[f] < 0 || V.mode[f] >= D) { delete ctx; return fail(nullptr, SG_EINVAL, "factor mode out of range"); }
+            if (V.power[f] < 1 || V.power[f] > kMaxPow) { delete ctx; return fail(nullptr, SG_EUNSUPPORTED, "factor power outside 1..16"); }
+            tot[V.mode[f]] += V.power[f];
+            if (tot[V.mode[f]] > kMaxPow) { delete ctx; return fail(nullptr, SG_EUNSUPPORTED, "total power of a mode > 16"); }
+            p.mfmode.push_back(V.mode[f]);
+            p.mfpow.push_back(V.power[f]);
+        }
+        p.mfoff.push_back(p.mfoff[m] + V.nfac[m]);
+    }
+    ctx->fp32 = (prec == SG_MIXED);
+    const int budget = std::min(smem_optin - 4096, ctx->fp32 ? 72 * 1024 : 110 * 1024);
+    std::string err = build_tables(p, budget, ctx->fp32 ? 4 : 8, &ctx->host);
+    if (!err.empty()) { delete ctx; return fail(nullptr, SG_EUNSUPPORTED, err); }
+    HostTables &T = ctx->host;
+    KParams &kp = ctx->kp;
+    kp.D = D; kp.L = L; kp.Dpad = T.Dpad;
+    kp.nmono = (int)p.mcoef.size(); kp.pmax = T.pmax; kp.kw = T.kw;
+    kp.n_cs = (int)T.n_cs; kp.n_terms = T.n_terms;
+    kp.cap = T.cap; kp.maxnb = T.maxnb; kp.matcap = T.matcap; kp.vtabcap = T.vtabcap;
+    *out = ctx;
+    return SG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sg_status sg_plan(int D, int L, const sg_basis *basis, const sg_grid *grids,
+                  const sg_hamiltonian *H, sg_precision prec, sg_ctx **out)
+{
+    return plan(D, L, basis, grids, H, prec, kPlanSmemOptin, out);
+}
+
+sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
+                    const sg_hamiltonian *H, sg_precision prec, sg_ctx **out)
+{
+    using namespace sg;
+    if (!out) return fail(nullptr, SG_EINVAL, "out is NULL");
+    *out = nullptr;
+    int device = 0, smem_optin = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+    e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
+    sg_ctx *ctx = nullptr;
+    sg_status st0 = plan(D, L, basis, grids, H, prec, smem_optin, &ctx);
+    if (st0 != SG_OK) return st0;
+    ctx->device = device;
+    Problem &p = ctx->prob;
+    HostTables &T = ctx->host;
+    KParams &kp = ctx->kp;
+    std::vector<float> tabf(T.tabd.begin(), T.tabd.end());
+    std::vector<int> zero(1, 0);
+    sg_status st = SG_OK;
+    const int *errp = nullptr;
+    if ((st = upload(ctx, T.levels, &kp.levels)) != SG_OK ||
+        (st = upload(ctx, T.coefs, &kp.coefs)) != SG_OK ||
+        (st = upload(ctx, T.order, &kp.order)) != SG_OK ||
+        (st = upload(ctx, T.rank_tab, &kp.rank_tab)) != SG_OK ||
+        (st = upload(ctx, T.lmin_tab, &kp.lmin_tab)) != SG_OK ||
+        (st = upload(ctx, T.lvl, &kp.lvl)) != SG_OK ||
+        (st = upload(ctx, T.tabd, &kp.tabd)) != SG_OK ||
+        (st = upload(ctx, tabf, &kp.tabf)) != SG_OK ||
+        (st = upload(ctx, p.mcoef, &kp.mcoef)) != SG_OK ||
+        (st = upload(ctx, p.mnfac, &kp.mnfac)) != SG_OK ||
+        (st = upload(ctx, p.mfoff, &kp.mfoff)) != SG_OK ||
+        (st = upload(ctx, p.mfmode, &kp.mfmode)) != SG_OK ||
+        (st = upload(ctx, p.mfpow, &kp.mfpow)) != SG_OK ||
+        (st = upload(ctx, zero, &errp)) != SG_OK) {
+        g_create_error = ctx->last_error;
+        free_all(ctx);
+        delete ctx;
+        return st;
+    }
+    kp.err = const_cast<int *>(errp);
+    ctx->has_device = true;
+    ctx->smem_bytes = apply_smem_bytes(kp, ctx->fp32);
+    e = configure_kernels(ctx->smem_bytes, ctx->fp32);
+    if (e != cudaSuccess) {
+        st = cuda_fail(nullptr, e, "cudaFuncSetAttribute");
+        free_all(ctx);
+        delete ctx;
+        return st;
+    }
+    *out = ctx;
+    return SG_OK;
+}
+
+sg_status sg_size(const sg_ctx *ctx, int64_t *n_cs, int64_t *n_terms, int64_t *n_s,
+                  int64_t *n_grid, int64_t *bytes_device)
+{
+    if (!ctx) return SG_EINVAL;
+    if (n_cs) *n_cs = ctx->host.n_cs;
+    if (n_terms) *n_terms = ctx->host.n_terms;
+    if (n_s) *n_s = ctx->host.n_s;
+    if (n_grid) *n_grid = ctx->host.n_grid;
+    if (bytes_device) *bytes_device = ctx->bytes_device;
+    return SG_OK;
+}
+
+sg_status sg_apply_H(sg_ctx *ctx, const double *x, double *y, int nvec, void *stream)
+{
+    if (!ctx) return SG_EINVAL;
+    if (!ctx->has_device) return fail(ctx, SG_EINVAL, "context was made by sg_plan (no device state)");
+    if (!x || !y) return fail(ctx, SG_EINVAL, "x or y is NULL");
+    if (nvec < 1) return fail(ctx, SG_EINVAL, "nvec must be >= 1");
+    const size_t n = (size_t)ctx->host.n_cs * nvec;
+    if ((x < y + n) && (y < x + n)) return fail(ctx, SG_EINVAL, "x and y overlap");
+    cudaError_t e = sg::launch_apply(ctx->kp, ctx->fp32, x, y, nvec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "apply launch");
+    return SG_OK;
+}
+
+sg_status sg_apply_H_host(sg_ctx *ctx, const double *x_host, double *y_host, int nvec, void *stream)
+{
+    if (!ctx) return SG_EINVAL;
+    if (!ctx->has_device) return fail(ctx, SG_EINVAL, "context was made by sg_plan (no device state)");
+    if (!x_host || !y_host) return fail(ctx, SG_EINVAL, "x_host or y_host is NULL");
+    if (nvec < 1) return fail(ctx, SG_EINVAL, "nvec must be >= 1");
+    const int64_t n = ctx->host.n_cs * (int64_t)nvec;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (n > ctx->stage_elems) {
+        if (ctx->stage_x) cudaFree(ctx->stage_x);
+        if (ctx->stage_y) cudaFree(ctx->stage_y);
+        ctx->stage_x = ctx->stage_y = nullptr;
+        ctx->stage_elems = 0;
+        if ((e = cudaMalloc(&ctx->stage_x, n * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&ctx->stage_y, n * sizeof(double))) != cudaSuccess)
+            return fail(ctx, SG_ENOMEM, std::string("staging cudaMalloc: ") + cudaGetErrorString(e));
+        ctx->stage_elems = n;
+    }
+    if ((e = cudaMemcpyAsync(ctx->stage_x, x_host, n * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "H2D copy");
+    if ((e = sg::launch_apply(ctx->kp, ctx->fp32, ctx->stage_x, ctx->stage_y, nvec, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "apply launch");
+    if ((e = cudaMemcpyAsync(y_host, ctx->stage_y, n * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "D2H copy");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+    return SG_OK;
+}
+
+sg_status sg_term_levels(const sg_ctx *ctx, int64_t t0, int64_t nt, int *levels_host, int *coef_host)
+{
+    if (!ctx) return SG_EINVAL;
+    const sg::HostTables &T = ctx->host;
+    if (t0 < 0 || nt < 0 || t0 + nt > T.n_terms || (nt > 0 && !levels_host)) return SG_EINVAL;
+    const int D = ctx->prob.D;
+    for (int64_t t = 0; t < nt; t++) {
+        for (int i = 0; i < D; i++) levels_host[t * D + i] = T.levels[(size_t)(t0 + t) * T.Dpad + i];
+        if (coef_host) coef_host[t] = T.coefs[t0 + t];
+    }
+    return SG_OK;
+}
+
+sg_status sg_index_map(sg_ctx *ctx, int64_t t0, int64_t nt, int64_t *offsets_host,
+                       int64_t *cs_index_dev, void *stream)
+{
+    if (!ctx) return SG_EINVAL;
+    const sg::HostTables &T = ctx->host;
+    if (t0 < 0 || nt < 0 || t0 + nt > T.n_terms || !offsets_host)
+        return fail(ctx, SG_EINVAL, "bad term range or NULL offsets");
+    const int D = ctx->prob.D, L = ctx->prob.L;
+    offsets_host[0] = 0;
+    for (int64_t t = 0; t < nt; t++) {
+        int64_t nb = 1;
+        for (int i = 0; i < D; i++) nb *= T.lvl[(size_t)i * (L + 1) + T.levels[(size_t)(t0 + t) * T.Dpad + i]].nb;
+        offsets_host[t + 1] = offsets_host[t] + nb;
+    }
+    if (!cs_index_dev || nt == 0) return SG_OK;
+    if (!ctx->has_device) return fail(ctx, SG_EINVAL, "context was made by sg_plan (no device state)");
+    int64_t *offs_dev = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMalloc(&offs_dev, sizeof(int64_t) * (nt + 1));
+    if (e != cudaSuccess) return fail(ctx, SG_ENOMEM, "cudaMalloc offsets");
+    e = cudaMemcpyAsync(offs_dev, offsets_host, sizeof(int64_t) * (nt + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = sg::launch_index_map(ctx->kp, t0, nt, offs_dev, cs_index_dev, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(offs_dev);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "index map");
+    return SG_OK;
+}
+
+sg_status sg_device_error(sg_ctx *ctx, int *code)
+{
+    if (!ctx || !code) return SG_EINVAL;
+    if (!ctx->has_device) return fail(ctx, SG_EINVAL, "context was made by sg_plan (no device state)");
+    int v = 0;
+    cudaError_t e = cudaMemcpy(&v, ctx->kp.err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "read error word");
+    *code = v;
+    if (v) {
+        int z = 0;
+        cudaMemcpy(ctx->kp.err, &z, sizeof(int), cudaMemcpyHostToDevice);
+    }
+    return SG_OK;
+}
+
+sg_status sg_compact_rank(const sg_ctx *ctx, const int *k, int64_t n, int64_t *rank)
+{
+    if (!ctx || n < 0 || (n > 0 && (!k || !rank))) return SG_EINVAL;
+    const sg::HostTables &T = ctx->host;
+    const int D = ctx->prob.D, L = ctx->prob.L;
+    for (int64_t q = 0; q < n; q++) {
+        const int *kq = k + q * D;
+        int64_t r = 0;
+        int s = 0;
+        bool ok = true;
+        for (int i = 0; i < D && ok; i++) {
+            if (kq[i] < 0 || kq[i] >= T.kw) { ok = false; break; }
+            const int lm = T.lmin_tab[(size_t)i * T.kw + kq[i]];
+            if (lm > L || s + lm > L) { ok = false; break; }
+            r += T.rank_tab[((size_t)i * (L + 1) + s) * T.kw + kq[i]];
+            s += lm;
+        }
+        rank[q] = ok ? r : -1;
+    }
+    return SG_OK;
+}
+
+sg_status sg_mode_tables(const sg_ctx *ctx, int mode, int level, int *nb, int *nq,
+                         double *B, double *BW, double *K, double *Q)
+{
+    if (!ctx || mode < 0 || mode >= ctx->prob.D || level < 0 || level > ctx->prob.L) return SG_EINVAL;
+    const sg::HostTables &T = ctx->host;
+    const sg::LevelInfo &li = T.lvl[(size_t)mode * (ctx->prob.L + 1) + level];
+    if (nb) *nb = li.nb;
+    if (nq) *nq = li.nq;
+    const double *t = T.tabd.data();
+    if (B) std::copy(t + li.offB, t + li.offB + li.nb * li.nq, B);
+    if (BW) std::copy(t + li.offBW, t + li.offBW + li.nb * li.nq, BW);
+    if (K) std::copy(t + li.offK, t + li.offK + li.nb * li.nb, K);
+    if (Q) std::copy(t + li.offQ, t + li.offQ + li.nq, Q);
+    return SG_OK;
+}
+
+const char *sg_last_error(const sg_ctx *ctx)
+{
+    return ctx ? ctx->last_error.c_str() : g_create_error.c_str();
+}
+
+void sg_destroy(sg_ctx *ctx)
+{
+    if (!ctx) return;
+    free_all(ctx);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,437 @@
+// Smolyak operator action on the GPU (sm_103a).
+//
+// One thread block per Smolyak term (terms ordered most-expensive first).  For
+// term l the block performs Alg. 1 of arXiv 2111.13655:
+//   1. extract the term from the compact vector (mapping table M^B, Table 2),
+//      the compact index computed combinatorially;
+//   2. basis -> grid, one mode at a time (Eq. (15));
+//   3. the operator on the grid: the potential multiplied point-wise; the
+//      kinetic part applied as per-mode matrices K_j = -omega_j/2 B_j^T W_j D2_j
+//      (equal to applying b'' on the grid because B_i^T W_i B_i = I for nq >= nb);
+//   4. grid -> basis (Eq. (14));
+//   5. compress-add D_l * result into the compact output (Eq. (16)), FP64 atomics.
+// Modes whose level holds a single basis function (nb = 1) are not expanded:
+// their quadrature sum is folded exactly into the potential through the
+// moments mu_p = sum_u w_u b_0(Q_u)^2 Q_u^p (the term tensor is rank one along
+// such a mode), so only the modes with nb > 1 ("slots") are transformed.
+// Terms whose grid does not fit in shared memory are processed in slices over
+// their first `s` slots (depth-first over the slice index, breadth-first
+// inside), which leaves the arithmetic of every slot unchanged.
+#include <cstdint>
+
+#include "sg_internal.h"
+
+namespace sg {
+
+namespace {
+
+struct Mono1 { int slot, pow; double cf; };
+struct Mono2 { int pair, pa, pb, pad; double cf; };
+struct PairT { int a, b, off, pad; };
+struct MonoG { int m, pad; double cf; };
+
+struct TermHdr {
+    int m, NB, s, NBO, NBI, nslice, nfib, bad;
+    int n1, npair, n2, ng, fsum;
+    int mode[kMaxD], lev[kMaxD], nb[kMaxD], nq[kMaxD];
+    int oB[kMaxD], oBW[kMaxD], oK[kMaxD], oF[kMaxD];  // shared-memory offsets per slot
+    int gQ[kMaxD];                                     // global offset of Q_u per slot
+    int stride[kMaxD];                                 // basis-tensor strides (last slot fastest)
+    int slot_of_mode[kMaxD];
+    int uS[kMaxD];                                     // grid indices of the current slice
+    double coef, C0, Kc;
+};
+
+__device__ __forceinline__ void set_err(const KParams &P, int code)
+{
+    if (P.err) atomicCAS(P.err, 0, code);
+}
+
+// Serial per-term set-up (thread 0): slots, split, shared-memory offsets and
+// the potential folded over the nb = 1 modes, grouped by the slots it touches.
+__device__ void decode_term(const KParams &P, int t, TermHdr &H, Mono1 *m1, Mono2 *m2, PairT *pr,
+                            MonoG *mg)
+{
+    const uint8_t *lt = P.levels + (size_t)t * P.Dpad;
+    H.m = 0; H.NB = 1; H.bad = 0; H.Kc = 0.0;
+    int mat = 0;
+    for (int i = 0; i < P.D; i++) {
+        const LevelInfo li = P.lvl[i * (P.L + 1) + lt[i]];
+        if (li.nb > 1) {
+            int j = H.m++;
+            H.mode[j] = i; H.lev[j] = lt[i]; H.nb[j] = li.nb; H.nq[j] = li.nq;
+            H.slot_of_mode[i] = j;
+            H.oB[j] = mat;  mat += li.nq * li.nb;
+            H.oBW[j] = mat; mat += li.nb * li.nq;
+            H.oK[j] = mat;  mat += li.nb * li.nb;
+            H.gQ[j] = li.offQ;
+            H.NB *= li.nb;
+        } else {
+            H.slot_of_mode[i] = -1;
+            H.Kc += P.tabd[li.offK];  // 1x1 kinetic matrix of a collapsed mode
+        }
+    }
+    if (mat > P.matcap || H.NB > P.maxnb) { H.bad = 1; return; }
+    int st = 1;
+    for (int j = H.m - 1; j >= 0; j--) { H.stride[j] = st; st *= H.nb[j]; }
+    // split: smallest s whose inner working set fits a grid buffer
+    H.s = 0;
+    if (H.m > 0) {
+        for (int s = 0; s < H.m; s++) {
+            int64_t stage = H.nb[H.m - 1];
+            for (int j = s; j <= H.m - 2; j++) stage *= H.nq[j];
+            H.s = s;
+            if (stage <= P.cap) break;
+        }
+        int64_t stage = H.nb[H.m - 1];
+        for (int j = H.s; j <= H.m - 2; j++) stage *= H.nq[j];
+        if (stage > P.cap) { H.bad = 2; return; }
+    }
+    H.NBO = 1; H.nslice = 1;
+    for (int j = 0; j < H.s; j++) { H.NBO *= H.nb[j]; H.nslice *= H.nq[j]; }
+    H.NBI = H.NB / H.NBO;
+    H.nfib = 1;
+    for (int j = H.s; j <= H.m - 2; j++) H.nfib *= H.nq[j];
+    int f = 0;
+    for (int j = 0; j < H.m; j++) { H.oF[j] = f; f += H.nq[j]; }
+    H.fsum = f;
+    // potential: fold collapsed modes through their moments, group by slots
+    H.C0 = 0.0; H.n1 = H.npair = H.n2 = H.ng = 0;
+    int voff = f;
+    for (int mm = 0; mm < P.nmono; mm++) {
+        int fmode[kMaxFac], fpow[kMaxFac], nf = 0;
+        for (int q = P.mfoff[mm]; q < P.mfoff[mm + 1]; q++) {
+            int md = P.mfmode[q], pw = P.mfpow[q], k = 0;
+            while (k < nf && fmode[k] != md) k++;
+            if (k == nf) { fmode[nf] = md; fpow[nf] = pw; nf++; } else fpow[k] += pw;
+        }
+        double cf = P.mcoef[mm];
+        int zs[kMaxFac], zp[kMaxFac], nz = 0;
+        for (int k = 0; k < nf; k++) {
+            int sl = H.slot_of_mode[fmode[k]];
+            if (sl < 0) {
+                const LevelInfo li = P.lvl[fmode[k] * (P.L + 1) + lt[fmode[k]]];
+                cf *= P.tabd[li.offMu + fpow[k]];
+            } else { zs[nz] = sl; zp[nz] = fpow[k]; nz++; }
+        }
+        if (nz == 0) {
+            H.C0 += cf;
+        } else if (nz == 1) {
+            m1[H.n1++] = Mono1{zs[0], zp[0], cf};
+        } else if (nz == 2) {
+            int a = zs[0], b = zs[1], pa = zp[0], pb = zp[1];
+            if (a > b) { int tt = a; a = b; b = tt; tt = pa; pa = pb; pb = tt; }
+            int p = 0;
+            while (p < H.npair && !(pr[p].a == a && pr[p].b == b)) p++;
+            if (p == H.npair) {
+                if (voff + H.nq[a] * H.nq[b] > P.vtabcap) { H.bad = 3; return; }
+                pr[p] = PairT{a, b, voff, 0};
+                voff += H.nq[a] * H.nq[b];
+                H.npair++;
+            }
+            m2[H.n2++] = Mono2{p, pa, pb, 0, cf};
+        } else {
+            mg[H.ng++] = MonoG{mm, 0, cf};
+        }
+    }
+    if (f > P.vtabcap) { H.bad = 3; return; }
+    H.coef = (double)P.coefs[t];
+}
+
+// compact index of the basis function with per-slot indices k[0..m-1]
+__device__ __forceinline__ int rank_of(const KParams &P, const TermHdr &H, const int *k)
+{
+    int r = 0, s = 0;
+    for (int j = 0; j < H.m; j++) {
+        const int i = H.mode[j];
+        r += P.rank_tab[(i * (P.L + 1) + s) * P.kw + k[j]];
+        s += P.lmin_tab[i * P.kw + k[j]];
+    }
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T ipow(T q, int p)
+{
+    T r = T(1);
+    for (int e = 0; e < p; e++) r *= q;
+    return r;
+}
+
+// out[a][r][c] = sum_k M[r*n + k] * in[a][k][c]
+template <typename T>
+__device__ void contract(const T *in, T *out, int A, int n, int r, int C, const T *M)
+{
+    const int total = A * r * C;
+    for (int e = threadIdx.x; e < total; e += kThreads) {
+        const int c = e % C;
+        const int tq = e / C;
+        const int rr = tq % r;
+        const int a = tq / r;
+        const T *ip = in + (a * n) * C + c;
+        const T *mp = M + rr * n;
+        T acc = T(0);
+        for (int k = 0; k < n; k++) acc += mp[k] * ip[k * C];
+        out[e] = acc;
+    }
+}
+
+template <typename T> struct Tab;
+template <> struct Tab<double> { static __device__ const double *get(const KParams &P) { return P.tabd; } };
+template <> struct Tab<float> { static __device__ const float *get(const KParams &P) { return P.tabf; } };
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_apply(const KParams P, const double *__restrict__ x,
+                                                    double *__restrict__ y, int nvec)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ TermHdr H;
+    const int tid = threadIdx.x;
+    const int nm = P.nmono > 0 ? P.nmono : 1;
+    Mono1 *m1 = reinterpret_cast<Mono1 *>(smraw);
+    Mono2 *m2 = reinterpret_cast<Mono2 *>(m1 + nm);
+    PairT *pr = reinterpret_cast<PairT *>(m2 + nm);
+    MonoG *mg = reinterpret_cast<MonoG *>(pr + nm);
+    T *mats = reinterpret_cast<T *>(mg + nm);
+    T *vtab = mats + P.matcap;
+    T *X = vtab + P.vtabcap;
+    T *Y = X + P.maxnb;
+    T *WoF = Y + P.maxnb;
+    T *WoB = WoF + P.maxnb;
+    T *bufA = WoB + P.maxnb;
+    T *bufB = bufA + P.cap;
+    int *rk = reinterpret_cast<int *>(bufB + P.cap);
+
+    const int t = P.order[blockIdx.x];
+    if (tid == 0) decode_term(P, t, H, m1, m2, pr, mg);
+    __syncthreads();
+    if (H.bad) {
+        if (tid == 0) set_err(P, 100 + H.bad);
+        return;
+    }
+    const T *tab = Tab<T>::get(P);
+    const int m = H.m;
+
+    // per-slot 1D matrices into shared memory
+    for (int j = 0; j < m; j++) {
+        const LevelInfo li = P.lvl[H.mode[j] * (P.L + 1) + H.lev[j]];
+        const int nbq = li.nb * li.nq;
+        for (int e = tid; e < nbq; e += kThreads) {
+            mats[H.oB[j] + e] = tab[li.offB + e];
+            mats[H.oBW[j] + e] = tab[li.offBW + e];
+        }
+        for (int e = tid; e < li.nb * li.nb; e += kThreads) mats[H.oK[j] + e] = tab[li.offK + e];
+    }
+    // potential tables: f_j[u] for one-slot monomials, g_p[ua][ub] for two-slot ones
+    for (int e = tid; e < H.fsum; e += kThreads) {
+        int j = 0;
+        while (j + 1 < m && e >= H.oF[j + 1]) j++;
+        const int u = e - H.oF[j];
+        const double q = P.tabd[H.gQ[j] + u];
+        double v = 0.0;
+        for (int a = 0; a < H.n1; a++)
+            if (m1[a].slot == j) v += m1[a].cf * ipow(q, m1[a].pow);
+        vtab[e] = (T)v;
+    }
+    for (int p = 0; p < H.npair; p++) {
+        const int a = pr[p].a, b = pr[p].b, nqb = H.nq[b];
+        for (int e = tid; e < H.nq[a] * nqb; e += kThreads) {
+            const int ua = e / nqb, ub = e % nqb;
+            const double qa = P.tabd[H.gQ[a] + ua], qb = P.tabd[H.gQ[b] + ub];
+            double v = 0.0;
+            for (int c = 0; c < H.n2; c++)
+                if (m2[c].pair == p) v += m2[c].cf * ipow(qa, m2[c].pa) * ipow(qb, m2[c].pb);
+            vtab[pr[p].off + e] = (T)v;
+        }
+    }
+    // compact indices of the term's basis functions
+    for (int e = tid; e < H.NB; e += kThreads) {
+        int k[kMaxD], rem = e;
+        for (int j = m - 1; j >= 0; j--) { k[j] = rem % H.nb[j]; rem /= H.nb[j]; }
+        rk[e] = rank_of(P, H, k);
+    }
+    __syncthreads();
+
+    for (int v = 0; v < nvec; v++) {
+        const double *xv = x + (size_t)v * P.n_cs;
+        double *yv = y + (size_t)v * P.n_cs;
+        for (int e = tid; e < H.NB; e += kThreads) { X[e] = (T)__ldg(xv + rk[e]); Y[e] = T(0); }
+        __syncthreads();
+        if (m > 0) {
+            const int s = H.s, mL = m - 1, nbL = H.nb[mL], nqL = H.nq[mL];
+            for (int sl = 0; sl < H.nslice; sl++) {
+                if (tid == 0) {
+                    int rem = sl;
+                    for (int j = s - 1; j >= 0; j--) { H.uS[j] = rem % H.nq[j]; rem /= H.nq[j]; }
+                }
+                __syncthreads();
+                // slice weights over the outer slots
+                for (int ko = tid; ko < H.NBO; ko += kThreads) {
+                    int rem = ko;
+                    T wf = T(1), wb = T(1);
+                    for (int j = s - 1; j >= 0; j--) {
+                        const int kj = rem % H.nb[j];
+                        rem /= H.nb[j];
+                        wf *= mats[H.oB[j] + H.uS[j] * H.nb[j] + kj];
+                        wb *= mats[H.oBW[j] + kj * H.nq[j] + H.uS[j]];
+                    }
+                    WoF[ko] = wf; WoB[ko] = wb;
+                }
+                __syncthreads();
+                for (int ki = tid; ki < H.NBI; ki += kThreads) {
+                    T acc = T(0);
+                    for (int ko = 0; ko < H.NBO; ko++) acc += WoF[ko] * X[ko * H.NBI + ki];
+                    bufA[ki] = acc;
+                }
+                __syncthreads();
+                T *cur = bufA, *oth = bufB;
+                // basis -> grid over the inner slots but the last
+                int A = 1;
+                for (int j = s; j < mL; j++) {
+                    int C = 1;
+                    for (int i = j + 1; i < m; i++) C *= H.nb[i];
+                    contract(cur, oth, A, H.nb[j], H.nq[j], C, mats + H.oB[j]);
+                    A *= H.nq[j];
+                    T *tp = cur; cur = oth; oth = tp;
+                    __syncthreads();
+                }
+                // last slot: basis -> grid, potential, grid -> basis, one fibre per thread
+                const T *BL = mats + H.oB[mL];
+                const T *BWL = mats + H.oBW[mL];
+                for (int fb = tid; fb < H.nfib; fb += kThreads) {
+                    int u[kMaxD];
+                    for (int j = 0; j < s; j++) u[j] = H.uS[j];
+                    int rem = fb;
+                    for (int j = mL - 1; j >= s; j--) { u[j] = rem % H.nq[j]; rem /= H.nq[j]; }
+                    T vpre = (T)H.C0;
+                    for (int j = 0; j < mL; j++) vpre += vtab[H.oF[j] + u[j]];
+                    for (int p = 0; p < H.npair; p++)
+                        if (pr[p].b != mL) vpre += vtab[pr[p].off + u[pr[p].a] * H.nq[pr[p].b] + u[pr[p].b]];
+                    T gin[kMaxLevelSize], acc[kMaxLevelSize];
+                    for (int k = 0; k < nbL; k++) { gin[k] = cur[fb * nbL + k]; acc[k] = T(0); }
+                    for (int uL = 0; uL < nqL; uL++) {
+                        T g = T(0);
+                        for (int k = 0; k < nbL; k++) g += BL[uL * nbL + k] * gin[k];
+                        T V = vpre + vtab[H.oF[mL] + uL];
+                        for (int p = 0; p < H.npair; p++)
+                            if (pr[p].b == mL) V += vtab[pr[p].off + u[pr[p].a] * nqL + uL];
+                        if (H.ng) {
+                            u[mL] = uL;
+                            for (int c = 0; c < H.ng; c++) {
+                                T term = (T)mg[c].cf;
+                                const int mm = mg[c].m;
+                                for (int q = P.mfoff[mm]; q < P.mfoff[mm + 1]; q++) {
+                                    const int sl2 = H.slot_of_mode[P.mfmode[q]];
+                                    if (sl2 >= 0)
+                                        term *= ipow((T)P.tabd[H.gQ[sl2] + u[sl2]], P.mfpow[q]);
+                                }
+                                V += term;
+                            }
+                        }
+                        const T w = V * g;
+                        for (int k = 0; k < nbL; k++) acc[k] += BWL[k * nqL + uL] * w;
+                    }
+                    for (int k = 0; k < nbL; k++) cur[fb * nbL + k] = acc[k];
+                }
+                __syncthreads();
+                // grid -> basis over the inner slots but the last, in reverse order
+                for (int j = mL - 1; j >= s; j--) {
+                    int Aj = 1, C = 1;
+                    for (int i = s; i < j; i++) Aj *= H.nq[i];
+                    for (int i = j + 1; i < m; i++) C *= H.nb[i];
+                    contract(cur, oth, Aj, H.nq[j], H.nb[j], C, mats + H.oBW[j]);
+                    T *tp = cur; cur = oth; oth = tp;
+                    __syncthreads();
+                }
+                // accumulate the slice into the term result
+                for (int e = tid; e < H.NB; e += kThreads) {
+                    const int ko = e / H.NBI, ki = e - ko * H.NBI;
+                    Y[e] += WoB[ko] * cur[ki];
+                }
+                __syncthreads();
+            }
+        }
+        // kinetic part in the basis, then compress-add with the combination coefficient
+        for (int e = tid; e < H.NB; e += kThreads) {
+            T acc = (T)(H.C0 * (m == 0) + H.Kc) * X[e];
+            int rem = e;
+            for (int j = m - 1; j >= 0; j--) {
+                const int nbj = H.nb[j], kj = rem % nbj;
+                rem /= nbj;
+                const int base = e - kj * H.stride[j];
+                const T *Kr = mats + H.oK[j] + kj * nbj;
+                for (int kp = 0; kp < nbj; kp++) acc += Kr[kp] * X[base + kp * H.stride[j]];
+            }
+            const double val = H.coef * (double)(Y[e] + acc);
+            atomicAdd(yv + rk[e], val);
+        }
+        __syncthreads();
+    }
+}
+
+// Mapping table M^B (Table 2) for terms [t0, t0+nt): k_0 fastest inside a term.
+__global__ void __launch_bounds__(kThreads) k_index_map(const KParams P, int64_t t0,
+                                                        const int64_t *__restrict__ offs,
+                                                        int64_t *__restrict__ out)
+{
+    __shared__ TermHdr H;
+    const int64_t t = t0 + blockIdx.x;
+    if (threadIdx.x == 0) {
+        const uint8_t *lt = P.levels + (size_t)t * P.Dpad;
+        H.m = 0; H.NB = 1;
+        for (int i = 0; i < P.D; i++) {
+            const LevelInfo li = P.lvl[i * (P.L + 1) + lt[i]];
+            if (li.nb > 1) { int j = H.m++; H.mode[j] = i; H.nb[j] = li.nb; H.NB *= li.nb; }
+        }
+    }
+    __syncthreads();
+    const int64_t base = offs[blockIdx.x];
+    for (int e = threadIdx.x; e < H.NB; e += kThreads) {
+        int k[kMaxD], rem = e;
+        for (int j = 0; j < H.m; j++) { k[j] = rem % H.nb[j]; rem /= H.nb[j]; }
+        out[base + e] = rank_of(P, H, k);
+    }
+}
+
+}  // namespace
+
+size_t apply_smem_bytes(const KParams &kp, bool fp32)
+{
+    const size_t rb = fp32 ? 4 : 8;
+    const size_t nm = kp.nmono > 0 ? kp.nmono : 1;
+    return nm * (sizeof(Mono1) + sizeof(Mono2) + sizeof(PairT) + sizeof(MonoG)) +
+           rb * ((size_t)kp.matcap + kp.vtabcap + 4 * (size_t)kp.maxnb + 2 * (size_t)kp.cap) +
+           4 * (size_t)kp.maxnb;
+}
+
+cudaError_t configure_kernels(size_t smem, bool fp32)
+{
+    if (fp32)
+        return cudaFuncSetAttribute(k_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(k_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_apply(const KParams &kp, bool fp32, const double *x, double *y, int nvec,
+                         cudaStream_t stream)
+{
+    const size_t smem = apply_smem_bytes(kp, fp32);
+    cudaError_t e = cudaMemsetAsync(y, 0, sizeof(double) * (size_t)kp.n_cs * nvec, stream);
+    if (e != cudaSuccess) return e;
+    if (kp.n_terms == 0) return cudaSuccess;
+    dim3 grid((unsigned)kp.n_terms);
+    if (fp32)
+        k_apply<float><<<grid, kThreads, smem, stream>>>(kp, x, y, nvec);
+    else
+        k_apply<double><<<grid, kThreads, smem, stream>>>(kp, x, y, nvec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_index_map(const KParams &kp, int64_t t0, int64_t nt, const int64_t *offs,
+                             int64_t *out, cudaStream_t stream)
+{
+    if (nt <= 0) return cudaSuccess;
+    k_index_map<<<(unsigned)nt, kThreads, 0, stream>>>(kp, t0, offs, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sg

@@ -1,0 +1,113 @@
+// Internal declarations of libsmolyak (host setup <-> CUDA kernels <-> C ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/smolyak.h"
+
+namespace sg {
+
+constexpr int kMaxD = 32;          // modes per problem
+constexpr int kMaxLevelSize = 32;  // nb(l), nq(l) at any level
+constexpr int kMaxMono = 256;      // monomials in V
+constexpr int kMaxFac = 8;         // factors per monomial
+constexpr int kMaxPow = 16;        // power of one factor
+constexpr int kThreads = 128;      // threads per term-CTA
+
+// Per (mode, level) entry: sizes and element offsets into the flat tables.
+struct LevelInfo {
+    int nb, nq;
+    int offB;   // B[u*nb+k]   = b_k(Q_u)                 (nq x nb)
+    int offBW;  // BW[k*nq+u]  = w_u b_k(Q_u)             (nb x nq)
+    int offK;   // K[k*nb+k']  = -omega/2 <b_k|d2/dQ2|b_k'> on the grid (nb x nb)
+    int offQ;   // Q[u]        = Q_u                      (nq)
+    int offMu;  // mu[p]       = sum_u w_u b_0(Q_u)^2 Q_u^p, p = 0..pmax (pmax+1)
+};
+
+// Everything a kernel needs, passed by value.
+struct KParams {
+    int D, L, Dpad;
+    int nmono, pmax, kw;
+    int n_cs;
+    int64_t n_terms;
+    const uint8_t *levels;   // [n_terms][Dpad], Table-2 order
+    const int *coefs;        // [n_terms] combination coefficient D_l
+    const int *order;        // [n_terms] Table-2 index of the p-th processed term
+    const int *rank_tab;     // [D][L+1][kw]: partial ranks T_i[s][k]
+    const uint8_t *lmin_tab; // [D][kw]: smallest level holding function k
+    const LevelInfo *lvl;    // [D][L+1]
+    const double *tabd;      // flat FP64 tables
+    const float *tabf;       // FP32 copies (same offsets)
+    const double *mcoef;     // [nmono]
+    const int *mnfac;        // [nmono]
+    const int *mfoff;        // [nmono+1]
+    const int *mfmode;       // [sum nfac]
+    const int *mfpow;        // [sum nfac]
+    // capacities of the per-CTA shared-memory areas (elements)
+    int cap;       // each of the two grid ping-pong buffers
+    int maxnb;     // term basis tensor
+    int matcap;    // per-term 1D matrices
+    int vtabcap;   // per-term potential tables
+    int *err;      // device error word (0 = fine)
+};
+
+// Host-side description of a problem (after validation).
+struct Problem {
+    int D = 0, L = 0;
+    std::vector<sg_basis> basis;
+    std::vector<sg_grid> grids;
+    std::vector<double> omega;
+    std::vector<double> mcoef;
+    std::vector<int> mnfac, mfoff, mfmode, mfpow;
+    sg_precision prec = SG_FP64;
+};
+
+// Result of the host setup: everything that is uploaded.
+struct HostTables {
+    int Dpad = 0, pmax = 0, kw = 0;
+    int64_t n_terms = 0, n_cs = 0, n_s = 0, n_grid = 0;
+    std::vector<uint8_t> levels;     // [n_terms][Dpad]
+    std::vector<int> coefs;          // [n_terms]
+    std::vector<int> order;          // processing order (Table-2 indices)
+    std::vector<int> rank_tab;       // [D][L+1][kw]
+    std::vector<uint8_t> lmin_tab;   // [D][kw]
+    std::vector<LevelInfo> lvl;      // [D][L+1]
+    std::vector<double> tabd;
+    int cap = 0, maxnb = 0, matcap = 0, vtabcap = 0;
+    int64_t flops_per_vec = 0;       // FMA-counted work of one real apply (2 flops per FMA)
+};
+
+// Host setup (sg_setup.cpp).  Returns an empty string on success, else the error text.
+std::string build_tables(const Problem &p, int smem_budget_bytes, int real_bytes, HostTables *out);
+
+// One-mode Gauss-Hermite rule with Hermite-function-normalised weights.
+std::string gauss_hermite(int n, std::vector<double> *x, std::vector<double> *wf);
+
+// Kernel launchers (sg_apply.cu).  Return cudaSuccess or the launch error.
+cudaError_t launch_apply(const KParams &kp, bool fp32, const double *x, double *y, int nvec,
+                         cudaStream_t stream);
+cudaError_t launch_index_map(const KParams &kp, int64_t t0, int64_t nt, const int64_t *offsets_dev,
+                             int64_t *cs_index, cudaStream_t stream);
+size_t apply_smem_bytes(const KParams &kp, bool fp32);
+cudaError_t configure_kernels(size_t smem_bytes, bool fp32);
+
+}  // namespace sg
+
+struct sg_ctx {
+    sg::Problem prob;
+    sg::HostTables host;
+    sg::KParams kp{};
+    int device = 0;
+    bool fp32 = false;
+    bool has_device = false;  // false for contexts made by sg_plan
+    size_t smem_bytes = 0;
+    int64_t bytes_device = 0;
+    std::vector<void *> allocations;
+    double *stage_x = nullptr, *stage_y = nullptr;  // host-API staging (device)
+    int64_t stage_elems = 0;
+    std::string last_error;
+};

@@ -1,0 +1,315 @@
+// Host setup of libsmolyak: 1D tables, terms, compact ranking, capacities.
+//
+// Everything here runs once per sg_create.  The formulas follow the paper
+// (arXiv 2111.13655):
+//   - terms l in R(l): L-n+1 <= |l| <= L, coefficient D_l = (-1)^{L-|l|} C(n-1, L-|l|)
+//     (Sec. 2, Eq. (8)), numbered in Table-2 order (l_0 varies fastest);
+//   - level -> size rules nb(l) = A + B l, nq(l) = A' + B' l (Sec. 2);
+//   - compact basis = union of the term boxes, lexicographic with mode 0
+//     slowest (Table 2), ranked combinatorially instead of through a stored
+//     mapping table M^B (Sec. 3);
+//   - 1D transfer matrices of Eqs. (14)/(15) on Gauss-Hermite grids.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+
+#include "sg_internal.h"
+
+namespace sg {
+
+namespace {
+
+// Orthonormal Hermite functions h_0..h_{n-1} at x (stable normalised recurrence).
+void hermite_fns(int n, double x, double *h)
+{
+    const double pi_m14 = 0.75112554446494248286;  // pi^(-1/4)
+    h[0] = pi_m14 * std::exp(-0.5 * x * x);
+    if (n > 1) h[1] = std::sqrt(2.0) * x * h[0];
+    for (int k = 2; k < n; k++)
+        h[k] = std::sqrt(2.0 / k) * x * h[k - 1] - std::sqrt((k - 1.0) / k) * h[k - 2];
+}
+
+int64_t binom(int n, int k)
+{
+    if (k < 0 || n < 0 || k > n) return 0;
+    int64_t r = 1;
+    for (int i = 1; i <= k; i++) r = r * (n - k + i) / i;
+    return r;
+}
+
+int nsz(int A, int B, int l) { return A + B * l; }
+
+}  // namespace
+
+// Gauss-Hermite rule: nodes are the n zeros of h_n, bracketed by a sign scan of
+// h_n over (-sqrt(2n+1)-1/2, sqrt(2n+1)+1/2), bisected and Newton-polished with
+// h_n' = sqrt(2n) h_{n-1} - x h_n; weights in the Hermite-function
+// normalisation from the Christoffel function, wf_u = 1 / sum_{k<n} h_k(x_u)^2
+// (so that sum_u wf_u h_k(x_u) h_k'(x_u) = delta_kk' for k, k' < n).
+std::string gauss_hermite(int n, std::vector<double> *x, std::vector<double> *wf)
+{
+    x->assign(n, 0.0);
+    wf->assign(n, 0.0);
+    if (n < 1 || n > 64) return "gauss_hermite: n out of range";
+    std::vector<double> h(n + 1);
+    auto hn = [&](double t) { hermite_fns(n + 1, t, h.data()); return h[n]; };
+    const double a = std::sqrt(2.0 * n + 1.0) + 0.5;
+    const int scan = 400 * n;
+    auto polish = [&](double r) {
+        for (int it = 0; it < 3; it++) {
+            hermite_fns(n + 1, r, h.data());
+            double d = std::sqrt(2.0 * n) * h[n - 1] - r * h[n];
+            if (d != 0.0 && h[n] != 0.0) r -= h[n] / d;
+        }
+        return r;
+    };
+    int found = 0;
+    double t0 = -a, f0 = hn(t0);
+    for (int i = 1; i <= scan && found < n; i++) {
+        double t1 = -a + 2.0 * a * i / scan, f1 = hn(t1);
+        if (f1 == 0.0) {                 // the scan landed on a zero
+            (*x)[found++] = polish(t1);
+        } else if (f0 != 0.0 && (f0 < 0) != (f1 < 0)) {
+            double lo = t0, hi = t1, flo = f0;
+            for (int it = 0; it < 200 && hi - lo > 1e-15 * (1 + std::fabs(lo)); it++) {
+                double mid = 0.5 * (lo + hi), fm = hn(mid);
+                if (fm == 0.0) { lo = hi = mid; break; }
+                if ((fm < 0) == (flo < 0)) { lo = mid; flo = fm; } else { hi = mid; }
+            }
+            (*x)[found++] = polish(0.5 * (lo + hi));
+        }
+        t0 = t1; f0 = f1;
+    }
+    if (found != n) return "gauss_hermite: root bracketing failed";
+    if (n % 2 == 1) (*x)[n / 2] = 0.0;
+    for (int u = 0; u < n; u++) {  // enforce the exact symmetry of the rule
+        double s = 0.5 * ((*x)[n - 1 - u] - (*x)[u]);
+        if (u < n / 2) { (*x)[u] = -s; (*x)[n - 1 - u] = s; }
+    }
+    for (int u = 0; u < n; u++) {
+        hermite_fns(n, (*x)[u], h.data());
+        double s = 0.0;
+        for (int k = 0; k < n; k++) s += h[k] * h[k];
+        (*wf)[u] = 1.0 / s;
+    }
+    return "";
+}
+
+std::string build_tables(const Problem &p, int smem_budget, int rb, HostTables *out)
+{
+    HostTables &T = *out;
+    const int D = p.D, L = p.L;
+    char buf[256];
+
+    // ---------------- per (mode, level) 1D tables ----------------
+    T.pmax = 0;
+    for (int m = 0; m < (int)p.mnfac.size(); m++) {
+        // largest total power of one mode inside one monomial
+        int pw[kMaxD] = {0};
+        for (int f = p.mfoff[m]; f < p.mfoff[m + 1]; f++) pw[p.mfmode[f]] += p.mfpow[f];
+        for (int i = 0; i < D; i++) T.pmax = std::max(T.pmax, pw[i]);
+    }
+    T.lvl.assign((size_t)D * (L + 1), LevelInfo{});
+    T.tabd.clear();
+    for (int i = 0; i < D; i++) {
+        const double q0 = p.basis[i].q0, s = p.basis[i].scale;
+        for (int l = 0; l <= L; l++) {
+            LevelInfo &li = T.lvl[(size_t)i * (L + 1) + l];
+            li.nb = nsz(p.basis[i].nb_A, p.basis[i].nb_B, l);
+            li.nq = nsz(p.grids[i].nq_A, p.grids[i].nq_B, l);
+            const int nb = li.nb, nq = li.nq;
+            std::vector<double> xg, wf;
+            std::string e = gauss_hermite(nq, &xg, &wf);
+            if (!e.empty()) return e;
+            std::vector<double> h(nb + 2), B(nq * nb), BW(nb * nq), D2(nq * nb), Q(nq), W(nq);
+            for (int u = 0; u < nq; u++) {
+                hermite_fns(nb + 2, xg[u], h.data());
+                W[u] = wf[u] / s;
+                Q[u] = q0 + xg[u] / s;
+                for (int k = 0; k < nb; k++) {
+                    B[u * nb + k] = std::sqrt(s) * h[k];
+                    // b_k'' from the ladder form of d/dx applied twice:
+                    //   h_k'' = 1/2 sqrt(k(k-1)) h_{k-2} - (k+1/2) h_k + 1/2 sqrt((k+1)(k+2)) h_{k+2}
+                    double d2 = -(k + 0.5) * h[k] + 0.5 * std::sqrt((k + 1.0) * (k + 2.0)) * h[k + 2];
+                    if (k >= 2) d2 += 0.5 * std::sqrt(k * (k - 1.0)) * h[k - 2];
+                    D2[u * nb + k] = std::sqrt(s) * s * s * d2;
+                }
+            }
+            for (int k = 0; k < nb; k++)
+                for (int u = 0; u < nq; u++) BW[k * nq + u] = W[u] * B[u * nb + k];
+            li.offB = (int)T.tabd.size();
+            T.tabd.insert(T.tabd.end(), B.begin(), B.end());
+            li.offBW = (int)T.tabd.size();
+            T.tabd.insert(T.tabd.end(), BW.begin(), BW.end());
+            li.offK = (int)T.tabd.size();
+            for (int k = 0; k < nb; k++)
+                for (int kp = 0; kp < nb; kp++) {
+                    double acc = 0.0;
+                    for (int u = 0; u < nq; u++) acc += BW[k * nq + u] * D2[u * nb + kp];
+                    T.tabd.push_back(-0.5 * p.omega[i] * acc);
+                }
+            li.offQ = (int)T.tabd.size();
+            T.tabd.insert(T.tabd.end(), Q.begin(), Q.end());
+            li.offMu = (int)T.tabd.size();
+            for (int pw = 0; pw <= T.pmax; pw++) {
+                double acc = 0.0;
+                for (int u = 0; u < nq; u++) acc += W[u] * B[u * nb] * B[u * nb] * std::pow(Q[u], pw);
+                T.tabd.push_back(acc);
+            }
+        }
+    }
+    if (T.tabd.size() >= (size_t)1 << 30) return "tables too large";
+
+    // ---------------- compact ranking ----------------
+    // lmin_i(k) = smallest level whose basis holds function k of mode i.
+    T.kw = 0;
+    for (int i = 0; i < D; i++) T.kw = std::max(T.kw, nsz(p.basis[i].nb_A, p.basis[i].nb_B, L));
+    const int kw = T.kw;
+    T.lmin_tab.assign((size_t)D * kw, 255);
+    for (int i = 0; i < D; i++)
+        for (int k = 0; k < kw; k++) {
+            int l = 0;
+            while (l <= L && nsz(p.basis[i].nb_A, p.basis[i].nb_B, l) <= k) l++;
+            if (l <= L) T.lmin_tab[(size_t)i * kw + k] = (uint8_t)l;
+        }
+    // cnt[i][R] = number of tails (k_i..k_{D-1}) with sum of lmin <= R (R = 0..L)
+    std::vector<int64_t> cnt((size_t)(D + 1) * (L + 1), 0);
+    for (int R = 0; R <= L; R++) cnt[(size_t)D * (L + 1) + R] = 1;
+    for (int i = D - 1; i >= 0; i--)
+        for (int R = 0; R <= L; R++) {
+            int64_t c = 0;
+            for (int k = 0; k < kw; k++) {
+                int lm = T.lmin_tab[(size_t)i * kw + k];
+                if (lm <= R) c += cnt[(size_t)(i + 1) * (L + 1) + (R - lm)];
+            }
+            cnt[(size_t)i * (L + 1) + R] = c;
+        }
+    T.n_cs = cnt[L];
+    if (T.n_cs >= ((int64_t)1 << 31) - 1) return "N_cs >= 2^31 is outside this build's limits";
+    // rank(k) = sum_i T_i[s_i][k_i], s_i = sum_{j<i} lmin_j(k_j),
+    // T_i[s][k] = sum_{v<k} cnt[i+1][L - s - lmin_i(v)]  (tails that precede k_i = k)
+    T.rank_tab.assign((size_t)D * (L + 1) * kw, 0);
+    for (int i = 0; i < D; i++)
+        for (int s = 0; s <= L; s++) {
+            int64_t acc = 0;
+            for (int k = 0; k < kw; k++) {
+                T.rank_tab[((size_t)i * (L + 1) + s) * kw + k] = (int)acc;
+                int lm = T.lmin_tab[(size_t)i * kw + k];
+                int R = L - s - lm;
+                if (lm <= L && R >= 0) acc += cnt[(size_t)(i + 1) * (L + 1) + R];
+            }
+        }
+
+    // ---------------- terms in Table-2 order (l_0 fastest) ----------------
+    T.Dpad = (D + 3) / 4 * 4;
+    T.levels.clear();
+    T.coefs.clear();
+    std::vector<int> l(D, 0);
+    // depth-first over modes D-1 (slowest) .. 0 (fastest), remaining budget `rem`
+    std::vector<int> stack;
+    struct Rec {
+        static void run(int i, int rem, int sum, int D, int L, std::vector<int> &l, HostTables &T)
+        {
+            if (i < 0) {
+                if (sum >= L - D + 1) {
+                    for (int j = 0; j < T.Dpad; j++) T.levels.push_back(j < D ? (uint8_t)l[j] : 0);
+                    int r = L - sum;
+                    int64_t c = binom(D - 1, r);
+                    T.coefs.push_back((int)((r % 2) ? -c : c));
+                }
+                return;
+            }
+            for (int v = 0; v <= rem; v++) {
+                l[i] = v;
+                run(i - 1, rem - v, sum + v, D, L, l, T);
+            }
+            l[i] = 0;
+        }
+    };
+    Rec::run(D - 1, L, 0, D, L, l, T);
+    T.n_terms = (int64_t)T.coefs.size();
+    if (T.n_terms >= ((int64_t)1 << 31)) return "too many terms";
+
+    // ---------------- per-term sizes, capacities, work ----------------
+    // Pair-table bound: distinct mode pairs that share a monomial.
+    std::vector<char> pair_seen((size_t)D * D, 0);
+    int64_t pair_entries = 0;
+    for (int m = 0; m < (int)p.mnfac.size(); m++)
+        for (int f = p.mfoff[m]; f < p.mfoff[m + 1]; f++)
+            for (int g = f + 1; g < p.mfoff[m + 1]; g++) {
+                int a = std::min(p.mfmode[f], p.mfmode[g]), b = std::max(p.mfmode[f], p.mfmode[g]);
+                if (a == b || pair_seen[(size_t)a * D + b]) continue;
+                pair_seen[(size_t)a * D + b] = 1;
+                int nqa = 0, nqb = 0;
+                for (int lv = 0; lv <= L; lv++) {
+                    nqa = std::max(nqa, T.lvl[(size_t)a * (L + 1) + lv].nq);
+                    nqb = std::max(nqb, T.lvl[(size_t)b * (L + 1) + lv].nq);
+                }
+                pair_entries += (int64_t)nqa * nqb;
+            }
+
+    std::vector<int64_t> cost(T.n_terms);
+    T.maxnb = 1;
+    T.matcap = 1;
+    int fsum_max = 1, stage_min_max = 1;
+    T.n_s = 0;
+    T.n_grid = 0;
+    T.flops_per_vec = 0;
+    for (int64_t t = 0; t < T.n_terms; t++) {
+        const uint8_t *lt = &T.levels[(size_t)t * T.Dpad];
+        int nb[kMaxD], nq[kMaxD], m = 0;
+        int64_t NB = 1, NG = 1, NGfull = 1;
+        int mats = 0, fsum = 0;
+        for (int i = 0; i < D; i++) {
+            const LevelInfo &li = T.lvl[(size_t)i * (L + 1) + lt[i]];
+            NGfull *= li.nq;
+            if (li.nb > 1) {
+                nb[m] = li.nb; nq[m] = li.nq; m++;
+                NB *= li.nb; NG *= li.nq;
+                mats += 2 * li.nb * li.nq + li.nb * li.nb + li.nq;
+                fsum += li.nq;
+            }
+        }
+        T.n_s += NB;
+        T.n_grid += NGfull;
+        T.maxnb = (int)std::max<int64_t>(T.maxnb, NB);
+        T.matcap = std::max(T.matcap, mats);
+        fsum_max = std::max(fsum_max, fsum);
+        if (m > 0) stage_min_max = std::max(stage_min_max, nb[m - 1]);
+        // FMA count of the collapsed route: forward and backward chains + kinetic
+        int64_t fma = 0;
+        for (int tt = 0; tt < m; tt++) {
+            int64_t sz = (int64_t)nb[tt] * nq[tt];
+            for (int j = 0; j < tt; j++) sz *= nq[j];
+            for (int j = tt + 1; j < m; j++) sz *= nb[j];
+            fma += 2 * sz;
+        }
+        for (int j = 0; j < m; j++) fma += NB * nb[j];
+        T.flops_per_vec += 2 * fma + NG + 2 * NB;
+        cost[t] = 2 * fma + 8 * NG + 16 * NB + 256;
+    }
+    T.vtabcap = fsum_max + (int)std::min<int64_t>(pair_entries, 1 << 24);
+
+    // Shared memory: fixed part + two grid buffers of `cap` elements.
+    const int nm = std::max(1, (int)p.mnfac.size());
+    size_t fixed = (size_t)rb * (T.matcap + T.vtabcap + 4 * (size_t)T.maxnb) + 4 * (size_t)T.maxnb +
+                   (size_t)nm * (16 + 24 + 16 + 16) + 1024;
+    if (fixed + 2 * (size_t)rb * stage_min_max > (size_t)smem_budget) {
+        snprintf(buf, sizeof buf, "a term needs %zu bytes of shared memory (budget %d)",
+                 fixed + 2 * (size_t)rb * stage_min_max, smem_budget);
+        return buf;
+    }
+    T.cap = (int)(((size_t)smem_budget - fixed) / (2 * (size_t)rb));
+    T.cap = std::max(T.cap, stage_min_max);
+
+    // processing order: most expensive terms first (longest-processing-time first)
+    T.order.resize(T.n_terms);
+    std::iota(T.order.begin(), T.order.end(), 0);
+    std::stable_sort(T.order.begin(), T.order.end(),
+                     [&](int a, int b) { return cost[a] > cost[b]; });
+    return "";
+}
+
+}  // namespace sg
