@@ -47,6 +47,34 @@ void free_all(sg_ctx *ctx)
     if (ctx->stage_x) cudaFree(ctx->stage_x);
     if (ctx->stage_y) cudaFree(ctx->stage_y);
     ctx->stage_x = ctx->stage_y = nullptr;
+    if (ctx->acc) cudaFree(ctx->acc);
+    if (ctx->maxbits) cudaFree(ctx->maxbits);
+    ctx->acc = nullptr;
+    ctx->maxbits = nullptr;
+    ctx->acc_nvec = 0;
+}
+
+// Apply workspace for nvec vectors: fixed-point accumulators (zeroed here and
+// left zeroed by every apply) and the per-vector max|x| words.
+sg_status ensure_workspace(sg_ctx *ctx, int nvec, cudaStream_t s)
+{
+    if (nvec <= ctx->acc_nvec) return SG_OK;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+    if (ctx->acc) cudaFree(ctx->acc);
+    if (ctx->maxbits) cudaFree(ctx->maxbits);
+    ctx->acc = nullptr;
+    ctx->maxbits = nullptr;
+    ctx->acc_nvec = 0;
+    const size_t words = (size_t)ctx->host.n_cs * nvec * sg::kAccDigits;
+    if ((e = cudaMalloc(&ctx->acc, words * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->maxbits, sizeof(long long) * nvec)) != cudaSuccess)
+        return fail(ctx, SG_ENOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+    if ((e = cudaMemsetAsync(ctx->acc, 0, words * sizeof(unsigned long long), s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "workspace memset");
+    ctx->acc_nvec = nvec;
+    ctx->kp.acc = ctx->acc;
+    return SG_OK;
 }
 
 // Device shared-memory opt-in limit of sm_100-class GPUs, used to size plans
@@ -164,6 +192,8 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
         (st = upload(ctx, p.mfoff, &kp.mfoff)) != SG_OK ||
         (st = upload(ctx, p.mfmode, &kp.mfmode)) != SG_OK ||
         (st = upload(ctx, p.mfpow, &kp.mfpow)) != SG_OK ||
+        (st = upload(ctx, T.harm_mono, &kp.harm_mono)) != SG_OK ||
+        (st = upload(ctx, T.esplit, &kp.esplit)) != SG_OK ||
         (st = upload(ctx, zero, &errp)) != SG_OK) {
         g_create_error = ctx->last_error;
         free_all(ctx);
@@ -204,7 +234,10 @@ sg_status sg_apply_H(sg_ctx *ctx, const double *x, double *y, int nvec, void *st
     if (nvec < 1) return fail(ctx, SG_EINVAL, "nvec must be >= 1");
     const size_t n = (size_t)ctx->host.n_cs * nvec;
     if ((x < y + n) && (y < x + n)) return fail(ctx, SG_EINVAL, "x and y overlap");
-    cudaError_t e = sg::launch_apply(ctx->kp, ctx->fp32, x, y, nvec, (cudaStream_t)stream);
+    sg_status st = ensure_workspace(ctx, nvec, (cudaStream_t)stream);
+    if (st != SG_OK) return st;
+    cudaError_t e = sg::launch_apply(ctx->kp, ctx->fp32, x, y, nvec, ctx->maxbits, nullptr,
+                                     (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "apply launch");
     return SG_OK;
 }
@@ -230,7 +263,10 @@ sg_status sg_apply_H_host(sg_ctx *ctx, const double *x_host, double *y_host, int
     }
     if ((e = cudaMemcpyAsync(ctx->stage_x, x_host, n * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "H2D copy");
-    if ((e = sg::launch_apply(ctx->kp, ctx->fp32, ctx->stage_x, ctx->stage_y, nvec, s)) != cudaSuccess)
+    sg_status st = ensure_workspace(ctx, nvec, s);
+    if (st != SG_OK) return st;
+    if ((e = sg::launch_apply(ctx->kp, ctx->fp32, ctx->stage_x, ctx->stage_y, nvec, ctx->maxbits,
+                              nullptr, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "apply launch");
     if ((e = cudaMemcpyAsync(y_host, ctx->stage_y, n * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "D2H copy");

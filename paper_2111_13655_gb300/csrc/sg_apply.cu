@@ -5,11 +5,20 @@
 //   1. extract the term from the compact vector (mapping table M^B, Table 2),
 //      the compact index computed combinatorially;
 //   2. basis -> grid, one mode at a time (Eq. (15));
-//   3. the operator on the grid: the potential multiplied point-wise; the
-//      kinetic part applied as per-mode matrices K_j = -omega_j/2 B_j^T W_j D2_j
-//      (equal to applying b'' on the grid because B_i^T W_i B_i = I for nq >= nb);
+//   3. the operator on the grid: the potential multiplied point-wise;
 //   4. grid -> basis (Eq. (14));
-//   5. compress-add D_l * result into the compact output (Eq. (16)), FP64 atomics.
+//   5. compress-add D_l * result into the compact output (Eq. (16)).
+// Operators that act on a single mode -- the kinetic part and every monomial
+// of the potential that involves one transformed mode -- are applied as
+// nb x nb matrices H1_j = K_j + sum_m c_m B_j^T W_j diag(Q^p) B_j in the basis:
+// because B_i^T W_i B_i = I for every other mode (nq >= nb), this equals
+// taking them through the grid.  The grid carries the monomials that couple
+// two or more transformed modes.  The harmonic part of a mode (when the
+// potential holds the quadratic that matches its basis) is diagonal in every
+// term and is added once in the compact basis by the finalize kernel.
+// The compress-add is exact: each D_l * y_l[k] is converted to an integer
+// multiple of 2^E and summed in four 32-bit digits held in int64 words, so the
+// result does not depend on the order in which terms finish.
 // Modes whose level holds a single basis function (nb = 1) are not expanded:
 // their quadrature sum is folded exactly into the potential through the
 // moments mu_p = sum_u w_u b_0(Q_u)^2 Q_u^p (the term tensor is rank one along
@@ -17,6 +26,7 @@
 // Terms whose grid does not fit in shared memory are processed in slices over
 // their first `s` slots (depth-first over the slice index, breadth-first
 // inside), which leaves the arithmetic of every slot unchanged.
+#include <algorithm>
 #include <cstdint>
 
 #include "sg_internal.h"
@@ -32,14 +42,16 @@ struct MonoG { int m, pad; double cf; };
 
 struct TermHdr {
     int m, NB, s, NBO, NBI, nslice, nfib, bad;
-    int n1, npair, n2, ng, fsum;
+    int n1, npair, n2, ng, grid;
     int mode[kMaxD], lev[kMaxD], nb[kMaxD], nq[kMaxD];
-    int oB[kMaxD], oBW[kMaxD], oK[kMaxD], oF[kMaxD];  // shared-memory offsets per slot
+    int oB[kMaxD], oBW[kMaxD], oK[kMaxD];              // shared-memory offsets per slot
+    int gM[kMaxD], gK[kMaxD];                          // global offsets of M_p and K per slot
     int gQ[kMaxD];                                     // global offset of Q_u per slot
     int stride[kMaxD];                                 // basis-tensor strides (last slot fastest)
     int slot_of_mode[kMaxD];
     int uS[kMaxD];                                     // grid indices of the current slice
-    double coef, C0, Kc;
+    double c0;                                         // constant of the term (collapsed modes)
+    int coef;                                          // D_l
 };
 
 __device__ __forceinline__ void set_err(const KParams &P, int code)
@@ -47,13 +59,13 @@ __device__ __forceinline__ void set_err(const KParams &P, int code)
     if (P.err) atomicCAS(P.err, 0, code);
 }
 
-// Serial per-term set-up (thread 0): slots, split, shared-memory offsets and
-// the potential folded over the nb = 1 modes, grouped by the slots it touches.
+// Serial per-term set-up (thread 0): slots, split, shared-memory offsets, and
+// the potential folded over the nb = 1 modes and grouped by the slots it touches.
 __device__ void decode_term(const KParams &P, int t, TermHdr &H, Mono1 *m1, Mono2 *m2, PairT *pr,
                             MonoG *mg)
 {
     const uint8_t *lt = P.levels + (size_t)t * P.Dpad;
-    H.m = 0; H.NB = 1; H.bad = 0; H.Kc = 0.0;
+    H.m = 0; H.NB = 1; H.bad = 0; H.c0 = 0.0;
     int mat = 0;
     for (int i = 0; i < P.D; i++) {
         const LevelInfo li = P.lvl[i * (P.L + 1) + lt[i]];
@@ -64,41 +76,23 @@ __device__ void decode_term(const KParams &P, int t, TermHdr &H, Mono1 *m1, Mono
             H.oB[j] = mat;  mat += li.nq * li.nb;
             H.oBW[j] = mat; mat += li.nb * li.nq;
             H.oK[j] = mat;  mat += li.nb * li.nb;
-            H.gQ[j] = li.offQ;
+            H.gQ[j] = li.offQ; H.gM[j] = li.offM; H.gK[j] = P.harm_mono[i] >= 0 ? -1 : li.offK;
             H.NB *= li.nb;
         } else {
             H.slot_of_mode[i] = -1;
-            H.Kc += P.tabd[li.offK];  // 1x1 kinetic matrix of a collapsed mode
+            if (P.harm_mono[i] < 0) H.c0 += P.tabd[li.offK];  // 1x1 kinetic of a collapsed mode
         }
     }
     if (mat > P.matcap || H.NB > P.maxnb) { H.bad = 1; return; }
     int st = 1;
     for (int j = H.m - 1; j >= 0; j--) { H.stride[j] = st; st *= H.nb[j]; }
-    // split: smallest s whose inner working set fits a grid buffer
-    H.s = 0;
-    if (H.m > 0) {
-        for (int s = 0; s < H.m; s++) {
-            int64_t stage = H.nb[H.m - 1];
-            for (int j = s; j <= H.m - 2; j++) stage *= H.nq[j];
-            H.s = s;
-            if (stage <= P.cap) break;
-        }
-        int64_t stage = H.nb[H.m - 1];
-        for (int j = H.s; j <= H.m - 2; j++) stage *= H.nq[j];
-        if (stage > P.cap) { H.bad = 2; return; }
-    }
-    H.NBO = 1; H.nslice = 1;
-    for (int j = 0; j < H.s; j++) { H.NBO *= H.nb[j]; H.nslice *= H.nq[j]; }
-    H.NBI = H.NB / H.NBO;
-    H.nfib = 1;
-    for (int j = H.s; j <= H.m - 2; j++) H.nfib *= H.nq[j];
-    int f = 0;
-    for (int j = 0; j < H.m; j++) { H.oF[j] = f; f += H.nq[j]; }
-    H.fsum = f;
     // potential: fold collapsed modes through their moments, group by slots
-    H.C0 = 0.0; H.n1 = H.npair = H.n2 = H.ng = 0;
-    int voff = f;
+    H.n1 = H.npair = H.n2 = H.ng = 0;
+    int voff = 0;
     for (int mm = 0; mm < P.nmono; mm++) {
+        bool split = false;
+        for (int i = 0; i < P.D && !split; i++) split = (P.harm_mono[i] == mm);
+        if (split) continue;  // harmonic part: added in the compact basis
         int fmode[kMaxFac], fpow[kMaxFac], nf = 0;
         for (int q = P.mfoff[mm]; q < P.mfoff[mm + 1]; q++) {
             int md = P.mfmode[q], pw = P.mfpow[q], k = 0;
@@ -115,7 +109,7 @@ __device__ void decode_term(const KParams &P, int t, TermHdr &H, Mono1 *m1, Mono
             } else { zs[nz] = sl; zp[nz] = fpow[k]; nz++; }
         }
         if (nz == 0) {
-            H.C0 += cf;
+            H.c0 += cf;
         } else if (nz == 1) {
             m1[H.n1++] = Mono1{zs[0], zp[0], cf};
         } else if (nz == 2) {
@@ -134,8 +128,83 @@ __device__ void decode_term(const KParams &P, int t, TermHdr &H, Mono1 *m1, Mono
             mg[H.ng++] = MonoG{mm, 0, cf};
         }
     }
-    if (f > P.vtabcap) { H.bad = 3; return; }
-    H.coef = (double)P.coefs[t];
+    H.grid = (H.m > 0) && (H.npair + H.ng > 0);
+    // split: smallest s whose inner working set fits a grid buffer
+    H.s = 0;
+    if (H.grid) {
+        for (int s = 0; s < H.m; s++) {
+            int64_t stage = H.nb[H.m - 1];
+            for (int j = s; j <= H.m - 2; j++) stage *= H.nq[j];
+            H.s = s;
+            if (stage <= P.cap) break;
+        }
+        int64_t stage = H.nb[H.m - 1];
+        for (int j = H.s; j <= H.m - 2; j++) stage *= H.nq[j];
+        if (stage > P.cap) { H.bad = 2; return; }
+    }
+    H.NBO = 1; H.nslice = 1;
+    for (int j = 0; j < H.s; j++) { H.NBO *= H.nb[j]; H.nslice *= H.nq[j]; }
+    H.NBI = H.NB / H.NBO;
+    H.nfib = 1;
+    for (int j = H.s; j <= H.m - 2; j++) H.nfib *= H.nq[j];
+    H.coef = P.coefs[t];
+}
+
+// Adds coef * r (r = +-mant * 2^e2) to the fixed-point accumulator acc[0..3]
+// in units of 2^E.  Integer arithmetic only: the result is exact up to the
+// rounding of values below 2^E, and independent of the order of additions.
+__device__ __forceinline__ void fx_add(unsigned long long *acc, unsigned long long mant, int e2, bool neg,
+                                       int coef, int E, int *err)
+{
+    if (mant == 0 || coef == 0) return;
+    if (coef < 0) { neg = !neg; coef = -coef; }
+    const unsigned __int128 Pm = (unsigned __int128)mant * (unsigned)coef;  // < 2^85, exact
+    const int sh = e2 - E;
+    unsigned __int128 F;
+    if (sh >= 0) {
+        if (sh > 126 || (Pm >> (126 - sh)) != 0) {  // would leave the 127-bit range
+            if (err) atomicCAS(err, 0, 200);
+            return;
+        }
+        F = Pm << sh;
+    } else {
+        const int rs = -sh;
+        if (rs >= 127) return;                        // below 2^E: rounds to zero
+        F = (Pm + ((unsigned __int128)1 << (rs - 1))) >> rs;
+    }
+#pragma unroll
+    for (int i = 0; i < kAccDigits; i++) {
+        const unsigned long long d = (unsigned long long)(F >> (32 * i)) & 0xFFFFFFFFull;
+        if (d) atomicAdd(acc + i, neg ? (unsigned long long)(-(long long)d) : d);
+    }
+}
+
+__device__ __forceinline__ void fx_add_real(unsigned long long *acc, double r, int coef, int E, int *err)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(r);
+    int ex = (int)((bits >> 52) & 0x7FF);
+    unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
+    if (ex == 0x7FF) { if (err) atomicCAS(err, 0, 201); return; }
+    if (ex == 0) ex = 1; else mant |= 1ull << 52;
+    fx_add(acc, mant, ex - 1075, (bits >> 63) != 0, coef, E, err);
+}
+
+__device__ __forceinline__ void fx_add_real(unsigned long long *acc, float r, int coef, int E, int *err)
+{
+    const unsigned bits = (unsigned)__float_as_uint(r);
+    int ex = (int)((bits >> 23) & 0xFF);
+    unsigned long long mant = bits & 0x7FFFFFu;
+    if (ex == 0xFF) { if (err) atomicCAS(err, 0, 201); return; }
+    if (ex == 0) ex = 1; else mant |= 1ull << 23;
+    fx_add(acc, mant, ex - 150, (bits >> 31) != 0, coef, E, err);
+}
+
+// E (the exponent of the accumulators' unit) of vector v from max|x_v|
+__device__ __forceinline__ int lsb_exponent(long long maxbits)
+{
+    const int ex = (int)((maxbits >> 52) & 0x7FF);
+    if (maxbits == 0) return -1000;
+    return (ex - 1022) - kAccLsbBelowMax;  // max|x| < 2^(ex-1022)
 }
 
 // compact index of the basis function with per-slot indices k[0..m-1]
@@ -182,7 +251,7 @@ template <> struct Tab<float> { static __device__ const float *get(const KParams
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_apply(const KParams P, const double *__restrict__ x,
-                                                    double *__restrict__ y, int nvec)
+                                                    const long long *__restrict__ maxbits, int nvec)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ TermHdr H;
@@ -212,27 +281,23 @@ __global__ void __launch_bounds__(kThreads) k_apply(const KParams P, const doubl
     const T *tab = Tab<T>::get(P);
     const int m = H.m;
 
-    // per-slot 1D matrices into shared memory
+    // per-slot 1D matrices: B and B^T W (grid part), H1 = K + sum_m c_m M_p (basis part)
     for (int j = 0; j < m; j++) {
         const LevelInfo li = P.lvl[H.mode[j] * (P.L + 1) + H.lev[j]];
-        const int nbq = li.nb * li.nq;
-        for (int e = tid; e < nbq; e += kThreads) {
-            mats[H.oB[j] + e] = tab[li.offB + e];
-            mats[H.oBW[j] + e] = tab[li.offBW + e];
+        const int nbq = li.nb * li.nq, nb2 = li.nb * li.nb;
+        if (H.grid)
+            for (int e = tid; e < nbq; e += kThreads) {
+                mats[H.oB[j] + e] = tab[li.offB + e];
+                mats[H.oBW[j] + e] = tab[li.offBW + e];
+            }
+        for (int e = tid; e < nb2; e += kThreads) {
+            double h = H.gK[j] >= 0 ? P.tabd[H.gK[j] + e] : 0.0;
+            for (int a = 0; a < H.n1; a++)
+                if (m1[a].slot == j) h += m1[a].cf * P.tabd[H.gM[j] + (m1[a].pow - 1) * nb2 + e];
+            mats[H.oK[j] + e] = (T)h;
         }
-        for (int e = tid; e < li.nb * li.nb; e += kThreads) mats[H.oK[j] + e] = tab[li.offK + e];
     }
-    // potential tables: f_j[u] for one-slot monomials, g_p[ua][ub] for two-slot ones
-    for (int e = tid; e < H.fsum; e += kThreads) {
-        int j = 0;
-        while (j + 1 < m && e >= H.oF[j + 1]) j++;
-        const int u = e - H.oF[j];
-        const double q = P.tabd[H.gQ[j] + u];
-        double v = 0.0;
-        for (int a = 0; a < H.n1; a++)
-            if (m1[a].slot == j) v += m1[a].cf * ipow(q, m1[a].pow);
-        vtab[e] = (T)v;
-    }
+    // potential tables g_p[ua][ub] of the monomials coupling two slots
     for (int p = 0; p < H.npair; p++) {
         const int a = pr[p].a, b = pr[p].b, nqb = H.nq[b];
         for (int e = tid; e < H.nq[a] * nqb; e += kThreads) {
@@ -254,10 +319,11 @@ __global__ void __launch_bounds__(kThreads) k_apply(const KParams P, const doubl
 
     for (int v = 0; v < nvec; v++) {
         const double *xv = x + (size_t)v * P.n_cs;
-        double *yv = y + (size_t)v * P.n_cs;
+        unsigned long long *accv = P.acc + (size_t)v * P.n_cs * kAccDigits;
+        const int E = lsb_exponent(maxbits[v]);
         for (int e = tid; e < H.NB; e += kThreads) { X[e] = (T)__ldg(xv + rk[e]); Y[e] = T(0); }
         __syncthreads();
-        if (m > 0) {
+        if (H.grid) {
             const int s = H.s, mL = m - 1, nbL = H.nb[mL], nqL = H.nq[mL];
             for (int sl = 0; sl < H.nslice; sl++) {
                 if (tid == 0) {
@@ -295,7 +361,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(const KParams P, const doubl
                     T *tp = cur; cur = oth; oth = tp;
                     __syncthreads();
                 }
-                // last slot: basis -> grid, potential, grid -> basis, one fibre per thread
+                // last slot: basis -> grid, coupling potential, grid -> basis, one fibre per thread
                 const T *BL = mats + H.oB[mL];
                 const T *BWL = mats + H.oBW[mL];
                 for (int fb = tid; fb < H.nfib; fb += kThreads) {
@@ -303,8 +369,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(const KParams P, const doubl
                     for (int j = 0; j < s; j++) u[j] = H.uS[j];
                     int rem = fb;
                     for (int j = mL - 1; j >= s; j--) { u[j] = rem % H.nq[j]; rem /= H.nq[j]; }
-                    T vpre = (T)H.C0;
-                    for (int j = 0; j < mL; j++) vpre += vtab[H.oF[j] + u[j]];
+                    T vpre = T(0);
                     for (int p = 0; p < H.npair; p++)
                         if (pr[p].b != mL) vpre += vtab[pr[p].off + u[pr[p].a] * H.nq[pr[p].b] + u[pr[p].b]];
                     T gin[kMaxLevelSize], acc[kMaxLevelSize];
@@ -312,7 +377,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(const KParams P, const doubl
                     for (int uL = 0; uL < nqL; uL++) {
                         T g = T(0);
                         for (int k = 0; k < nbL; k++) g += BL[uL * nbL + k] * gin[k];
-                        T V = vpre + vtab[H.oF[mL] + uL];
+                        T V = vpre;
                         for (int p = 0; p < H.npair; p++)
                             if (pr[p].b == mL) V += vtab[pr[p].off + u[pr[p].a] * nqL + uL];
                         if (H.ng) {
@@ -351,9 +416,9 @@ __global__ void __launch_bounds__(kThreads) k_apply(const KParams P, const doubl
                 __syncthreads();
             }
         }
-        // kinetic part in the basis, then compress-add with the combination coefficient
+        // single-mode matrices in the basis, then the exact compress-add with D_l
         for (int e = tid; e < H.NB; e += kThreads) {
-            T acc = (T)(H.C0 * (m == 0) + H.Kc) * X[e];
+            T acc = (T)H.c0 * X[e];
             int rem = e;
             for (int j = m - 1; j >= 0; j--) {
                 const int nbj = H.nb[j], kj = rem % nbj;
@@ -362,10 +427,52 @@ __global__ void __launch_bounds__(kThreads) k_apply(const KParams P, const doubl
                 const T *Kr = mats + H.oK[j] + kj * nbj;
                 for (int kp = 0; kp < nbj; kp++) acc += Kr[kp] * X[base + kp * H.stride[j]];
             }
-            const double val = H.coef * (double)(Y[e] + acc);
-            atomicAdd(yv + rk[e], val);
+            fx_add_real(accv + (size_t)rk[e] * kAccDigits, Y[e] + acc, H.coef, E, P.err);
         }
         __syncthreads();
+    }
+}
+
+// max |x| of each vector (as the bit pattern of a non-negative double)
+__global__ void k_maxabs(const double *__restrict__ x, int n, long long *__restrict__ maxbits)
+{
+    const int v = blockIdx.y;
+    long long mb = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const long long b = __double_as_longlong(x[(size_t)v * n + i]) & 0x7FFFFFFFFFFFFFFFll;
+        mb = b > mb ? b : mb;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long other = __shfl_xor_sync(0xffffffffu, mb, o);
+        mb = other > mb ? other : mb;
+    }
+    if ((threadIdx.x & 31) == 0 && mb) atomicMax(maxbits + v, mb);
+}
+
+// y = (accumulated integer) * 2^E + esplit * x; clears the accumulators
+__global__ void k_finalize(const KParams P, const double *__restrict__ x, double *__restrict__ y,
+                           const long long *__restrict__ maxbits, int nvec)
+{
+    const size_t total = (size_t)nvec * P.n_cs;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int v = (int)(i / P.n_cs);
+        const size_t r = i - (size_t)v * P.n_cs;
+        unsigned long long *a = P.acc + i * kAccDigits;
+        unsigned __int128 tot = 0;
+#pragma unroll
+        for (int d = 0; d < kAccDigits; d++) {
+            const __int128 dv = (__int128)(long long)a[d];
+            tot += (unsigned __int128)dv << (32 * d);
+            a[d] = 0ull;
+        }
+        const __int128 st = (__int128)tot;
+        const long long hi = (long long)(st >> 64);
+        const unsigned long long lo = (unsigned long long)tot;
+        const double val = scalbn((double)hi, 64) + (double)lo;
+        const long long mb = maxbits[v];
+        const double out = ((mb >> 52) & 0x7FF) == 0x7FF ? __longlong_as_double(0x7FF8000000000000ll)
+                                                          : scalbn(val, lsb_exponent(mb));
+        y[i] = out + P.esplit[r] * x[i];
     }
 }
 
@@ -412,17 +519,26 @@ cudaError_t configure_kernels(size_t smem, bool fp32)
 }
 
 cudaError_t launch_apply(const KParams &kp, bool fp32, const double *x, double *y, int nvec,
-                         cudaStream_t stream)
+                         long long *maxbits, int *lsb_exp, cudaStream_t stream)
 {
+    (void)lsb_exp;
     const size_t smem = apply_smem_bytes(kp, fp32);
-    cudaError_t e = cudaMemsetAsync(y, 0, sizeof(double) * (size_t)kp.n_cs * nvec, stream);
+    cudaError_t e = cudaMemsetAsync(maxbits, 0, sizeof(long long) * nvec, stream);
     if (e != cudaSuccess) return e;
-    if (kp.n_terms == 0) return cudaSuccess;
-    dim3 grid((unsigned)kp.n_terms);
-    if (fp32)
-        k_apply<float><<<grid, kThreads, smem, stream>>>(kp, x, y, nvec);
-    else
-        k_apply<double><<<grid, kThreads, smem, stream>>>(kp, x, y, nvec);
+    dim3 gmax(64, nvec);
+    k_maxabs<<<gmax, 256, 0, stream>>>(x, kp.n_cs, maxbits);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (kp.n_terms > 0) {
+        dim3 grid((unsigned)kp.n_terms);
+        if (fp32)
+            k_apply<float><<<grid, kThreads, smem, stream>>>(kp, x, maxbits, nvec);
+        else
+            k_apply<double><<<grid, kThreads, smem, stream>>>(kp, x, maxbits, nvec);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const size_t total = (size_t)nvec * kp.n_cs;
+    const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 16);
+    k_finalize<<<blocks, 256, 0, stream>>>(kp, x, y, maxbits, nvec);
     return cudaGetLastError();
 }
 

@@ -26,7 +26,14 @@ struct LevelInfo {
     int offK;   // K[k*nb+k']  = -omega/2 <b_k|d2/dQ2|b_k'> on the grid (nb x nb)
     int offQ;   // Q[u]        = Q_u                      (nq)
     int offMu;  // mu[p]       = sum_u w_u b_0(Q_u)^2 Q_u^p, p = 0..pmax (pmax+1)
+    int offM;   // M_p[k*nb+k'] = sum_u w_u b_k(Q_u) Q_u^p b_k'(Q_u), p = 1..pmax (pmax blocks nb x nb)
 };
+
+// Fixed-point accumulation of the compact result: every contribution D_l * y_l[k]
+// is added exactly as an integer multiple of 2^E (E chosen per vector from
+// max|x|), split into four signed 32-bit digits held in int64 words.
+constexpr int kAccDigits = 4;
+constexpr int kAccLsbBelowMax = 80;  // E = exponent(max|x|) - 80
 
 // Everything a kernel needs, passed by value.
 struct KParams {
@@ -47,6 +54,9 @@ struct KParams {
     const int *mfoff;        // [nmono+1]
     const int *mfmode;       // [sum nfac]
     const int *mfpow;        // [sum nfac]
+    const int *harm_mono;    // [D] monomial holding the harmonic part of mode i (-1: not split)
+    const double *esplit;    // [n_cs] sum over split modes of omega_i s_i^2 (k_i + 1/2)
+    unsigned long long *acc; // [nvec][n_cs][kAccDigits] fixed-point accumulators
     // capacities of the per-CTA shared-memory areas (elements)
     int cap;       // each of the two grid ping-pong buffers
     int maxnb;     // term basis tensor
@@ -77,6 +87,8 @@ struct HostTables {
     std::vector<uint8_t> lmin_tab;   // [D][kw]
     std::vector<LevelInfo> lvl;      // [D][L+1]
     std::vector<double> tabd;
+    std::vector<int> harm_mono;      // [D]
+    std::vector<double> esplit;      // [n_cs]
     int cap = 0, maxnb = 0, matcap = 0, vtabcap = 0;
     int64_t flops_per_vec = 0;       // FMA-counted work of one real apply (2 flops per FMA)
 };
@@ -89,7 +101,7 @@ std::string gauss_hermite(int n, std::vector<double> *x, std::vector<double> *wf
 
 // Kernel launchers (sg_apply.cu).  Return cudaSuccess or the launch error.
 cudaError_t launch_apply(const KParams &kp, bool fp32, const double *x, double *y, int nvec,
-                         cudaStream_t stream);
+                         long long *maxbits, int *lsb_exp, cudaStream_t stream);
 cudaError_t launch_index_map(const KParams &kp, int64_t t0, int64_t nt, const int64_t *offsets_dev,
                              int64_t *cs_index, cudaStream_t stream);
 size_t apply_smem_bytes(const KParams &kp, bool fp32);
@@ -109,5 +121,9 @@ struct sg_ctx {
     std::vector<void *> allocations;
     double *stage_x = nullptr, *stage_y = nullptr;  // host-API staging (device)
     int64_t stage_elems = 0;
+    // apply workspace: fixed-point accumulators and per-vector scale exponents
+    unsigned long long *acc = nullptr;
+    long long *maxbits = nullptr;
+    int acc_nvec = 0;
     std::string last_error;
 };

@@ -158,7 +158,35 @@ std::string build_tables(const Problem &p, int smem_budget, int rb, HostTables *
                 for (int u = 0; u < nq; u++) acc += W[u] * B[u * nb] * B[u * nb] * std::pow(Q[u], pw);
                 T.tabd.push_back(acc);
             }
+            // single-mode potential factors in the basis: M_p = B^T W diag(Q^p) B
+            li.offM = (int)T.tabd.size();
+            for (int pw = 1; pw <= std::max(T.pmax, 1); pw++)
+                for (int k = 0; k < nb; k++)
+                    for (int kp = 0; kp < nb; kp++) {
+                        double acc = 0.0;
+                        for (int u = 0; u < nq; u++) acc += BW[k * nq + u] * std::pow(Q[u], pw) * B[u * nb + kp];
+                        T.tabd.push_back(acc);
+                    }
         }
+    }
+    // Harmonic split.  For a mode centred at q0 = 0 with scale s, the basis
+    // functions are eigenfunctions of -omega/2 d^2/dQ^2 + omega s^4/2 Q^2 with
+    // eigenvalue omega s^2 (k+1/2), at every level and on every grid with
+    // nq >= nb.  When the potential holds exactly that quadratic monomial, the
+    // pair is diagonal in every term, and the combination identity
+    // sum_{l in R(l), l >= k} D_l = 1 adds it once: it is taken out of the
+    // term actions and applied in the compact basis.
+    T.harm_mono.assign(D, -1);
+    for (int i = 0; i < D; i++) {
+        if (p.basis[i].q0 != 0.0 || !(p.omega[i] > 0.0)) continue;
+        const double s = p.basis[i].scale;
+        const double want = 0.5 * p.omega[i] * s * s * s * s;
+        for (int m = 0; m < (int)p.mnfac.size(); m++)
+            if (p.mnfac[m] == 1 && p.mfmode[p.mfoff[m]] == i && p.mfpow[p.mfoff[m]] == 2 &&
+                std::fabs(p.mcoef[m] - want) <= 4e-16 * std::fabs(want)) {
+                T.harm_mono[i] = m;
+                break;
+            }
     }
     if (T.tabd.size() >= (size_t)1 << 30) return "tables too large";
 
@@ -202,13 +230,38 @@ std::string build_tables(const Problem &p, int smem_budget, int rb, HostTables *
             }
         }
 
+    // harmonic energies of the split modes over the compact basis, enumerated
+    // in compact order (lexicographic, mode 0 slowest) under sum lmin <= L
+    {
+        T.esplit.assign(T.n_cs, 0.0);
+        std::vector<int> k(D, 0), c(D, 0);
+        int sum = 0;
+        int64_t r = 0;
+        for (;;) {
+            double e = 0.0;
+            for (int i = 0; i < D; i++)
+                if (T.harm_mono[i] >= 0)
+                    e += p.omega[i] * p.basis[i].scale * p.basis[i].scale * (k[i] + 0.5);
+            if (r >= T.n_cs) return "compact enumeration overran N_cs";
+            T.esplit[r++] = e;
+            int i = D - 1;
+            while (i >= 0) {
+                k[i]++;
+                int lm = k[i] < kw ? T.lmin_tab[(size_t)i * kw + k[i]] : 255;
+                if (lm <= L && sum - c[i] + lm <= L) { sum += lm - c[i]; c[i] = lm; break; }
+                sum -= c[i]; c[i] = 0; k[i] = 0; i--;
+            }
+            if (i < 0) break;
+        }
+        if (r != T.n_cs) return "compact enumeration does not match N_cs";
+    }
+
     // ---------------- terms in Table-2 order (l_0 fastest) ----------------
     T.Dpad = (D + 3) / 4 * 4;
     T.levels.clear();
     T.coefs.clear();
     std::vector<int> l(D, 0);
     // depth-first over modes D-1 (slowest) .. 0 (fastest), remaining budget `rem`
-    std::vector<int> stack;
     struct Rec {
         static void run(int i, int rem, int sum, int D, int L, std::vector<int> &l, HostTables &T)
         {
@@ -268,7 +321,7 @@ std::string build_tables(const Problem &p, int smem_budget, int rb, HostTables *
             if (li.nb > 1) {
                 nb[m] = li.nb; nq[m] = li.nq; m++;
                 NB *= li.nb; NG *= li.nq;
-                mats += 2 * li.nb * li.nq + li.nb * li.nb + li.nq;
+                mats += 2 * li.nb * li.nq + li.nb * li.nb;
                 fsum += li.nq;
             }
         }
