@@ -20,10 +20,11 @@ from paper_2111_13655_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
-# FP32 contractions: each term's result carries ~1e-7 relative error, which the
-# combination coefficients amplify like FP64 rounding is amplified (see FP64
-# results); 2e-5 leaves a margin of ~10 over what C3 shows.
-MIXED_TOL = 2e-5
+# FP32 contractions: each term's result carries ~6e-8 relative error; the
+# combination coefficients (|D_l| up to 462 at D=12) amplify it in a random
+# walk over the ~200 terms sharing a compact function.  D=12 L=10 shows 5e-7;
+# 5e-6 keeps a factor 10 of margin.
+MIXED_TOL = 5e-6
 
 
 def rel_per_vector(a, b):
