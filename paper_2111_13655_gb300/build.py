@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsmolyak.so")
-SOURCES = ["sg_setup.cpp", "sg_api.cpp", "sg_apply.cu"]
+SOURCES = ["sg_setup.cpp", "sg_api.cpp", "sg_apply.cu", "sg_apply_fast.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

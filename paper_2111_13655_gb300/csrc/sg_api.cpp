@@ -176,6 +176,7 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
     HostTables &T = ctx->host;
     KParams &kp = ctx->kp;
     std::vector<float> tabf(T.tabd.begin(), T.tabd.end());
+    std::vector<float> ftabf(T.ftab.begin(), T.ftab.end());
     std::vector<int> zero(1, 0);
     sg_status st = SG_OK;
     const int *errp = nullptr;
@@ -194,7 +195,16 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
         (st = upload(ctx, p.mfpow, &kp.mfpow)) != SG_OK ||
         (st = upload(ctx, T.harm_mono, &kp.harm_mono)) != SG_OK ||
         (st = upload(ctx, T.esplit, &kp.esplit)) != SG_OK ||
-        (st = upload(ctx, zero, &errp)) != SG_OK) {
+        (st = upload(ctx, zero, &errp)) != SG_OK ||
+        (T.fast && ((st = upload(ctx, T.pair_modes, &kp.fast.pair_modes)) != SG_OK ||
+                    (st = upload(ctx, T.h1off, &kp.fast.h1off)) != SG_OK ||
+                    (st = upload(ctx, T.goff, &kp.fast.goff)) != SG_OK ||
+                    (st = upload(ctx, T.ioff, &kp.fast.ioff)) != SG_OK ||
+                    (st = upload(ctx, T.soff, &kp.fast.soff)) != SG_OK ||
+                    (st = upload(ctx, T.spoff, &kp.fast.spoff)) != SG_OK ||
+                    (st = upload(ctx, T.fsc, &kp.fast.sc)) != SG_OK ||
+                    (st = upload(ctx, T.ftab, &kp.fast.tabd)) != SG_OK ||
+                    (st = upload(ctx, ftabf, &kp.fast.tabf)) != SG_OK))) {
         g_create_error = ctx->last_error;
         free_all(ctx);
         delete ctx;
@@ -202,8 +212,19 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
     }
     kp.err = const_cast<int *>(errp);
     ctx->has_device = true;
-    ctx->smem_bytes = apply_smem_bytes(kp, ctx->fp32);
-    e = configure_kernels(ctx->smem_bytes, ctx->fp32);
+    if (T.fast) {
+        kp.fast.enabled = 1;
+        kp.fast.nb1 = T.nb1;
+        kp.fast.nq1 = T.nq1;
+        kp.fast.npairs = (int)T.pair_modes.size() / 2;
+        kp.fast.c0const = T.c0const;
+        kp.cap = T.fast_cap;
+        ctx->smem_bytes = fast_smem_bytes(kp, ctx->fp32);
+        e = configure_fast_kernels(kp, ctx->fp32);
+    } else {
+        ctx->smem_bytes = apply_smem_bytes(kp, ctx->fp32);
+        e = configure_kernels(ctx->smem_bytes, ctx->fp32);
+    }
     if (e != cudaSuccess) {
         st = cuda_fail(nullptr, e, "cudaFuncSetAttribute");
         free_all(ctx);

@@ -29,9 +29,13 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "sg_fixed.cuh"
 #include "sg_internal.h"
 
 namespace sg {
+
+using fx::fx_add_real;
+using fx::lsb_exponent;
 
 namespace {
 
@@ -148,63 +152,6 @@ __device__ void decode_term(const KParams &P, int t, TermHdr &H, Mono1 *m1, Mono
     H.nfib = 1;
     for (int j = H.s; j <= H.m - 2; j++) H.nfib *= H.nq[j];
     H.coef = P.coefs[t];
-}
-
-// Adds coef * r (r = +-mant * 2^e2) to the fixed-point accumulator acc[0..3]
-// in units of 2^E.  Integer arithmetic only: the result is exact up to the
-// rounding of values below 2^E, and independent of the order of additions.
-__device__ __forceinline__ void fx_add(unsigned long long *acc, unsigned long long mant, int e2, bool neg,
-                                       int coef, int E, int *err)
-{
-    if (mant == 0 || coef == 0) return;
-    if (coef < 0) { neg = !neg; coef = -coef; }
-    const unsigned __int128 Pm = (unsigned __int128)mant * (unsigned)coef;  // < 2^85, exact
-    const int sh = e2 - E;
-    unsigned __int128 F;
-    if (sh >= 0) {
-        if (sh > 126 || (Pm >> (126 - sh)) != 0) {  // would leave the 127-bit range
-            if (err) atomicCAS(err, 0, 200);
-            return;
-        }
-        F = Pm << sh;
-    } else {
-        const int rs = -sh;
-        if (rs >= 127) return;                        // below 2^E: rounds to zero
-        F = (Pm + ((unsigned __int128)1 << (rs - 1))) >> rs;
-    }
-#pragma unroll
-    for (int i = 0; i < kAccDigits; i++) {
-        const unsigned long long d = (unsigned long long)(F >> (32 * i)) & 0xFFFFFFFFull;
-        if (d) atomicAdd(acc + i, neg ? (unsigned long long)(-(long long)d) : d);
-    }
-}
-
-__device__ __forceinline__ void fx_add_real(unsigned long long *acc, double r, int coef, int E, int *err)
-{
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(r);
-    int ex = (int)((bits >> 52) & 0x7FF);
-    unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
-    if (ex == 0x7FF) { if (err) atomicCAS(err, 0, 201); return; }
-    if (ex == 0) ex = 1; else mant |= 1ull << 52;
-    fx_add(acc, mant, ex - 1075, (bits >> 63) != 0, coef, E, err);
-}
-
-__device__ __forceinline__ void fx_add_real(unsigned long long *acc, float r, int coef, int E, int *err)
-{
-    const unsigned bits = (unsigned)__float_as_uint(r);
-    int ex = (int)((bits >> 23) & 0xFF);
-    unsigned long long mant = bits & 0x7FFFFFu;
-    if (ex == 0xFF) { if (err) atomicCAS(err, 0, 201); return; }
-    if (ex == 0) ex = 1; else mant |= 1ull << 23;
-    fx_add(acc, mant, ex - 150, (bits >> 31) != 0, coef, E, err);
-}
-
-// E (the exponent of the accumulators' unit) of vector v from max|x_v|
-__device__ __forceinline__ int lsb_exponent(long long maxbits)
-{
-    const int ex = (int)((maxbits >> 52) & 0x7FF);
-    if (maxbits == 0) return -1000;
-    return (ex - 1022) - kAccLsbBelowMax;  // max|x| < 2^(ex-1022)
 }
 
 // compact index of the basis function with per-slot indices k[0..m-1]
@@ -528,7 +475,9 @@ cudaError_t launch_apply(const KParams &kp, bool fp32, const double *x, double *
     dim3 gmax(64, nvec);
     k_maxabs<<<gmax, 256, 0, stream>>>(x, kp.n_cs, maxbits);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (kp.n_terms > 0) {
+    if (kp.fast.enabled) {
+        if ((e = launch_apply_fast(kp, fp32, x, nvec, maxbits, stream)) != cudaSuccess) return e;
+    } else if (kp.n_terms > 0) {
         dim3 grid((unsigned)kp.n_terms);
         if (fp32)
             k_apply<float><<<grid, kThreads, smem, stream>>>(kp, x, maxbits, nvec);

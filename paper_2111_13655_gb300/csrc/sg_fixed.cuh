@@ -1,0 +1,71 @@
+// Exact fixed-point accumulation of the compact result (device code shared by
+// the kernels).  A value r is added as an integer multiple of 2^E, held in
+// kAccDigits signed 32-bit digits stored in int64 words: integer additions are
+// exact and associative, so the sum does not depend on the order of additions.
+#pragma once
+
+#include "sg_internal.h"
+
+namespace sg {
+namespace fx {
+
+// Adds coef * r (r = +-mant * 2^e2) to the fixed-point accumulator acc[0..3]
+// in units of 2^E.  Integer arithmetic only: the result is exact up to the
+// rounding of values below 2^E, and independent of the order of additions.
+static __device__ __forceinline__ void fx_add(unsigned long long *acc, unsigned long long mant, int e2, bool neg,
+                                       int coef, int E, int *err)
+{
+    if (mant == 0 || coef == 0) return;
+    if (coef < 0) { neg = !neg; coef = -coef; }
+    const unsigned __int128 Pm = (unsigned __int128)mant * (unsigned)coef;  // < 2^85, exact
+    const int sh = e2 - E;
+    unsigned __int128 F;
+    if (sh >= 0) {
+        if (sh > 126 || (Pm >> (126 - sh)) != 0) {  // would leave the 127-bit range
+            if (err) atomicCAS(err, 0, 200);
+            return;
+        }
+        F = Pm << sh;
+    } else {
+        const int rs = -sh;
+        if (rs >= 127) return;                        // below 2^E: rounds to zero
+        F = (Pm + ((unsigned __int128)1 << (rs - 1))) >> rs;
+    }
+#pragma unroll
+    for (int i = 0; i < kAccDigits; i++) {
+        const unsigned long long d = (unsigned long long)(F >> (32 * i)) & 0xFFFFFFFFull;
+        if (d) atomicAdd(acc + i, neg ? (unsigned long long)(-(long long)d) : d);
+    }
+}
+
+static __device__ __forceinline__ void fx_add_real(unsigned long long *acc, double r, int coef, int E, int *err)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(r);
+    int ex = (int)((bits >> 52) & 0x7FF);
+    unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
+    if (ex == 0x7FF) { if (err) atomicCAS(err, 0, 201); return; }
+    if (ex == 0) ex = 1; else mant |= 1ull << 52;
+    fx_add(acc, mant, ex - 1075, (bits >> 63) != 0, coef, E, err);
+}
+
+static __device__ __forceinline__ void fx_add_real(unsigned long long *acc, float r, int coef, int E, int *err)
+{
+    const unsigned bits = (unsigned)__float_as_uint(r);
+    int ex = (int)((bits >> 23) & 0xFF);
+    unsigned long long mant = bits & 0x7FFFFFu;
+    if (ex == 0xFF) { if (err) atomicCAS(err, 0, 201); return; }
+    if (ex == 0) ex = 1; else mant |= 1ull << 23;
+    fx_add(acc, mant, ex - 150, (bits >> 31) != 0, coef, E, err);
+}
+
+// E (the exponent of the accumulators' unit) of vector v from max|x_v|
+static __device__ __forceinline__ int lsb_exponent(long long maxbits)
+{
+    const int ex = (int)((maxbits >> 52) & 0x7FF);
+    if (maxbits == 0) return -1000;
+    return (ex - 1022) - kAccLsbBelowMax;  // max|x| < 2^(ex-1022)
+}
+
+
+}  // namespace fx
+}  // namespace sg

@@ -35,6 +35,28 @@ struct LevelInfo {
 constexpr int kAccDigits = 4;
 constexpr int kAccLsbBelowMax = 80;  // E = exponent(max|x|) - 80
 
+constexpr int kMaxPairs = 64;  // coupled mode pairs handled by the fast path
+
+// Fast-path tables (potentials whose monomials touch at most two modes).
+// All offsets are element offsets into FastParams::tab (T precision) or
+// ::sc (FP64 scalars); -1 marks an absent entry.
+struct FastParams {
+    int enabled;
+    int nb1, nq1;          // uniform sizes of level 1 (0 if modes differ)
+    int npairs;            // coupled mode pairs (i < i')
+    const int *pair_modes; // [npairs][2]
+    const int *h1off;      // [D][L+1]: single-mode matrix (nb x nb) of an active level
+    const int *goff;       // [npairs][L+1][L+1]: coupling table G[u_i][u_i'] (active levels)
+    const int *ioff;       // [npairs][2][L+1][L+1]: induced matrix on side s's mode at
+                           //   level l_s when the partner is collapsed at level l_o
+    const int *soff;       // [D][L+1]: scalar of a collapsed mode (into sc)
+    const int *spoff;      // [npairs][L+1][L+1]: scalar of a pair with both modes collapsed
+    const double *sc;      // scalars
+    const double *tabd;    // FP64 fast tables
+    const float *tabf;     // FP32 copies
+    double c0const;        // constant monomials
+};
+
 // Everything a kernel needs, passed by value.
 struct KParams {
     int D, L, Dpad;
@@ -57,6 +79,7 @@ struct KParams {
     const int *harm_mono;    // [D] monomial holding the harmonic part of mode i (-1: not split)
     const double *esplit;    // [n_cs] sum over split modes of omega_i s_i^2 (k_i + 1/2)
     unsigned long long *acc; // [nvec][n_cs][kAccDigits] fixed-point accumulators
+    FastParams fast;
     // capacities of the per-CTA shared-memory areas (elements)
     int cap;       // each of the two grid ping-pong buffers
     int maxnb;     // term basis tensor
@@ -89,6 +112,13 @@ struct HostTables {
     std::vector<double> tabd;
     std::vector<int> harm_mono;      // [D]
     std::vector<double> esplit;      // [n_cs]
+    // fast path
+    bool fast = false;
+    int nb1 = 0, nq1 = 0;
+    std::vector<int> pair_modes, h1off, goff, ioff, soff, spoff;
+    std::vector<double> ftab, fsc;
+    double c0const = 0.0;
+    int fast_cap = 0, fast_maxnb = 0, fast_matcap = 0;
     int cap = 0, maxnb = 0, matcap = 0, vtabcap = 0;
     int64_t flops_per_vec = 0;       // FMA-counted work of one real apply (2 flops per FMA)
 };
@@ -106,6 +136,13 @@ cudaError_t launch_index_map(const KParams &kp, int64_t t0, int64_t nt, const in
                              int64_t *cs_index, cudaStream_t stream);
 size_t apply_smem_bytes(const KParams &kp, bool fp32);
 cudaError_t configure_kernels(size_t smem_bytes, bool fp32);
+
+// Fast path (sg_apply_fast.cu)
+std::string build_fast_tables(const Problem &p, HostTables *T);
+size_t fast_smem_bytes(const KParams &kp, bool fp32);
+cudaError_t configure_fast_kernels(const KParams &kp, bool fp32);
+cudaError_t launch_apply_fast(const KParams &kp, bool fp32, const double *x, int nvec,
+                              const long long *maxbits, cudaStream_t stream);
 
 }  // namespace sg
 

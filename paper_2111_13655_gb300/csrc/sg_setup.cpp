@@ -357,11 +357,167 @@ std::string build_tables(const Problem &p, int smem_budget, int rb, HostTables *
     T.cap = (int)(((size_t)smem_budget - fixed) / (2 * (size_t)rb));
     T.cap = std::max(T.cap, stage_min_max);
 
+    // fast path (potentials with at most two-mode monomials)
+    std::string fe = build_fast_tables(p, &T);
+    if (!fe.empty()) return fe;
+    if (T.fast) {
+        const size_t fixedF = (size_t)rb * (T.matcap + 4 * (size_t)T.maxnb) + 4 * (size_t)T.maxnb + 1024;
+        if (fixedF + 2 * (size_t)rb * 64 > (size_t)smem_budget) T.fast = false;
+        else T.fast_cap = (int)(((size_t)smem_budget - fixedF) / (2 * (size_t)rb));
+    }
+
     // processing order: most expensive terms first (longest-processing-time first)
     T.order.resize(T.n_terms);
     std::iota(T.order.begin(), T.order.end(), 0);
     std::stable_sort(T.order.begin(), T.order.end(),
                      [&](int a, int b) { return cost[a] > cost[b]; });
+    return "";
+}
+
+}  // namespace sg
+
+namespace sg {
+
+// Fast-path tables.  Valid when every monomial of V touches at most two
+// distinct modes.  A term's operator then splits exactly into
+//   c0 I + sum_{slots j} H1_j + (x_j B_j^T W_j) diag(sum_{active pairs p} G_p) (x_j B_j),
+// where the single-mode matrices H1_j and the scalar c0 collect, for the
+// term's levels, the kinetic part, the one-mode monomials and the two-mode
+// monomials whose partner mode holds one basis function (folded through
+// that mode's quadrature moments), and G_p tabulates the two-mode monomials
+// on the grids of the pair's levels.  Everything here depends only on
+// (mode, level) combinations, so it is computed once.
+std::string build_fast_tables(const Problem &p, HostTables *Tp)
+{
+    HostTables &T = *Tp;
+    const int D = p.D, L = p.L, Lp = L + 1;
+    T.fast = false;
+    const int nmono = (int)p.mcoef.size();
+    // distinct modes (and summed powers) of every monomial
+    std::vector<std::vector<std::pair<int, int>>> facs(nmono);
+    for (int m = 0; m < nmono; m++) {
+        for (int f = p.mfoff[m]; f < p.mfoff[m + 1]; f++) {
+            bool found = false;
+            for (auto &pr : facs[m])
+                if (pr.first == p.mfmode[f]) { pr.second += p.mfpow[f]; found = true; }
+            if (!found) facs[m].push_back({p.mfmode[f], p.mfpow[f]});
+        }
+        if (facs[m].size() > 2) return "";  // not eligible: the generic kernel handles it
+        if (facs[m].size() == 2 && facs[m][0].first > facs[m][1].first) std::swap(facs[m][0], facs[m][1]);
+    }
+    auto split = [&](int m) {
+        for (int i = 0; i < D; i++) if (T.harm_mono[i] == m) return true;
+        return false;
+    };
+    auto LI = [&](int i, int l) -> const LevelInfo & { return T.lvl[(size_t)i * Lp + l]; };
+    const double *td = T.tabd.data();
+    auto mu = [&](int i, int l, int pw) { return td[LI(i, l).offMu + pw]; };
+    auto Mp = [&](int i, int l, int pw) { return td + LI(i, l).offM + (size_t)(pw - 1) * LI(i, l).nb * LI(i, l).nb; };
+
+    // uniform level-1 sizes (for the register block)
+    T.nb1 = T.nq1 = 0;
+    if (L >= 1) {
+        T.nb1 = LI(0, 1).nb; T.nq1 = LI(0, 1).nq;
+        for (int i = 1; i < D; i++)
+            if (LI(i, 1).nb != T.nb1 || LI(i, 1).nq != T.nq1) { T.nb1 = T.nq1 = 0; break; }
+    }
+    // coupled pairs
+    std::vector<int> pidx((size_t)D * D, -1);
+    T.pair_modes.clear();
+    for (int m = 0; m < nmono; m++)
+        if (facs[m].size() == 2) {
+            int a = facs[m][0].first, b = facs[m][1].first;
+            if (pidx[(size_t)a * D + b] < 0) {
+                pidx[(size_t)a * D + b] = (int)T.pair_modes.size() / 2;
+                T.pair_modes.push_back(a);
+                T.pair_modes.push_back(b);
+            }
+        }
+    const int np = (int)T.pair_modes.size() / 2;
+    if (np > kMaxPairs) return "";
+    T.ftab.clear();
+    T.fsc.clear();
+    T.c0const = 0.0;
+    for (int m = 0; m < nmono; m++)
+        if (facs[m].empty()) T.c0const += p.mcoef[m];
+    // single-mode matrices (active levels) and scalars (collapsed levels)
+    T.h1off.assign((size_t)D * Lp, -1);
+    T.soff.assign((size_t)D * Lp, -1);
+    for (int i = 0; i < D; i++)
+        for (int l = 0; l <= L; l++) {
+            const LevelInfo &li = LI(i, l);
+            const int nb = li.nb;
+            const bool sp = T.harm_mono[i] >= 0;
+            if (nb > 1) {
+                T.h1off[(size_t)i * Lp + l] = (int)T.ftab.size();
+                for (int e = 0; e < nb * nb; e++) {
+                    double h = sp ? 0.0 : td[li.offK + e];
+                    for (int m = 0; m < nmono; m++)
+                        if (facs[m].size() == 1 && facs[m][0].first == i && !split(m))
+                            h += p.mcoef[m] * Mp(i, l, facs[m][0].second)[e];
+                    T.ftab.push_back(h);
+                }
+            } else {
+                T.soff[(size_t)i * Lp + l] = (int)T.fsc.size();
+                double sc = sp ? 0.0 : td[li.offK];
+                for (int m = 0; m < nmono; m++)
+                    if (facs[m].size() == 1 && facs[m][0].first == i && !split(m))
+                        sc += p.mcoef[m] * mu(i, l, facs[m][0].second);
+                T.fsc.push_back(sc);
+            }
+        }
+    // pair tables, induced matrices, pair scalars
+    T.goff.assign((size_t)np * Lp * Lp, -1);
+    T.ioff.assign((size_t)np * 2 * Lp * Lp, -1);
+    T.spoff.assign((size_t)np * Lp * Lp, -1);
+    for (int P = 0; P < np; P++) {
+        const int a = T.pair_modes[2 * P], b = T.pair_modes[2 * P + 1];
+        for (int la = 0; la <= L; la++)
+            for (int lb = 0; la + lb <= L; lb++) {
+                const LevelInfo &A = LI(a, la), &B = LI(b, lb);
+                const size_t key = ((size_t)P * Lp + la) * Lp + lb;
+                if (A.nb > 1 && B.nb > 1) {
+                    T.goff[key] = (int)T.ftab.size();
+                    for (int ua = 0; ua < A.nq; ua++)
+                        for (int ub = 0; ub < B.nq; ub++) {
+                            double g = 0.0;
+                            for (int m = 0; m < nmono; m++)
+                                if (facs[m].size() == 2 && facs[m][0].first == a && facs[m][1].first == b)
+                                    g += p.mcoef[m] * std::pow(td[A.offQ + ua], facs[m][0].second) *
+                                         std::pow(td[B.offQ + ub], facs[m][1].second);
+                            T.ftab.push_back(g);
+                        }
+                } else if (A.nb > 1 || B.nb > 1) {
+                    // one side active: induced single-mode matrix on that side
+                    const int side = A.nb > 1 ? 0 : 1;
+                    const int act = side == 0 ? a : b, lact = side == 0 ? la : lb;
+                    const int col = side == 0 ? b : a, lcol = side == 0 ? lb : la;
+                    const int nb = LI(act, lact).nb;
+                    T.ioff[(((size_t)P * 2 + side) * Lp + lact) * Lp + lcol] = (int)T.ftab.size();
+                    for (int e = 0; e < nb * nb; e++) {
+                        double h = 0.0;
+                        for (int m = 0; m < nmono; m++)
+                            if (facs[m].size() == 2 && facs[m][0].first == a && facs[m][1].first == b) {
+                                const int pact = side == 0 ? facs[m][0].second : facs[m][1].second;
+                                const int pcol = side == 0 ? facs[m][1].second : facs[m][0].second;
+                                h += p.mcoef[m] * mu(col, lcol, pcol) * Mp(act, lact, pact)[e];
+                            }
+                        T.ftab.push_back(h);
+                    }
+                } else {
+                    T.spoff[key] = (int)T.fsc.size();
+                    double sc = 0.0;
+                    for (int m = 0; m < nmono; m++)
+                        if (facs[m].size() == 2 && facs[m][0].first == a && facs[m][1].first == b)
+                            sc += p.mcoef[m] * mu(a, la, facs[m][0].second) * mu(b, lb, facs[m][1].second);
+                    T.fsc.push_back(sc);
+                }
+            }
+    }
+    if (T.ftab.size() >= ((size_t)1 << 30)) return "fast tables too large";
+    if (T.fsc.empty()) T.fsc.push_back(0.0);
+    if (T.ftab.empty()) T.ftab.push_back(0.0);
+    T.fast = true;
     return "";
 }
 
