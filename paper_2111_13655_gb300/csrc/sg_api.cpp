@@ -216,6 +216,7 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
         kp.fast.enabled = 1;
         kp.fast.nb1 = T.nb1;
         kp.fast.nq1 = T.nq1;
+        kp.fast.uni1 = T.uni1;
         kp.fast.npairs = (int)T.pair_modes.size() / 2;
         kp.fast.c0const = T.c0const;
         kp.cap = T.fast_cap;

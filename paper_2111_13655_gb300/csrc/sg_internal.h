@@ -43,6 +43,7 @@ constexpr int kMaxPairs = 64;  // coupled mode pairs handled by the fast path
 struct FastParams {
     int enabled;
     int nb1, nq1;          // uniform sizes of level 1 (0 if modes differ)
+    int uni1;              // 1 if every mode has the same level-1 tables B, B^T W
     int npairs;            // coupled mode pairs (i < i')
     const int *pair_modes; // [npairs][2]
     const int *h1off;      // [D][L+1]: single-mode matrix (nb x nb) of an active level
@@ -114,7 +115,7 @@ struct HostTables {
     std::vector<double> esplit;      // [n_cs]
     // fast path
     bool fast = false;
-    int nb1 = 0, nq1 = 0;
+    int nb1 = 0, nq1 = 0, uni1 = 0;
     std::vector<int> pair_modes, h1off, goff, ioff, soff, spoff;
     std::vector<double> ftab, fsc;
     double c0const = 0.0;

@@ -361,9 +361,13 @@ std::string build_tables(const Problem &p, int smem_budget, int rb, HostTables *
     std::string fe = build_fast_tables(p, &T);
     if (!fe.empty()) return fe;
     if (T.fast) {
-        const size_t fixedF = (size_t)rb * (T.matcap + 4 * (size_t)T.maxnb) + 4 * (size_t)T.maxnb + 1024;
-        if (fixedF + 2 * (size_t)rb * 64 > (size_t)smem_budget) T.fast = false;
-        else T.fast_cap = (int)(((size_t)smem_budget - fixedF) / (2 * (size_t)rb));
+        // fast kernel: matrices, slice weights (2 maxnb) and ranks, then a work
+        // area for X, Y and two grid buffers (sized per term and vector chunk)
+        const int fbudget = std::min(smem_budget, rb == 4 ? 70 * 1024 : 106 * 1024);
+        const size_t fixedF = (size_t)rb * (T.matcap + 2 * (size_t)T.maxnb) + 4 * ((size_t)T.maxnb + 1) + 1024;
+        const size_t need = (size_t)rb * (2 * (size_t)T.maxnb + 2 * 64);
+        if (fixedF + need > (size_t)fbudget) T.fast = false;
+        else T.fast_cap = (int)(((size_t)fbudget - fixedF) / (size_t)rb);
     }
 
     // processing order: most expensive terms first (longest-processing-time first)
@@ -420,6 +424,20 @@ std::string build_fast_tables(const Problem &p, HostTables *Tp)
         T.nb1 = LI(0, 1).nb; T.nq1 = LI(0, 1).nq;
         for (int i = 1; i < D; i++)
             if (LI(i, 1).nb != T.nb1 || LI(i, 1).nq != T.nq1) { T.nb1 = T.nq1 = 0; break; }
+    }
+    // identical level-1 tables in every mode (lets the kernel keep one copy in registers)
+    T.uni1 = 0;
+    if (T.nb1 > 0) {
+        T.uni1 = 1;
+        const LevelInfo &l0 = LI(0, 1);
+        for (int i = 1; i < D && T.uni1; i++) {
+            const LevelInfo &li = LI(i, 1);
+            for (int e = 0; e < l0.nb * l0.nq; e++)
+                if (td[li.offB + e] != td[l0.offB + e] || td[li.offBW + e] != td[l0.offBW + e]) {
+                    T.uni1 = 0;
+                    break;
+                }
+        }
     }
     // coupled pairs
     std::vector<int> pidx((size_t)D * D, -1);
