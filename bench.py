@@ -247,7 +247,9 @@ def main():
             t = torch.tensor([total_ms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             total_ms = float(t.item())
-        assert sg.sg_device_error(ctx) == 0
+        derr = sg.sg_device_error(ctx)
+        if derr:
+            raise RuntimeError(f"device error code {derr} in the {prec} apply")
         lv, _ = sg.sg_term_levels(ctx)
         f_alg = algorithmic_flops_per_vector(lv) * nvec
         ms = total_ms / steps

@@ -174,24 +174,22 @@ __device__ void fast_decode(const KParams &P, int t, int nvec, int work, FHdr &H
         for (int j = R + s; j < m; j++) sz *= H.nq[j];
         return sz;
     };
-    int s1 = -1;
-    if (H.grid)
-        for (int s = 0; s <= m - R && s1 < 0; s++)
-            if (2 * (int64_t)NB + 2 * stage_of(s) <= work) s1 = s;
-    if ((H.grid && s1 < 0) || 2 * (int64_t)NB > work) { H.bad = 2; return; }
-    int vb = nvec < kMaxVB ? nvec : kMaxVB, sv = H.grid ? s1 : 0;
-    for (; vb > 1; vb--) {
-        if (!H.grid) {
-            if (2 * (int64_t)NB * vb <= work) break;
-            continue;
-        }
-        int found = -1;
-        for (int s = 0; s <= m - R && s <= s1 + 1 && found < 0; s++)
-            if ((2 * (int64_t)NB + 2 * stage_of(s)) * vb <= work) found = s;
-        if (found >= 0) { sv = found; break; }
+    // slicing depth: the smallest that leaves room for a chunk of 4 vectors (2,
+    // then 1, for very large terms).  It depends on the term only, so a
+    // vector's arithmetic does not depend on how many vectors are applied
+    // together.  The chunk is then the largest that fits at that depth.
+    int sv = 0;
+    if (H.grid) {
+        sv = -1;
+        for (int vt = 4; vt >= 1 && sv < 0; vt /= 2)
+            for (int s = 0; s <= m - R && sv < 0; s++)
+                if ((2 * (int64_t)NB + 2 * stage_of(s)) * vt <= work) sv = s;
+        if (sv < 0) { H.bad = 2; return; }
     }
-    if (vb < 1) vb = 1;
-    if (vb == 1) sv = H.grid ? s1 : 0;
+    if (2 * (int64_t)NB > work) { H.bad = 2; return; }
+    const int64_t per_vec = 2 * (int64_t)NB + (H.grid ? 2 * stage_of(sv) : 0);
+    int vb = nvec < kMaxVB ? nvec : kMaxVB;
+    while (vb > 1 && per_vec * vb > work) vb--;
     H.vb = vb; H.s = sv;
     H.NBO = 1; H.nslice = 1;
     for (int j = R; j < R + sv; j++) { H.NBO *= H.nb[j]; H.nslice *= H.nq[j]; }
@@ -278,7 +276,7 @@ __device__ __forceinline__ void rstage(const T (&in)[SZ], T (&out)[SZ], const T 
 // of the chunk, the inner slots basis -> grid, times the potential, grid ->
 // basis, in place in Z[i][v][g].
 template <typename T, int R, int NB1, int NQ1, bool UNI>
-__device__ void reg_phase(const KParams &P, const FHdr &H, const T *mats, T *Z)
+__device__ void reg_phase(const KParams &P, const FHdr &H, const T *mats, T *Z, const int vb)
 {
     constexpr int NBI = cpow(NB1, R), NGI = cpow(NQ1, R), SZ = NGI;
     constexpr int RA = R > 0 ? R : 1;
@@ -292,7 +290,7 @@ __device__ void reg_phase(const KParams &P, const FHdr &H, const T *mats, T *Z)
             Bm[b][e] = R > 0 ? mats[H.oB[b] + e] : T(0);
             BWm[b][e] = R > 0 ? mats[H.oBW[b] + e] : T(0);
         }
-    const int s0 = R + H.s, NGs = H.NGs, vb = H.vb;
+    const int s0 = R + H.s, NGs = H.NGs;
     for (int g = threadIdx.x; g < NGs; g += kFT) {
         // potential on the inner grid of this outer point, accumulated pair by pair
         T V[SZ];
@@ -521,10 +519,10 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 3 : 2)
                 if (cur == X) oth = bufA;
                 // inner slots and potential, in registers
                 switch (R) {
-                    case 0: reg_phase<T, 0, NB1, NQ1, UNI>(P, H, mats, cur); break;
-                    case 1: if constexpr (RMAX >= 1) reg_phase<T, 1, NB1, NQ1, UNI>(P, H, mats, cur); break;
-                    case 2: if constexpr (RMAX >= 2) reg_phase<T, 2, NB1, NQ1, UNI>(P, H, mats, cur); break;
-                    case 3: if constexpr (RMAX >= 3) reg_phase<T, 3, NB1, NQ1, UNI>(P, H, mats, cur); break;
+                    case 0: reg_phase<T, 0, NB1, NQ1, UNI>(P, H, mats, cur, vb); break;
+                    case 1: if constexpr (RMAX >= 1) reg_phase<T, 1, NB1, NQ1, UNI>(P, H, mats, cur, vb); break;
+                    case 2: if constexpr (RMAX >= 2) reg_phase<T, 2, NB1, NQ1, UNI>(P, H, mats, cur, vb); break;
+                    case 3: if constexpr (RMAX >= 3) reg_phase<T, 3, NB1, NQ1, UNI>(P, H, mats, cur, vb); break;
                     default: break;
                 }
                 __syncthreads();

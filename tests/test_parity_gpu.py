@@ -136,6 +136,17 @@ def test_batched_vectors_equal_single_vectors_bitwise(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_eight_vector_chunks_with_slicing_equal_single_vectors_bitwise(precision):
+    """D=12 L=8: the largest terms are sliced and processed in chunks of several
+    vectors; every vector must come out as if applied alone."""
+    p = synth.workload_C3(L=8)
+    x = synth.random_vectors(125970, 8, 12)
+    y8 = gpu_apply(p, x, precision)
+    y1 = np.stack([gpu_apply(p, x[i:i + 1], precision)[0] for i in range(8)])
+    assert np.array_equal(y8, y1)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_power_of_two_scaling_is_exact(precision):
     """H(2^k x) = 2^k H(x) bit for bit: the accumulator unit follows max|x|."""
     p = synth.workload_C2()
