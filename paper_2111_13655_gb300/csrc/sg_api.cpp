@@ -204,7 +204,9 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
                     (st = upload(ctx, T.spoff, &kp.fast.spoff)) != SG_OK ||
                     (st = upload(ctx, T.fsc, &kp.fast.sc)) != SG_OK ||
                     (st = upload(ctx, T.ftab, &kp.fast.tabd)) != SG_OK ||
-                    (st = upload(ctx, ftabf, &kp.fast.tabf)) != SG_OK))) {
+                    (st = upload(ctx, ftabf, &kp.fast.tabf)) != SG_OK ||
+                    (st = upload(ctx, T.fdesc, &kp.fast.desc)) != SG_OK ||
+                    (st = upload(ctx, T.fdesc_off, &kp.fast.desc_off)) != SG_OK))) {
         g_create_error = ctx->last_error;
         free_all(ctx);
         delete ctx;
@@ -219,9 +221,27 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
         kp.fast.uni1 = T.uni1;
         kp.fast.npairs = (int)T.pair_modes.size() / 2;
         kp.fast.c0const = T.c0const;
+        kp.fast.desccap = T.fdesccap;
+        kp.fast.gcap = T.fgcap;
         kp.cap = T.fast_cap;
-        ctx->smem_bytes = fast_smem_bytes(kp, ctx->fp32);
-        e = configure_fast_kernels(kp, ctx->fp32);
+        // M^B in the fast kernel's layout order, built on the device
+        void *rp = nullptr;
+        e = cudaMalloc(&rp, std::max<size_t>(1, (size_t)T.franks) * sizeof(int));
+        if (e != cudaSuccess) {
+            st = fail(nullptr, SG_ENOMEM, std::string("cudaMalloc (index maps): ") + cudaGetErrorString(e));
+            free_all(ctx);
+            delete ctx;
+            return st;
+        }
+        ctx->allocations.push_back(rp);
+        ctx->bytes_device += (int64_t)T.franks * (int64_t)sizeof(int);
+        kp.fast.ranks = static_cast<const int *>(rp);
+        e = launch_build_ranks(kp, static_cast<int *>(rp), 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) {
+            ctx->smem_bytes = fast_smem_bytes(kp, ctx->fp32);
+            e = configure_fast_kernels(kp, ctx->fp32);
+        }
     } else {
         ctx->smem_bytes = apply_smem_bytes(kp, ctx->fp32);
         e = configure_kernels(ctx->smem_bytes, ctx->fp32);

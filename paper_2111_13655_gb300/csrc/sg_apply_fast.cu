@@ -45,7 +45,11 @@ struct FHdr {
     int bymode[kMaxD];                                   // positions sorted by mode
     int pos_of_mode[kMaxD], lev_of_mode[kMaxD];
     int npair, nind;
-    int pa[kMaxPairs], pb[kMaxPairs], pg[kMaxPairs];     // active pairs: positions, G offset
+    int pa[kMaxPairs], pb[kMaxPairs], pg[kMaxPairs];     // active pairs: positions, G offset (shared)
+    int pgg[kMaxPairs];                                  // G offset in the global fast tables
+    int gB[kMaxD], gBW[kMaxD], gH1[kMaxD];               // global offsets of B, B^T W, H1 base
+    long long rank_off;
+    int gsize;
     int ipos[kMaxPairs], ioffs[kMaxPairs];               // induced matrices: position, offset
     int uS[kMaxD];                                       // slice indices of the sliced positions
 };
@@ -76,127 +80,101 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// Per-term set-up by warp 0: lane i looks at mode i, lane p at coupled pair p.
-template <int NB1, int NQ1, int RMAX>
-__device__ void fast_decode(const KParams &P, int t, int nvec, int work, FHdr &H)
+// Per-term set-up from the term's record (built on the host): warp 0 copies
+// the record to shared memory and parses it, lane 0 derives the layout.
+__device__ void load_record(const KParams &P, int p, int4 *buf, FHdr &H)
 {
-    const FastParams &F = P.fast;
-    const int Lp = P.L + 1, lane = threadIdx.x & 31;
-    const uint8_t *lt = P.levels + (size_t)t * P.Dpad;
-    int lev = 0, nb = 1, nq = 1;
-    double c0 = 0.0;
-    if (lane < P.D) {
-        lev = lt[lane];
-        const LevelInfo li = P.lvl[lane * Lp + lev];
-        nb = li.nb; nq = li.nq;
-        if (nb <= 1) c0 += F.sc[F.soff[lane * Lp + lev]];
-        H.lev_of_mode[lane] = lev;
+    const int lane = threadIdx.x & 31;
+    const unsigned lo = P.fast.desc_off[p], hi = P.fast.desc_off[p + 1];
+    for (unsigned u = lo + lane; u < hi; u += 32) buf[u - lo] = P.fast.desc[u];
+    __syncwarp();
+    const FDescHdr *hd = reinterpret_cast<const FDescHdr *>(buf);
+    const int m = hd->m, np = hd->npair, ni = hd->nind;
+    const FDescPos *ps = reinterpret_cast<const FDescPos *>(buf + 3);
+    const FDescPair *pr = reinterpret_cast<const FDescPair *>(buf + 3 + m);
+    const FDescInd *in = reinterpret_cast<const FDescInd *>(buf + 3 + m + np);
+    for (int j = lane; j < m; j += 32) {
+        H.mode[j] = ps[j].mode; H.lev[j] = ps[j].lev; H.nb[j] = ps[j].nb; H.nq[j] = ps[j].nq;
+        H.gB[j] = ps[j].offB; H.gBW[j] = ps[j].offBW; H.gH1[j] = ps[j].offH1;
     }
-    const bool active = lane < P.D && nb > 1;
-    const bool lvl1 = active && nb == NB1 && nq == NQ1;
-    const unsigned am = __ballot_sync(0xffffffffu, active);
-    unsigned l1m = __ballot_sync(0xffffffffu, lvl1);
-    unsigned im = 0;
-    for (int r = 0; r < RMAX && l1m; r++) {  // the last RMAX level-1 modes become inner
-        const int hi = 31 - __clz(l1m);
-        im |= 1u << hi;
-        l1m &= ~(1u << hi);
-    }
-    const unsigned om = am & ~im;
-    const int R = __popc(im), m = __popc(am);
-    const unsigned below = (1u << lane) - 1u;
-    int pos = -1;
-    if (active) pos = ((im >> lane) & 1u) ? __popc(im & below) : R + __popc(om & below);
-    if (lane < P.D) H.pos_of_mode[lane] = pos;
-    if (active) {
-        H.mode[pos] = lane; H.lev[pos] = lev; H.nb[pos] = nb; H.nq[pos] = nq;
-        H.bymode[__popc(am & below)] = pos;
+    for (int q = lane; q < np; q += 32) { H.pa[q] = pr[q].pa; H.pb[q] = pr[q].pb; H.pg[q] = pr[q].gsm; H.pgg[q] = pr[q].goff; }
+    for (int q = lane; q < ni; q += 32) { H.ipos[q] = in[q].pos; H.ioffs[q] = in[q].ioff; }
+    if (lane == 0) {
+        H.m = m; H.R = hd->R; H.NB = hd->NB; H.coef = hd->coef; H.s = hd->s;
+        H.npair = np; H.nind = ni; H.gsize = hd->gsize; H.c0 = hd->c0; H.rank_off = hd->rank_off;
+        H.grid = np > 0;
     }
     __syncwarp();
-    int nact = 0, nind = 0;
-    for (int p0 = 0; p0 < F.npairs; p0 += 32) {
-        const int p = p0 + lane;
-        int a = 0, b = 0, pa = -1, pb = -1;
-        if (p < F.npairs) {
-            a = F.pair_modes[2 * p]; b = F.pair_modes[2 * p + 1];
-            pa = H.pos_of_mode[a]; pb = H.pos_of_mode[b];
-        }
-        const bool isact = p < F.npairs && pa >= 0 && pb >= 0;
-        const bool isind = p < F.npairs && ((pa >= 0) != (pb >= 0));
-        const unsigned actm = __ballot_sync(0xffffffffu, isact), indm = __ballot_sync(0xffffffffu, isind);
-        if (p < F.npairs) {
-            const int la = H.lev_of_mode[a], lb = H.lev_of_mode[b];
-            const int key = (p * Lp + la) * Lp + lb;
-            if (isact) {
-                const int q = nact + __popc(actm & below);
-                H.pa[q] = pa; H.pb[q] = pb; H.pg[q] = F.goff[key];
-            } else if (isind) {
-                const int side = pa >= 0 ? 0 : 1;
-                const int lact = side == 0 ? la : lb, lcol = side == 0 ? lb : la;
-                const int q = nind + __popc(indm & below);
-                H.ipos[q] = side == 0 ? pa : pb;
-                H.ioffs[q] = F.ioff[((p * 2 + side) * Lp + lact) * Lp + lcol];
-            } else {
-                c0 += F.sc[F.spoff[key]];
-            }
-        }
-        nact += __popc(actm);
-        nind += __popc(indm);
-    }
-    c0 = warp_sum(c0);
-    __syncwarp();
-    if (lane != 0) return;
-    H.c0 = c0 + F.c0const;
-    H.coef = P.coefs[t];
-    H.m = m; H.R = R;
-    H.npair = nact; H.nind = nind;
-    H.grid = nact > 0;
+}
+
+// Layout quantities of the term (lane 0, shared memory only).
+__device__ void derive_layout(const KParams &P, int nvec, int work, FHdr &H)
+{
+    const int m = H.m, R = H.R;
     H.bad = 0;
-    int mat = 0, NB = 1, NBIn = 1;
+    int mat = 0, NBIn = 1;
     for (int j = 0; j < m; j++) {
         H.oB[j] = mat;  mat += H.nq[j] * H.nb[j];
         H.oBW[j] = mat; mat += H.nb[j] * H.nq[j];
         H.oH[j] = mat;  mat += H.nb[j] * H.nb[j];
         H.bmag[j] = rmag(H.nb[j]);
         H.qmag[j] = rmag(H.nq[j]);
-        NB *= H.nb[j];
         if (j < R) NBIn *= H.nb[j];
     }
-    if (mat > P.matcap || NB > P.maxnb) { H.bad = 1; return; }
-    H.NB = NB; H.NBIn = NBIn; H.NBo = NB / NBIn;
+    if (mat > P.matcap || H.NB > P.maxnb || H.gsize > P.fast.gcap) { H.bad = 1; return; }
+    H.NBIn = NBIn; H.NBo = H.NB / NBIn;
     int st = 1;
     for (int j = R - 1; j >= 0; j--) { H.ostride[j] = st; H.smag[j] = rmag(st); st *= H.nb[j]; }
     st = 1;
     for (int j = m - 1; j >= R; j--) { H.ostride[j] = st; H.smag[j] = rmag(st); st *= H.nb[j]; }
-    // vector chunk and slicing: X, Y (NB*vb each) + two grid buffers (stage*vb each)
-    auto stage_of = [&](int s) {
-        int64_t sz = NBIn;
-        for (int j = R + s; j < m; j++) sz *= H.nq[j];
-        return sz;
-    };
-    // slicing depth: the smallest that leaves room for a chunk of 4 vectors (2,
-    // then 1, for very large terms).  It depends on the term only, so a
-    // vector's arithmetic does not depend on how many vectors are applied
-    // together.  The chunk is then the largest that fits at that depth.
-    int sv = 0;
-    if (H.grid) {
-        sv = -1;
-        for (int vt = 4; vt >= 1 && sv < 0; vt /= 2)
-            for (int s = 0; s <= m - R && sv < 0; s++)
-                if ((2 * (int64_t)NB + 2 * stage_of(s)) * vt <= work) sv = s;
-        if (sv < 0) { H.bad = 2; return; }
+    // positions in mode order: merge of the inner and outer groups (each sorted)
+    for (int a = 0, i = 0, o = R; a < m; a++) {
+        if (o >= m || (i < R && H.mode[i] < H.mode[o])) H.bymode[a] = i++;
+        else H.bymode[a] = o++;
     }
-    if (2 * (int64_t)NB > work) { H.bad = 2; return; }
-    const int64_t per_vec = 2 * (int64_t)NB + (H.grid ? 2 * stage_of(sv) : 0);
+    const int sv = H.s;
+    int64_t stage = NBIn;
+    for (int j = R + sv; j < m; j++) stage *= H.nq[j];
+    const int64_t per_vec = 2 * (int64_t)H.NB + (H.grid ? 2 * stage : 0);
+    if (per_vec > work) { H.bad = 2; return; }
     int vb = nvec < kMaxVB ? nvec : kMaxVB;
     while (vb > 1 && per_vec * vb > work) vb--;
-    H.vb = vb; H.s = sv;
+    H.vb = vb;
     H.NBO = 1; H.nslice = 1;
     for (int j = R; j < R + sv; j++) { H.NBO *= H.nb[j]; H.nslice *= H.nq[j]; }
     H.NBrest = 1; H.NGs = 1;
     for (int j = R + sv; j < m; j++) { H.NBrest *= H.nb[j]; H.NGs *= H.nq[j]; }
     int gs = 1;
     for (int j = m - 1; j >= R + sv; j--) { H.gstride[j] = gs; H.gmag[j] = rmag(gs); gs *= H.nq[j]; }
+}
+
+// M^B in layout order: compact index of every basis function of every term
+// (built once per context; the same partial-rank arithmetic as the generic kernel).
+__global__ void __launch_bounds__(kFT) k_build_ranks(const KParams P, int *__restrict__ ranks)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ FHdr H;
+    int4 *buf = reinterpret_cast<int4 *>(smraw);
+    if (threadIdx.x < 32) {
+        load_record(P, blockIdx.x, buf, H);
+        if (threadIdx.x == 0) derive_layout(P, 1, 1 << 30, H);
+    }
+    __syncthreads();
+    const int m = H.m, R = H.R, NBo = H.NBo, Lp = P.L + 1;
+    for (int e = threadIdx.x; e < H.NB; e += kFT) {
+        const int i = e / NBo, o = e - i * NBo;
+        int r = 0, s = 0;
+        for (int a = 0; a < m; a++) {
+            const int j = H.bymode[a];
+            const int src = j < R ? i : o;
+            const int q = fdiv(src, H.ostride[j], H.smag[j]);
+            const int kj = q - fdiv(q, H.nb[j], H.bmag[j]) * H.nb[j];
+            const int md = H.mode[j];
+            r += P.rank_tab[(md * Lp + s) * P.kw + kj];
+            s += P.lmin_tab[md * P.kw + kj];
+        }
+        ranks[H.rank_off + e] = r;
+    }
 }
 
 // out[a][r][c] = sum_k M[r][k] in[a][k][c], matrix in registers, one fibre (a, c) per thread
@@ -276,12 +254,11 @@ __device__ __forceinline__ void rstage(const T (&in)[SZ], T (&out)[SZ], const T 
 // of the chunk, the inner slots basis -> grid, times the potential, grid ->
 // basis, in place in Z[i][v][g].
 template <typename T, int R, int NB1, int NQ1, bool UNI>
-__device__ void reg_phase(const KParams &P, const FHdr &H, const T *mats, T *Z, const int vb)
+__device__ void reg_phase(const FHdr &H, const T *mats, const T *G, T *Z, const int vb)
 {
     constexpr int NBI = cpow(NB1, R), NGI = cpow(NQ1, R), SZ = NGI;
     constexpr int RA = R > 0 ? R : 1;
     constexpr int NM = UNI ? 1 : RA;
-    const T *G = FTab<T>::f(P);
     T Bm[NM][NQ1 * NB1], BWm[NM][NB1 * NQ1];
 #pragma unroll
     for (int b = 0; b < NM; b++)
@@ -382,13 +359,18 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 3 : 2)
     __shared__ FHdr H;
     const int tid = threadIdx.x;
     T *mats = reinterpret_cast<T *>(smraw);
-    T *WoF = mats + P.matcap;
+    T *gtab = mats + P.matcap;
+    T *WoF = gtab + P.fast.gcap;
     T *WoB = WoF + P.maxnb;
     int *rk = reinterpret_cast<int *>(WoB + P.maxnb);
-    T *work = reinterpret_cast<T *>(rk + P.maxnb + (P.maxnb & 1));
+    T *work = reinterpret_cast<T *>(
+        reinterpret_cast<unsigned char *>(smraw) +
+        (((size_t)(P.matcap + P.fast.gcap + 2 * P.maxnb) * sizeof(T) + 4 * (size_t)P.maxnb + 15) & ~(size_t)15));
 
-    const int t = P.order[blockIdx.x];
-    if (tid < 32) fast_decode<NB1, NQ1, RMAX>(P, t, nvec, P.cap, H);
+    if (tid < 32) {
+        load_record(P, blockIdx.x, reinterpret_cast<int4 *>(work), H);
+        if (tid == 0) derive_layout(P, nvec, P.cap, H);
+    }
     __syncthreads();
     if (H.bad) {
         if (tid == 0 && P.err) atomicCAS(P.err, 0, 110 + H.bad);
@@ -397,39 +379,28 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 3 : 2)
     const T *tab = FTab<T>::t(P);
     const T *ftab = FTab<T>::f(P);
     const int m = H.m, R = H.R, NB = H.NB, NBo = H.NBo;
-    const int Lp = P.L + 1;
 
-    // per-position matrices: B, B^T W (grid part) and H1 = base + induced
+    // per-position matrices: B, B^T W (grid part) and H1 = base + induced;
+    // G tables of the active pairs; the term's compact indices
     for (int j = 0; j < m; j++) {
-        const LevelInfo li = P.lvl[H.mode[j] * Lp + H.lev[j]];
+        const int nb = H.nb[j], nq = H.nq[j];
         if (H.grid)
-            for (int e = tid; e < li.nb * li.nq; e += kFT) {
-                mats[H.oB[j] + e] = tab[li.offB + e];
-                mats[H.oBW[j] + e] = tab[li.offBW + e];
+            for (int e = tid; e < nb * nq; e += kFT) {
+                mats[H.oB[j] + e] = tab[H.gB[j] + e];
+                mats[H.oBW[j] + e] = tab[H.gBW[j] + e];
             }
-        const int h1 = P.fast.h1off[H.mode[j] * Lp + H.lev[j]];
-        for (int e = tid; e < li.nb * li.nb; e += kFT) {
-            T hv = ftab[h1 + e];
+        for (int e = tid; e < nb * nb; e += kFT) {
+            T hv = ftab[H.gH1[j] + e];
             for (int q = 0; q < H.nind; q++)
                 if (H.ipos[q] == j) hv += ftab[H.ioffs[q] + e];
             mats[H.oH[j] + e] = hv;
         }
     }
-    // compact index of element e = (i, o), rank accumulated over positions in mode order
-    for (int e = tid; e < NB; e += kFT) {
-        const int i = e / NBo, o = e - i * NBo;
-        int r = 0, s = 0;
-        for (int a = 0; a < m; a++) {
-            const int j = H.bymode[a];
-            const int src = j < R ? i : o;
-            const int q = fdiv(src, H.ostride[j], H.smag[j]);
-            const int kj = q - fdiv(q, H.nb[j], H.bmag[j]) * H.nb[j];
-            const int md = H.mode[j];
-            r += P.rank_tab[(md * Lp + s) * P.kw + kj];
-            s += P.lmin_tab[md * P.kw + kj];
-        }
-        rk[e] = r;
+    for (int p = 0; p < H.npair; p++) {
+        const int sz = H.nq[H.pa[p]] * H.nq[H.pb[p]];
+        for (int e = tid; e < sz; e += kFT) gtab[H.pg[p] + e] = ftab[H.pgg[p] + e];
     }
+    for (int e = tid; e < NB; e += kFT) rk[e] = __ldg(P.fast.ranks + H.rank_off + e);
     __syncthreads();
 
     for (int v0 = 0; v0 < nvec; v0 += H.vb) {
@@ -519,10 +490,10 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 3 : 2)
                 if (cur == X) oth = bufA;
                 // inner slots and potential, in registers
                 switch (R) {
-                    case 0: reg_phase<T, 0, NB1, NQ1, UNI>(P, H, mats, cur, vb); break;
-                    case 1: if constexpr (RMAX >= 1) reg_phase<T, 1, NB1, NQ1, UNI>(P, H, mats, cur, vb); break;
-                    case 2: if constexpr (RMAX >= 2) reg_phase<T, 2, NB1, NQ1, UNI>(P, H, mats, cur, vb); break;
-                    case 3: if constexpr (RMAX >= 3) reg_phase<T, 3, NB1, NQ1, UNI>(P, H, mats, cur, vb); break;
+                    case 0: reg_phase<T, 0, NB1, NQ1, UNI>(H, mats, gtab, cur, vb); break;
+                    case 1: if constexpr (RMAX >= 1) reg_phase<T, 1, NB1, NQ1, UNI>(H, mats, gtab, cur, vb); break;
+                    case 2: if constexpr (RMAX >= 2) reg_phase<T, 2, NB1, NQ1, UNI>(H, mats, gtab, cur, vb); break;
+                    case 3: if constexpr (RMAX >= 3) reg_phase<T, 3, NB1, NQ1, UNI>(H, mats, gtab, cur, vb); break;
                     default: break;
                 }
                 __syncthreads();
@@ -576,12 +547,12 @@ template <typename T, bool UNI>
 cudaError_t dispatch_u(const KParams &kp, const double *x, int nvec, const long long *maxbits, size_t smem,
                        cudaStream_t stream, bool configure)
 {
-    constexpr int RM = sizeof(T) == 4 ? 3 : 1;
+    // the register-slot count must be fast_rmax(...) (the host built the records with it)
+    constexpr bool F32 = sizeof(T) == 4;
     const int nb1 = kp.fast.nb1, nq1 = kp.fast.nq1;
-    if (nb1 == 2 && nq1 == 3) return launch_t<T, 2, 3, RM, UNI>(kp, x, nvec, maxbits, smem, stream, configure);
-    if (nb1 == 2 && nq1 == 2) return launch_t<T, 2, 2, RM, UNI>(kp, x, nvec, maxbits, smem, stream, configure);
-    if (nb1 == 3 && nq1 == 3)
-        return launch_t<T, 3, 3, (RM > 2 ? 2 : RM), UNI>(kp, x, nvec, maxbits, smem, stream, configure);
+    if (nb1 == 2 && nq1 == 3) return launch_t<T, 2, 3, F32 ? 3 : 1, UNI>(kp, x, nvec, maxbits, smem, stream, configure);
+    if (nb1 == 2 && nq1 == 2) return launch_t<T, 2, 2, F32 ? 3 : 1, UNI>(kp, x, nvec, maxbits, smem, stream, configure);
+    if (nb1 == 3 && nq1 == 3) return launch_t<T, 3, 3, F32 ? 2 : 1, UNI>(kp, x, nvec, maxbits, smem, stream, configure);
     return launch_t<T, 1, 1, 0, UNI>(kp, x, nvec, maxbits, smem, stream, configure);
 }
 
@@ -598,8 +569,16 @@ cudaError_t dispatch(const KParams &kp, const double *x, int nvec, const long lo
 size_t fast_smem_bytes(const KParams &kp, bool fp32)
 {
     const size_t rb = fp32 ? 4 : 8;
-    return rb * ((size_t)kp.matcap + 2 * (size_t)kp.maxnb + (size_t)kp.cap) +
-           4 * (size_t)(kp.maxnb + (kp.maxnb & 1));
+    const size_t head = ((size_t)(kp.matcap + kp.fast.gcap + 2 * kp.maxnb) * rb + 4 * (size_t)kp.maxnb + 15) & ~(size_t)15;
+    return head + rb * (size_t)kp.cap;
+}
+
+cudaError_t launch_build_ranks(const KParams &kp, int *ranks, cudaStream_t stream)
+{
+    if (kp.n_terms == 0) return cudaSuccess;
+    const size_t smem = 16 * (size_t)kp.fast.desccap;
+    k_build_ranks<<<(unsigned)kp.n_terms, kFT, smem, stream>>>(kp, ranks);
+    return cudaGetLastError();
 }
 
 cudaError_t configure_fast_kernels(const KParams &kp, bool fp32)

@@ -37,6 +37,30 @@ constexpr int kAccLsbBelowMax = 80;  // E = exponent(max|x|) - 80
 
 constexpr int kMaxPairs = 64;  // coupled mode pairs handled by the fast path
 
+// Number of level-1 slots the fast kernel keeps in registers ("inner" slots);
+// the host descriptor builder and the kernel dispatch both use this.
+inline int fast_rmax(bool fp32, int nb1, int nq1)
+{
+    if (nb1 == 2 && (nq1 == 3 || nq1 == 2)) return fp32 ? 3 : 1;
+    if (nb1 == 3 && nq1 == 3) return fp32 ? 2 : 1;
+    return 0;
+}
+
+// Per-term record of the fast kernel, in processing order, 16-byte units:
+// header | positions[m] | active pairs[npair] | induced matrices[nind] (padded).
+// Positions: the inner slots (mode order) first, then the outer slots (mode order).
+struct alignas(16) FDescHdr {
+    int m, R, NB, coef;          // positions, inner positions, basis size, D_l
+    int s, npair, nind, gsize;   // slicing depth, active pairs, induced matrices, G-table words
+    double c0;                   // constant of the term (collapsed modes)
+    long long rank_off;          // start of the term's compact indices (layout order)
+};
+struct FDescPos { unsigned char mode, lev, nb, nq; int offB, offBW, offH1; };
+struct FDescPair { unsigned char pa, pb, r0, r1; int goff, gsm, r2; };  // gsm: shared-memory offset of G
+struct FDescInd { unsigned char pos, r0, r1, r2; int ioff; };
+static_assert(sizeof(FDescHdr) == 48 && sizeof(FDescPos) == 16 && sizeof(FDescPair) == 16 &&
+              sizeof(FDescInd) == 8, "descriptor layout");
+
 // Fast-path tables (potentials whose monomials touch at most two modes).
 // All offsets are element offsets into FastParams::tab (T precision) or
 // ::sc (FP64 scalars); -1 marks an absent entry.
@@ -56,6 +80,11 @@ struct FastParams {
     const double *tabd;    // FP64 fast tables
     const float *tabf;     // FP32 copies
     double c0const;        // constant monomials
+    const int4 *desc;      // term records (processing order)
+    const unsigned *desc_off;  // [n_terms+1] record starts, in 16-byte units
+    const int *ranks;      // compact index of every basis function of every term (layout order)
+    int desccap;           // largest record, in 16-byte units
+    int gcap;              // largest set of a term's G tables, in words
 };
 
 // Everything a kernel needs, passed by value.
@@ -120,6 +149,10 @@ struct HostTables {
     std::vector<double> ftab, fsc;
     double c0const = 0.0;
     int fast_cap = 0, fast_maxnb = 0, fast_matcap = 0;
+    std::vector<int4> fdesc;          // term records
+    std::vector<unsigned> fdesc_off;  // [n_terms+1]
+    int64_t franks = 0;               // total compact indices (N_s)
+    int fdesccap = 0, fgcap = 0;
     int cap = 0, maxnb = 0, matcap = 0, vtabcap = 0;
     int64_t flops_per_vec = 0;       // FMA-counted work of one real apply (2 flops per FMA)
 };
@@ -138,8 +171,10 @@ cudaError_t launch_index_map(const KParams &kp, int64_t t0, int64_t nt, const in
 size_t apply_smem_bytes(const KParams &kp, bool fp32);
 cudaError_t configure_kernels(size_t smem_bytes, bool fp32);
 
-// Fast path (sg_apply_fast.cu)
+// Fast path (sg_apply_fast.cu, sg_setup.cpp)
 std::string build_fast_tables(const Problem &p, HostTables *T);
+std::string build_fast_descs(const Problem &p, bool fp32, HostTables *T, int fbudget, int rb);
+cudaError_t launch_build_ranks(const KParams &kp, int *ranks, cudaStream_t stream);
 size_t fast_smem_bytes(const KParams &kp, bool fp32);
 cudaError_t configure_fast_kernels(const KParams &kp, bool fp32);
 cudaError_t launch_apply_fast(const KParams &kp, bool fp32, const double *x, int nvec,

@@ -360,21 +360,20 @@ std::string build_tables(const Problem &p, int smem_budget, int rb, HostTables *
     // fast path (potentials with at most two-mode monomials)
     std::string fe = build_fast_tables(p, &T);
     if (!fe.empty()) return fe;
-    if (T.fast) {
-        // fast kernel: matrices, slice weights (2 maxnb) and ranks, then a work
-        // area for X, Y and two grid buffers (sized per term and vector chunk)
-        const int fbudget = std::min(smem_budget, rb == 4 ? 70 * 1024 : 106 * 1024);
-        const size_t fixedF = (size_t)rb * (T.matcap + 2 * (size_t)T.maxnb) + 4 * ((size_t)T.maxnb + 1) + 1024;
-        const size_t need = (size_t)rb * (2 * (size_t)T.maxnb + 2 * 64);
-        if (fixedF + need > (size_t)fbudget) T.fast = false;
-        else T.fast_cap = (int)(((size_t)fbudget - fixedF) / (size_t)rb);
-    }
 
     // processing order: most expensive terms first (longest-processing-time first)
     T.order.resize(T.n_terms);
     std::iota(T.order.begin(), T.order.end(), 0);
     std::stable_sort(T.order.begin(), T.order.end(),
                      [&](int a, int b) { return cost[a] > cost[b]; });
+
+    if (T.fast) {
+        // fast kernel: matrices, G tables, slice weights and ranks, then a work
+        // area for X, Y and two grid buffers (sized per term and vector chunk)
+        const int fbudget = std::min(smem_budget, rb == 4 ? 70 * 1024 : 106 * 1024);
+        std::string de = build_fast_descs(p, rb == 4, &T, fbudget, rb);
+        if (!de.empty()) return de;
+    }
     return "";
 }
 
@@ -536,6 +535,147 @@ std::string build_fast_tables(const Problem &p, HostTables *Tp)
     if (T.fsc.empty()) T.fsc.push_back(0.0);
     if (T.ftab.empty()) T.ftab.push_back(0.0);
     T.fast = true;
+    return "";
+}
+
+}  // namespace sg
+
+namespace sg {
+
+namespace {
+
+template <typename S>
+void put(std::vector<int4> &v, size_t unit, size_t byte, const S &x)
+{
+    std::memcpy(reinterpret_cast<char *>(v.data() + unit) + byte, &x, sizeof(S));
+}
+
+}  // namespace
+
+// Per-term records of the fast kernel (processing order).  For every term:
+// the transformed modes ("positions", the last fast_rmax level-1 modes first as
+// inner register slots, then the others, each group in mode order) with the
+// offsets of their tables, the term constant c0, the active coupled pairs with
+// the offsets of their G tables, the induced single-mode matrices, and the
+// slicing depth that lets a chunk of 4 (2, 1) vectors fit the shared-memory
+// work area.  First pass: shared memory for G tables; then the work area; then
+// the records.
+std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fbudget, int rb)
+{
+    HostTables &T = *Tp;
+    const int D = p.D, L = p.L, Lp = L + 1;
+    const int RMAX = fast_rmax(fp32, T.nb1, T.nq1);
+    const int np = (int)T.pair_modes.size() / 2;
+    auto LI = [&](int i, int l) -> const LevelInfo & { return T.lvl[(size_t)i * Lp + l]; };
+    // pass 1: G-table words per term
+    int gcap = 1;
+    for (int64_t q = 0; q < T.n_terms; q++) {
+        const uint8_t *lt = &T.levels[(size_t)T.order[q] * T.Dpad];
+        int g = 0;
+        for (int P = 0; P < np; P++) {
+            const int a = T.pair_modes[2 * P], b = T.pair_modes[2 * P + 1];
+            if (LI(a, lt[a]).nb > 1 && LI(b, lt[b]).nb > 1) g += LI(a, lt[a]).nq * LI(b, lt[b]).nq;
+        }
+        gcap = std::max(gcap, g);
+    }
+    T.fgcap = gcap;
+    const size_t fixedF = (size_t)rb * (T.matcap + gcap + 2 * (size_t)T.maxnb) + 4 * ((size_t)T.maxnb + 4) + 1024;
+    if (fixedF + (size_t)rb * (2 * (size_t)T.maxnb + 128) > (size_t)fbudget) { T.fast = false; return ""; }
+    const int work = (int)(((size_t)fbudget - fixedF) / (size_t)rb);
+    if ((size_t)work * rb < 16 * (3 + (size_t)kMaxD + 2 * (size_t)np)) { T.fast = false; return ""; }
+    T.fast_cap = work;
+    // pass 2: records
+    T.fdesc.clear();
+    T.fdesc_off.assign(T.n_terms + 1, 0);
+    T.fdesccap = 0;
+    int64_t rank_off = 0;
+    for (int64_t q = 0; q < T.n_terms; q++) {
+        const int t = T.order[q];
+        const uint8_t *lt = &T.levels[(size_t)t * T.Dpad];
+        int act[kMaxD], na = 0, pos_of_mode[kMaxD];
+        bool l1[kMaxD], inner[kMaxD];
+        double c0 = T.c0const;
+        for (int i = 0; i < D; i++) {
+            pos_of_mode[i] = -1;
+            const LevelInfo &li = LI(i, lt[i]);
+            if (li.nb > 1) { act[na] = i; l1[na] = li.nb == T.nb1 && li.nq == T.nq1; inner[na] = false; na++; }
+            else c0 += T.fsc[T.soff[(size_t)i * Lp + lt[i]]];
+        }
+        int R = 0;
+        for (int a = na - 1; a >= 0 && R < RMAX; a--)
+            if (l1[a]) { inner[a] = true; R++; }
+        int pos = 0;
+        int posmode[kMaxD];
+        for (int a = 0; a < na; a++) if (inner[a]) { pos_of_mode[act[a]] = pos; posmode[pos++] = act[a]; }
+        for (int a = 0; a < na; a++) if (!inner[a]) { pos_of_mode[act[a]] = pos; posmode[pos++] = act[a]; }
+        int64_t NB = 1, NBIn = 1;
+        for (int j = 0; j < na; j++) {
+            NB *= LI(posmode[j], lt[posmode[j]]).nb;
+            if (j < R) NBIn *= LI(posmode[j], lt[posmode[j]]).nb;
+        }
+        // pairs
+        std::vector<FDescPair> prs;
+        std::vector<FDescInd> inds;
+        int gsize = 0;
+        for (int P = 0; P < np; P++) {
+            const int a = T.pair_modes[2 * P], b = T.pair_modes[2 * P + 1];
+            const int pa = pos_of_mode[a], pb = pos_of_mode[b];
+            const size_t key = ((size_t)P * Lp + lt[a]) * Lp + lt[b];
+            if (pa >= 0 && pb >= 0) {
+                FDescPair e{(unsigned char)pa, (unsigned char)pb, 0, 0, T.goff[key], gsize, 0};
+                gsize += LI(a, lt[a]).nq * LI(b, lt[b]).nq;
+                prs.push_back(e);
+            } else if (pa >= 0 || pb >= 0) {
+                const int side = pa >= 0 ? 0 : 1;
+                const int lact = side == 0 ? lt[a] : lt[b], lcol = side == 0 ? lt[b] : lt[a];
+                FDescInd e{(unsigned char)(side == 0 ? pa : pb), 0, 0, 0,
+                           T.ioff[(((size_t)P * 2 + side) * Lp + lact) * Lp + lcol]};
+                inds.push_back(e);
+            } else {
+                c0 += T.fsc[T.spoff[key]];
+            }
+        }
+        // slicing depth (the same rule the kernel relies on)
+        const bool grid = !prs.empty();
+        auto stage_of = [&](int s) {
+            int64_t sz = NBIn;
+            for (int j = R + s; j < na; j++) sz *= LI(posmode[j], lt[posmode[j]]).nq;
+            return sz;
+        };
+        int sv = 0;
+        if (grid) {
+            sv = -1;
+            for (int vt = 4; vt >= 1 && sv < 0; vt /= 2)
+                for (int s = 0; s <= na - R && sv < 0; s++)
+                    if ((2 * NB + 2 * stage_of(s)) * vt <= work) sv = s;
+            if (sv < 0) { T.fast = false; T.fdesc.clear(); return ""; }  // generic kernel instead
+        }
+        if (2 * NB > work) { T.fast = false; T.fdesc.clear(); return ""; }
+        // record
+        const int units = 3 + na + (int)prs.size() + ((int)inds.size() + 1) / 2;
+        const size_t u0 = T.fdesc.size();
+        T.fdesc.resize(u0 + units, int4{0, 0, 0, 0});
+        FDescHdr h{};
+        h.m = na; h.R = R; h.NB = (int)NB; h.coef = T.coefs[t];
+        h.s = sv; h.npair = (int)prs.size(); h.nind = (int)inds.size(); h.gsize = gsize;
+        h.c0 = c0; h.rank_off = rank_off;
+        put(T.fdesc, u0, 0, h);
+        for (int j = 0; j < na; j++) {
+            const int i = posmode[j];
+            const LevelInfo &li = LI(i, lt[i]);
+            FDescPos e{(unsigned char)i, (unsigned char)lt[i], (unsigned char)li.nb, (unsigned char)li.nq,
+                       li.offB, li.offBW, T.h1off[(size_t)i * Lp + lt[i]]};
+            put(T.fdesc, u0 + 3 + j, 0, e);
+        }
+        for (size_t q2 = 0; q2 < prs.size(); q2++) put(T.fdesc, u0 + 3 + na + q2, 0, prs[q2]);
+        for (size_t q2 = 0; q2 < inds.size(); q2++)
+            put(T.fdesc, u0 + 3 + na + prs.size() + q2 / 2, 8 * (q2 % 2), inds[q2]);
+        T.fdesc_off[q + 1] = (unsigned)(u0 + units);
+        T.fdesccap = std::max(T.fdesccap, units);
+        rank_off += NB;
+    }
+    if (T.fdesc.size() >= ((size_t)1 << 32)) return "fast-path records too large";
+    T.franks = rank_off;
     return "";
 }
 
