@@ -223,6 +223,11 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
         kp.fast.c0const = T.c0const;
         kp.fast.desccap = T.fdesccap;
         kp.fast.gcap = T.fgcap;
+        kp.fast.nbocap = T.fnbocap;
+        kp.fast.n_big = T.fn_big;
+        kp.fast.work_cta = T.fwork_cta;
+        kp.fast.work_warp = T.fwork_warp;
+        kp.matcap = T.matcap;
         kp.cap = T.fast_cap;
         // M^B in the fast kernel's layout order, built on the device
         void *rp = nullptr;

@@ -35,24 +35,29 @@ constexpr int kMaxVB = 8;  // vectors per chunk
 struct FHdr {
     int m, R, NB, NBo, grid, bad, coef;
     int s, vb, NBO, NBrest, NBIn, nslice, NGs;
+    int npair, nind, gsize;
     double c0;
-    int mode[kMaxD], lev[kMaxD], nb[kMaxD], nq[kMaxD];  // by layout position
+    long long rank_off;
+    int mode[kMaxD], nb[kMaxD], nq[kMaxD];               // by layout position
     int ostride[kMaxD];                                  // stride of a position inside its block (i or o)
     unsigned smag[kMaxD], bmag[kMaxD];                   // reciprocals of ostride and nb
     int oB[kMaxD], oBW[kMaxD], oH[kMaxD];                // shared-memory offsets of B, B^T W, H1
     int gstride[kMaxD];                                  // outer grid strides inside a slice
     unsigned gmag[kMaxD], qmag[kMaxD];                   // reciprocals of gstride and nq
     int bymode[kMaxD];                                   // positions sorted by mode
-    int pos_of_mode[kMaxD], lev_of_mode[kMaxD];
-    int npair, nind;
-    int pa[kMaxPairs], pb[kMaxPairs], pg[kMaxPairs];     // active pairs: positions, G offset (shared)
-    int pgg[kMaxPairs];                                  // G offset in the global fast tables
     int gB[kMaxD], gBW[kMaxD], gH1[kMaxD];               // global offsets of B, B^T W, H1 base
-    long long rank_off;
-    int gsize;
-    int ipos[kMaxPairs], ioffs[kMaxPairs];               // induced matrices: position, offset
     int uS[kMaxD];                                       // slice indices of the sliced positions
+    int pg[kMaxPairs], pgg[kMaxPairs], ioffs[kMaxPairs]; // G offsets (shared, global), induced offsets
+    unsigned char pa[kMaxPairs], pb[kMaxPairs], ipos[kMaxPairs];
 };
+constexpr int kHdrBytes = 4096;  // per-group header budget the host plans with
+static_assert(sizeof(FHdr) <= kHdrBytes, "term header too large");
+
+template <int GS>
+__device__ __forceinline__ void gsync()
+{
+    if (GS == 32) __syncwarp(); else __syncthreads();
+}
 
 // floor(x / d) for x * d < 2^32, via a 32-bit reciprocal (mag = ceil(2^32 / d), d > 1)
 __device__ __forceinline__ unsigned rmag(unsigned d) { return d <= 1 ? 0u : 0xFFFFFFFFu / d + 1u; }
@@ -94,7 +99,7 @@ __device__ void load_record(const KParams &P, int p, int4 *buf, FHdr &H)
     const FDescPair *pr = reinterpret_cast<const FDescPair *>(buf + 3 + m);
     const FDescInd *in = reinterpret_cast<const FDescInd *>(buf + 3 + m + np);
     for (int j = lane; j < m; j += 32) {
-        H.mode[j] = ps[j].mode; H.lev[j] = ps[j].lev; H.nb[j] = ps[j].nb; H.nq[j] = ps[j].nq;
+        H.mode[j] = ps[j].mode; H.nb[j] = ps[j].nb; H.nq[j] = ps[j].nq;
         H.gB[j] = ps[j].offB; H.gBW[j] = ps[j].offBW; H.gH1[j] = ps[j].offH1;
     }
     for (int q = lane; q < np; q += 32) { H.pa[q] = pr[q].pa; H.pb[q] = pr[q].pb; H.pg[q] = pr[q].gsm; H.pgg[q] = pr[q].goff; }
@@ -121,7 +126,7 @@ __device__ void derive_layout(const KParams &P, int nvec, int work, FHdr &H)
         H.qmag[j] = rmag(H.nq[j]);
         if (j < R) NBIn *= H.nb[j];
     }
-    if (mat > P.matcap || H.NB > P.maxnb || H.gsize > P.fast.gcap) { H.bad = 1; return; }
+    if (mat > P.matcap || H.gsize > P.fast.gcap) { H.bad = 1; return; }
     H.NBIn = NBIn; H.NBo = H.NB / NBIn;
     int st = 1;
     for (int j = R - 1; j >= 0; j--) { H.ostride[j] = st; H.smag[j] = rmag(st); st *= H.nb[j]; }
@@ -142,6 +147,7 @@ __device__ void derive_layout(const KParams &P, int nvec, int work, FHdr &H)
     H.vb = vb;
     H.NBO = 1; H.nslice = 1;
     for (int j = R; j < R + sv; j++) { H.NBO *= H.nb[j]; H.nslice *= H.nq[j]; }
+    if (H.NBO > P.fast.nbocap) { H.bad = 3; return; }
     H.NBrest = 1; H.NGs = 1;
     for (int j = R + sv; j < m; j++) { H.NBrest *= H.nb[j]; H.NGs *= H.nq[j]; }
     int gs = 1;
@@ -178,16 +184,16 @@ __global__ void __launch_bounds__(kFT) k_build_ranks(const KParams P, int *__res
 }
 
 // out[a][r][c] = sum_k M[r][k] in[a][k][c], matrix in registers, one fibre (a, c) per thread
-template <typename T, int N, int RR>
+template <typename T, int N, int RR, int GS>
 __device__ __forceinline__ void fcontract_t(const T *__restrict__ in, T *__restrict__ out, int A, int C,
-                                            const T *__restrict__ M)
+                                            const T *__restrict__ M, int tid)
 {
     T mr[RR * N];
 #pragma unroll
     for (int i = 0; i < RR * N; i++) mr[i] = M[i];
     const int total = A * C;
     const unsigned mag = rmag(C);
-    for (int f = threadIdx.x; f < total; f += kFT) {
+    for (int f = tid; f < total; f += GS) {
         const int a = fdiv(f, C, mag), c = f - a * C;
         const T *ip = in + a * N * C + c;
         T *op = out + a * RR * C + c;
@@ -204,12 +210,12 @@ __device__ __forceinline__ void fcontract_t(const T *__restrict__ in, T *__restr
     }
 }
 
-template <typename T>
+template <typename T, int GS>
 __device__ void fcontract_rt(const T *__restrict__ in, T *__restrict__ out, int A, int n, int r, int C,
-                             const T *__restrict__ M)
+                             const T *__restrict__ M, int tid)
 {
     const int total = A * r * C;
-    for (int e = threadIdx.x; e < total; e += kFT) {
+    for (int e = tid; e < total; e += GS) {
         const int c = e % C, tq = e / C, rr = tq % r, a = tq / r;
         const T *ip = in + (a * n) * C + c;
         const T *mp = M + rr * n;
@@ -219,14 +225,14 @@ __device__ void fcontract_rt(const T *__restrict__ in, T *__restrict__ out, int 
     }
 }
 
-template <typename T>
-__device__ void fcontract(const T *in, T *out, int A, int n, int r, int C, const T *M)
+template <typename T, int GS>
+__device__ void fcontract(const T *in, T *out, int A, int n, int r, int C, const T *M, int tid)
 {
-#define SG_FC(NN, RRR) case (NN) * 64 + (RRR): fcontract_t<T, NN, RRR>(in, out, A, C, M); return;
+#define SG_FC(NN, RRR) case (NN) * 64 + (RRR): fcontract_t<T, NN, RRR, GS>(in, out, A, C, M, tid); return;
     switch (n * 64 + r) {
         SG_FC(2, 2) SG_FC(2, 3) SG_FC(3, 2) SG_FC(3, 3) SG_FC(3, 4) SG_FC(4, 3) SG_FC(4, 4) SG_FC(4, 5)
         SG_FC(5, 4) SG_FC(5, 5) SG_FC(5, 6) SG_FC(6, 5) SG_FC(6, 6) SG_FC(6, 7) SG_FC(7, 6)
-        default: fcontract_rt(in, out, A, n, r, C, M); return;
+        default: fcontract_rt<T, GS>(in, out, A, n, r, C, M, tid); return;
     }
 #undef SG_FC
 }
@@ -253,8 +259,8 @@ __device__ __forceinline__ void rstage(const T (&in)[SZ], T (&out)[SZ], const T 
 // Register phase: for every outer grid point g of the slice and every vector
 // of the chunk, the inner slots basis -> grid, times the potential, grid ->
 // basis, in place in Z[i][v][g].
-template <typename T, int R, int NB1, int NQ1, bool UNI>
-__device__ void reg_phase(const FHdr &H, const T *mats, const T *G, T *Z, const int vb)
+template <typename T, int R, int NB1, int NQ1, bool UNI, int GS>
+__device__ void reg_phase(const FHdr &H, const T *mats, const T *G, T *Z, const int vb, const int tid)
 {
     constexpr int NBI = cpow(NB1, R), NGI = cpow(NQ1, R), SZ = NGI;
     constexpr int RA = R > 0 ? R : 1;
@@ -268,7 +274,7 @@ __device__ void reg_phase(const FHdr &H, const T *mats, const T *G, T *Z, const 
             BWm[b][e] = R > 0 ? mats[H.oBW[b] + e] : T(0);
         }
     const int s0 = R + H.s, NGs = H.NGs;
-    for (int g = threadIdx.x; g < NGs; g += kFT) {
+    for (int g = tid; g < NGs; g += GS) {
         // potential on the inner grid of this outer point, accumulated pair by pair
         T V[SZ];
 #pragma unroll
@@ -351,27 +357,45 @@ __device__ void reg_phase(const FHdr &H, const T *mats, const T *G, T *Z, const 
     }
 }
 
-template <typename T, int NB1, int NQ1, int RMAX, bool UNI>
-__global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 3 : 2)
-    k_apply_fast(const KParams P, const double *__restrict__ x, const long long *__restrict__ maxbits, int nvec)
+// Shared-memory partition of one term group: matrices, G tables, slice
+// weights (head), then the work area for X, Y and the two grid buffers.
+__host__ __device__ inline size_t part_head_bytes(const KParams &P, size_t rb)
 {
+    return (((size_t)P.matcap + P.fast.gcap + 2 * (size_t)P.fast.nbocap) * rb + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t part_bytes(const KParams &P, size_t rb, int work)
+{
+    return (part_head_bytes(P, rb) + (size_t)work * rb + 15) & ~(size_t)15;
+}
+
+// GS threads process one term: GS = 128 (one block per term, the largest
+// terms) or GS = 32 (one warp per term, four terms per block, no block-wide
+// barriers).  Terms [p0, p0 + pcount) of the processing order.
+template <typename T, int NB1, int NQ1, int RMAX, bool UNI, int GS>
+__global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 3 : 2)
+    k_apply_fast(const KParams P, const double *__restrict__ x, const long long *__restrict__ maxbits, int nvec,
+                 int p0, int pcount, int work_cap)
+{
+    constexpr int NG = kFT / GS;
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ FHdr H;
-    const int tid = threadIdx.x;
-    T *mats = reinterpret_cast<T *>(smraw);
+    __shared__ FHdr Hs[NG];
+    const int grp = threadIdx.x / GS, tid = threadIdx.x % GS;
+    FHdr &H = Hs[grp];
+    const int pidx = blockIdx.x * NG + grp;
+    if (pidx >= pcount) return;
+    const size_t rb = sizeof(T);
+    unsigned char *base = smraw + (size_t)grp * part_bytes(P, rb, work_cap);
+    T *mats = reinterpret_cast<T *>(base);
     T *gtab = mats + P.matcap;
     T *WoF = gtab + P.fast.gcap;
-    T *WoB = WoF + P.maxnb;
-    int *rk = reinterpret_cast<int *>(WoB + P.maxnb);
-    T *work = reinterpret_cast<T *>(
-        reinterpret_cast<unsigned char *>(smraw) +
-        (((size_t)(P.matcap + P.fast.gcap + 2 * P.maxnb) * sizeof(T) + 4 * (size_t)P.maxnb + 15) & ~(size_t)15));
+    T *WoB = WoF + P.fast.nbocap;
+    T *work = reinterpret_cast<T *>(base + part_head_bytes(P, rb));
 
     if (tid < 32) {
-        load_record(P, blockIdx.x, reinterpret_cast<int4 *>(work), H);
-        if (tid == 0) derive_layout(P, nvec, P.cap, H);
+        load_record(P, p0 + pidx, reinterpret_cast<int4 *>(work), H);
+        if (tid == 0) derive_layout(P, nvec, work_cap, H);
     }
-    __syncthreads();
+    gsync<GS>();
     if (H.bad) {
         if (tid == 0 && P.err) atomicCAS(P.err, 0, 110 + H.bad);
         return;
@@ -379,17 +403,17 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 3 : 2)
     const T *tab = FTab<T>::t(P);
     const T *ftab = FTab<T>::f(P);
     const int m = H.m, R = H.R, NB = H.NB, NBo = H.NBo;
+    const int *rk = P.fast.ranks + H.rank_off;
 
-    // per-position matrices: B, B^T W (grid part) and H1 = base + induced;
-    // G tables of the active pairs; the term's compact indices
+    // per-position matrices: B, B^T W (grid part) and H1 = base + induced; G tables of the active pairs
     for (int j = 0; j < m; j++) {
         const int nb = H.nb[j], nq = H.nq[j];
         if (H.grid)
-            for (int e = tid; e < nb * nq; e += kFT) {
+            for (int e = tid; e < nb * nq; e += GS) {
                 mats[H.oB[j] + e] = tab[H.gB[j] + e];
                 mats[H.oBW[j] + e] = tab[H.gBW[j] + e];
             }
-        for (int e = tid; e < nb * nb; e += kFT) {
+        for (int e = tid; e < nb * nb; e += GS) {
             T hv = ftab[H.gH1[j] + e];
             for (int q = 0; q < H.nind; q++)
                 if (H.ipos[q] == j) hv += ftab[H.ioffs[q] + e];
@@ -398,34 +422,33 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 3 : 2)
     }
     for (int p = 0; p < H.npair; p++) {
         const int sz = H.nq[H.pa[p]] * H.nq[H.pb[p]];
-        for (int e = tid; e < sz; e += kFT) gtab[H.pg[p] + e] = ftab[H.pgg[p] + e];
+        for (int e = tid; e < sz; e += GS) gtab[H.pg[p] + e] = ftab[H.pgg[p] + e];
     }
-    for (int e = tid; e < NB; e += kFT) rk[e] = __ldg(P.fast.ranks + H.rank_off + e);
-    __syncthreads();
+    gsync<GS>();
 
     for (int v0 = 0; v0 < nvec; v0 += H.vb) {
         const int vb = min(H.vb, nvec - v0);
         T *X = work, *Y = work + NB * vb, *bufA = Y + NB * vb;
         // gather: X[i][v][o]
-        for (int e = tid; e < NB; e += kFT) {
+        for (int e = tid; e < NB; e += GS) {
             const int i = e / NBo, o = e - i * NBo;
-            for (int v = 0; v < vb; v++)
-                X[(i * vb + v) * NBo + o] = (T)__ldg(x + (size_t)(v0 + v) * P.n_cs + rk[e]);
+            const int r = __ldg(rk + e);
+            for (int v = 0; v < vb; v++) X[(i * vb + v) * NBo + o] = (T)__ldg(x + (size_t)(v0 + v) * P.n_cs + r);
         }
-        __syncthreads();
+        gsync<GS>();
         // basis part: Y = c0 X + sum_j H1_j x_j X, all vectors of the chunk per element
-        for (int e = tid; e < NB; e += kFT) {
+        for (int e = tid; e < NB; e += GS) {
             const int i = e / NBo, o = e - i * NBo;
-            const int base = i * vb * NBo + o;
+            const int base0 = i * vb * NBo + o;
             T acc[kMaxVB];
 #pragma unroll
-            for (int v = 0; v < kMaxVB; v++) acc[v] = v < vb ? (T)H.c0 * X[base + v * NBo] : T(0);
+            for (int v = 0; v < kMaxVB; v++) acc[v] = v < vb ? (T)H.c0 * X[base0 + v * NBo] : T(0);
             for (int j = 0; j < m; j++) {
                 const int src = j < R ? i : o;
                 const int q = fdiv(src, H.ostride[j], H.smag[j]);
                 const int nbj = H.nb[j], kj = q - fdiv(q, nbj, H.bmag[j]) * nbj;
                 const int st = j < R ? H.ostride[j] * vb * NBo : H.ostride[j];
-                const T *xp = X + base - kj * st;
+                const T *xp = X + base0 - kj * st;
                 const T *Hr = mats + H.oH[j] + kj * nbj;
                 for (int kp = 0; kp < nbj; kp++) {
                     const T hv = Hr[kp];
@@ -436,11 +459,11 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 3 : 2)
             }
 #pragma unroll
             for (int v = 0; v < kMaxVB; v++)
-                if (v < vb) Y[base + v * NBo] = acc[v];
+                if (v < vb) Y[base0 + v * NBo] = acc[v];
         }
-        __syncthreads();
+        gsync<GS>();
         if (H.grid) {
-            const int p0 = R + H.s;
+            const int ps = R + H.s;
             const int NBIv = H.NBIn * vb;
             T *bufB = bufA + (size_t)H.NBIn * H.NGs * vb;
             for (int sl = 0; sl < H.nslice; sl++) {
@@ -448,13 +471,13 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 3 : 2)
                 if (H.s > 0) {
                     if (tid == 0) {
                         int rem = sl;
-                        for (int j = p0 - 1; j >= R; j--) { H.uS[j] = rem % H.nq[j]; rem /= H.nq[j]; }
+                        for (int j = ps - 1; j >= R; j--) { H.uS[j] = rem % H.nq[j]; rem /= H.nq[j]; }
                     }
-                    __syncthreads();
-                    for (int ko = tid; ko < H.NBO; ko += kFT) {
+                    gsync<GS>();
+                    for (int ko = tid; ko < H.NBO; ko += GS) {
                         int rem = ko;
                         T wf = T(1), wb = T(1);
-                        for (int j = p0 - 1; j >= R; j--) {
+                        for (int j = ps - 1; j >= R; j--) {
                             const int kj = rem % H.nb[j];
                             rem /= H.nb[j];
                             wf *= mats[H.oB[j] + H.uS[j] * H.nb[j] + kj];
@@ -462,106 +485,125 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 3 : 2)
                         }
                         WoF[ko] = wf; WoB[ko] = wb;
                     }
-                    __syncthreads();
+                    gsync<GS>();
                     // Xs[iv][rest] = sum_ko WoF[ko] X[iv][ko][rest]
-                    for (int e = tid; e < NBIv * H.NBrest; e += kFT) {
+                    for (int e = tid; e < NBIv * H.NBrest; e += GS) {
                         const int iv = e / H.NBrest, rr = e - iv * H.NBrest;
                         const T *xp = X + (size_t)iv * NBo + rr;
                         T acc = T(0);
                         for (int ko = 0; ko < H.NBO; ko++) acc += WoF[ko] * xp[ko * H.NBrest];
                         bufA[e] = acc;
                     }
-                    __syncthreads();
+                    gsync<GS>();
                     cur = bufA; oth = bufB; spare = bufA;
                 } else {
                     cur = X; oth = bufA; spare = bufB;  // X is not needed after the basis part
                 }
                 // outer basis -> grid (ping-pong between the two grid buffers)
                 int A = NBIv;
-                for (int j = p0; j < m; j++) {
+                for (int j = ps; j < m; j++) {
                     int C = 1;
                     for (int i2 = j + 1; i2 < m; i2++) C *= H.nb[i2];
-                    fcontract(cur, oth, A, H.nb[j], H.nq[j], C, mats + H.oB[j]);
+                    fcontract<T, GS>(cur, oth, A, H.nb[j], H.nq[j], C, mats + H.oB[j], tid);
                     A *= H.nq[j];
                     T *freed = (cur == X) ? spare : cur;
                     cur = oth; oth = freed;
-                    __syncthreads();
+                    gsync<GS>();
                 }
                 if (cur == X) oth = bufA;
                 // inner slots and potential, in registers
                 switch (R) {
-                    case 0: reg_phase<T, 0, NB1, NQ1, UNI>(H, mats, gtab, cur, vb); break;
-                    case 1: if constexpr (RMAX >= 1) reg_phase<T, 1, NB1, NQ1, UNI>(H, mats, gtab, cur, vb); break;
-                    case 2: if constexpr (RMAX >= 2) reg_phase<T, 2, NB1, NQ1, UNI>(H, mats, gtab, cur, vb); break;
-                    case 3: if constexpr (RMAX >= 3) reg_phase<T, 3, NB1, NQ1, UNI>(H, mats, gtab, cur, vb); break;
+                    case 0: reg_phase<T, 0, NB1, NQ1, UNI, GS>(H, mats, gtab, cur, vb, tid); break;
+                    case 1: if constexpr (RMAX >= 1) reg_phase<T, 1, NB1, NQ1, UNI, GS>(H, mats, gtab, cur, vb, tid); break;
+                    case 2: if constexpr (RMAX >= 2) reg_phase<T, 2, NB1, NQ1, UNI, GS>(H, mats, gtab, cur, vb, tid); break;
+                    case 3: if constexpr (RMAX >= 3) reg_phase<T, 3, NB1, NQ1, UNI, GS>(H, mats, gtab, cur, vb, tid); break;
                     default: break;
                 }
-                __syncthreads();
+                gsync<GS>();
                 // outer grid -> basis, reverse order
-                for (int j = m - 1; j >= p0; j--) {
+                for (int j = m - 1; j >= ps; j--) {
                     int Aj = NBIv, C = 1;
-                    for (int i2 = p0; i2 < j; i2++) Aj *= H.nq[i2];
+                    for (int i2 = ps; i2 < j; i2++) Aj *= H.nq[i2];
                     for (int i2 = j + 1; i2 < m; i2++) C *= H.nb[i2];
-                    fcontract(cur, oth, Aj, H.nq[j], H.nb[j], C, mats + H.oBW[j]);
+                    fcontract<T, GS>(cur, oth, Aj, H.nq[j], H.nb[j], C, mats + H.oBW[j], tid);
                     T *tp = cur; cur = oth; oth = tp;
-                    __syncthreads();
+                    gsync<GS>();
                 }
                 // Y[iv][ko][rest] += WoB[ko] cur[iv][rest]
                 if (H.s > 0) {
-                    for (int e = tid; e < NB * vb; e += kFT) {
+                    for (int e = tid; e < NB * vb; e += GS) {
                         const int rr = e % H.NBrest, t2 = e / H.NBrest, ko = t2 % H.NBO, iv = t2 / H.NBO;
                         Y[e] += WoB[ko] * cur[iv * H.NBrest + rr];
                     }
                 } else {
-                    for (int e = tid; e < NB * vb; e += kFT) Y[e] += cur[e];
+                    for (int e = tid; e < NB * vb; e += GS) Y[e] += cur[e];
                 }
-                __syncthreads();
+                gsync<GS>();
             }
         }
         // exact compress-add of D_l * y_l
-        for (int e = tid; e < NB; e += kFT) {
+        for (int e = tid; e < NB; e += GS) {
             const int i = e / NBo, o = e - i * NBo;
-            const int r = rk[e];
+            const int r = __ldg(rk + e);
             for (int v = 0; v < vb; v++) {
                 unsigned long long *acc = P.acc + ((size_t)(v0 + v) * P.n_cs + r) * kAccDigits;
                 fx::fx_add_real(acc, Y[(i * vb + v) * NBo + o], H.coef, fx::lsb_exponent(maxbits[v0 + v]),
                                 P.err);
             }
         }
-        __syncthreads();
+        gsync<GS>();
     }
 }
 
+struct LaunchArgs {
+    const double *x;
+    int nvec;
+    const long long *maxbits;
+    cudaStream_t stream;
+    bool configure;
+};
+
 template <typename T, int NB1, int NQ1, int RMAX, bool UNI>
-cudaError_t launch_t(const KParams &kp, const double *x, int nvec, const long long *maxbits,
-                     size_t smem, cudaStream_t stream, bool configure)
+cudaError_t launch_t(const KParams &kp, const LaunchArgs &a)
 {
-    if (configure)
-        return cudaFuncSetAttribute(k_apply_fast<T, NB1, NQ1, RMAX, UNI>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_apply_fast<T, NB1, NQ1, RMAX, UNI><<<(unsigned)kp.n_terms, kFT, smem, stream>>>(kp, x, maxbits, nvec);
+    const size_t rb = sizeof(T);
+    const size_t smem_cta = part_bytes(kp, rb, kp.fast.work_cta);
+    const size_t smem_warp = (size_t)(kFT / 32) * part_bytes(kp, rb, kp.fast.work_warp);
+    if (a.configure) {
+        cudaError_t e = cudaFuncSetAttribute(k_apply_fast<T, NB1, NQ1, RMAX, UNI, kFT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cta);
+        if (e != cudaSuccess || kp.fast.work_warp <= 0) return e;
+        return cudaFuncSetAttribute(k_apply_fast<T, NB1, NQ1, RMAX, UNI, 32>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_warp);
+    }
+    const int nbig = kp.fast.n_big, nrest = (int)kp.n_terms - nbig;
+    if (nbig > 0)
+        k_apply_fast<T, NB1, NQ1, RMAX, UNI, kFT><<<(unsigned)nbig, kFT, smem_cta, a.stream>>>(
+            kp, a.x, a.maxbits, a.nvec, 0, nbig, kp.fast.work_cta);
+    if (nrest > 0) {
+        const unsigned blocks = (unsigned)((nrest + kFT / 32 - 1) / (kFT / 32));
+        k_apply_fast<T, NB1, NQ1, RMAX, UNI, 32><<<blocks, kFT, smem_warp, a.stream>>>(
+            kp, a.x, a.maxbits, a.nvec, nbig, nrest, kp.fast.work_warp);
+    }
     return cudaGetLastError();
 }
 
 template <typename T, bool UNI>
-cudaError_t dispatch_u(const KParams &kp, const double *x, int nvec, const long long *maxbits, size_t smem,
-                       cudaStream_t stream, bool configure)
+cudaError_t dispatch_u(const KParams &kp, const LaunchArgs &a)
 {
     // the register-slot count must be fast_rmax(...) (the host built the records with it)
     constexpr bool F32 = sizeof(T) == 4;
     const int nb1 = kp.fast.nb1, nq1 = kp.fast.nq1;
-    if (nb1 == 2 && nq1 == 3) return launch_t<T, 2, 3, F32 ? 3 : 1, UNI>(kp, x, nvec, maxbits, smem, stream, configure);
-    if (nb1 == 2 && nq1 == 2) return launch_t<T, 2, 2, F32 ? 3 : 1, UNI>(kp, x, nvec, maxbits, smem, stream, configure);
-    if (nb1 == 3 && nq1 == 3) return launch_t<T, 3, 3, F32 ? 2 : 1, UNI>(kp, x, nvec, maxbits, smem, stream, configure);
-    return launch_t<T, 1, 1, 0, UNI>(kp, x, nvec, maxbits, smem, stream, configure);
+    if (nb1 == 2 && nq1 == 3) return launch_t<T, 2, 3, F32 ? 3 : 1, UNI>(kp, a);
+    if (nb1 == 2 && nq1 == 2) return launch_t<T, 2, 2, F32 ? 3 : 1, UNI>(kp, a);
+    if (nb1 == 3 && nq1 == 3) return launch_t<T, 3, 3, F32 ? 2 : 1, UNI>(kp, a);
+    return launch_t<T, 1, 1, 0, UNI>(kp, a);
 }
 
 template <typename T>
-cudaError_t dispatch(const KParams &kp, const double *x, int nvec, const long long *maxbits, size_t smem,
-                     cudaStream_t stream, bool configure)
+cudaError_t dispatch(const KParams &kp, const LaunchArgs &a)
 {
-    return kp.fast.uni1 ? dispatch_u<T, true>(kp, x, nvec, maxbits, smem, stream, configure)
-                        : dispatch_u<T, false>(kp, x, nvec, maxbits, smem, stream, configure);
+    return kp.fast.uni1 ? dispatch_u<T, true>(kp, a) : dispatch_u<T, false>(kp, a);
 }
 
 }  // namespace
@@ -569,8 +611,7 @@ cudaError_t dispatch(const KParams &kp, const double *x, int nvec, const long lo
 size_t fast_smem_bytes(const KParams &kp, bool fp32)
 {
     const size_t rb = fp32 ? 4 : 8;
-    const size_t head = ((size_t)(kp.matcap + kp.fast.gcap + 2 * kp.maxnb) * rb + 4 * (size_t)kp.maxnb + 15) & ~(size_t)15;
-    return head + rb * (size_t)kp.cap;
+    return std::max(part_bytes(kp, rb, kp.fast.work_cta), (size_t)(kFT / 32) * part_bytes(kp, rb, kp.fast.work_warp));
 }
 
 cudaError_t launch_build_ranks(const KParams &kp, int *ranks, cudaStream_t stream)
@@ -583,18 +624,16 @@ cudaError_t launch_build_ranks(const KParams &kp, int *ranks, cudaStream_t strea
 
 cudaError_t configure_fast_kernels(const KParams &kp, bool fp32)
 {
-    const size_t smem = fast_smem_bytes(kp, fp32);
-    return fp32 ? dispatch<float>(kp, nullptr, 0, nullptr, smem, 0, true)
-                : dispatch<double>(kp, nullptr, 0, nullptr, smem, 0, true);
+    LaunchArgs a{nullptr, 0, nullptr, 0, true};
+    return fp32 ? dispatch<float>(kp, a) : dispatch<double>(kp, a);
 }
 
 cudaError_t launch_apply_fast(const KParams &kp, bool fp32, const double *x, int nvec,
                               const long long *maxbits, cudaStream_t stream)
 {
     if (kp.n_terms == 0) return cudaSuccess;
-    const size_t smem = fast_smem_bytes(kp, fp32);
-    return fp32 ? dispatch<float>(kp, x, nvec, maxbits, smem, stream, false)
-                : dispatch<double>(kp, x, nvec, maxbits, smem, stream, false);
+    LaunchArgs a{x, nvec, maxbits, stream, false};
+    return fp32 ? dispatch<float>(kp, a) : dispatch<double>(kp, a);
 }
 
 }  // namespace sg

@@ -85,6 +85,9 @@ struct FastParams {
     const int *ranks;      // compact index of every basis function of every term (layout order)
     int desccap;           // largest record, in 16-byte units
     int gcap;              // largest set of a term's G tables, in words
+    int nbocap;            // largest sliced outer block (slice weights)
+    int n_big;             // terms [0, n_big) run one per block, the rest one per warp
+    int work_cta, work_warp;   // work-area capacities (elements) of the two kernels
 };
 
 // Everything a kernel needs, passed by value.
@@ -152,7 +155,7 @@ struct HostTables {
     std::vector<int4> fdesc;          // term records
     std::vector<unsigned> fdesc_off;  // [n_terms+1]
     int64_t franks = 0;               // total compact indices (N_s)
-    int fdesccap = 0, fgcap = 0;
+    int fdesccap = 0, fgcap = 0, fnbocap = 1, fn_big = 0, fwork_cta = 0, fwork_warp = 0;
     int cap = 0, maxnb = 0, matcap = 0, vtabcap = 0;
     int64_t flops_per_vec = 0;       // FMA-counted work of one real apply (2 flops per FMA)
 };

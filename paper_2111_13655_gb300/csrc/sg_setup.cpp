@@ -557,9 +557,10 @@ void put(std::vector<int4> &v, size_t unit, size_t byte, const S &x)
 // inner register slots, then the others, each group in mode order) with the
 // offsets of their tables, the term constant c0, the active coupled pairs with
 // the offsets of their G tables, the induced single-mode matrices, and the
-// slicing depth that lets a chunk of 4 (2, 1) vectors fit the shared-memory
-// work area.  First pass: shared memory for G tables; then the work area; then
-// the records.
+// slicing depth for its kernel.  The most expensive terms (a prefix of the
+// processing order) run one per thread block; the others one per warp, four
+// per block, in a quarter of the block's shared memory each.  A term goes to
+// the warp form when it fits that quarter with at most one sliced mode.
 std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fbudget, int rb)
 {
     HostTables &T = *Tp;
@@ -567,30 +568,17 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
     const int RMAX = fast_rmax(fp32, T.nb1, T.nq1);
     const int np = (int)T.pair_modes.size() / 2;
     auto LI = [&](int i, int l) -> const LevelInfo & { return T.lvl[(size_t)i * Lp + l]; };
-    // pass 1: G-table words per term
-    int gcap = 1;
-    for (int64_t q = 0; q < T.n_terms; q++) {
-        const uint8_t *lt = &T.levels[(size_t)T.order[q] * T.Dpad];
-        int g = 0;
-        for (int P = 0; P < np; P++) {
-            const int a = T.pair_modes[2 * P], b = T.pair_modes[2 * P + 1];
-            if (LI(a, lt[a]).nb > 1 && LI(b, lt[b]).nb > 1) g += LI(a, lt[a]).nq * LI(b, lt[b]).nq;
-        }
-        gcap = std::max(gcap, g);
-    }
-    T.fgcap = gcap;
-    const size_t fixedF = (size_t)rb * (T.matcap + gcap + 2 * (size_t)T.maxnb) + 4 * ((size_t)T.maxnb + 4) + 1024;
-    if (fixedF + (size_t)rb * (2 * (size_t)T.maxnb + 128) > (size_t)fbudget) { T.fast = false; return ""; }
-    const int work = (int)(((size_t)fbudget - fixedF) / (size_t)rb);
-    if ((size_t)work * rb < 16 * (3 + (size_t)kMaxD + 2 * (size_t)np)) { T.fast = false; return ""; }
-    T.fast_cap = work;
-    // pass 2: records
-    T.fdesc.clear();
-    T.fdesc_off.assign(T.n_terms + 1, 0);
-    T.fdesccap = 0;
-    int64_t rank_off = 0;
-    for (int64_t q = 0; q < T.n_terms; q++) {
-        const int t = T.order[q];
+
+    struct TermPlan {
+        int na, R, posmode[kMaxD];
+        int64_t NB, NBIn;
+        bool grid;
+        int gsize;
+        double c0;
+        std::vector<FDescPair> prs;
+        std::vector<FDescInd> inds;
+    };
+    auto plan_term = [&](int t, TermPlan &tp) {
         const uint8_t *lt = &T.levels[(size_t)t * T.Dpad];
         int act[kMaxD], na = 0, pos_of_mode[kMaxD];
         bool l1[kMaxD], inner[kMaxD];
@@ -605,74 +593,129 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
         for (int a = na - 1; a >= 0 && R < RMAX; a--)
             if (l1[a]) { inner[a] = true; R++; }
         int pos = 0;
-        int posmode[kMaxD];
-        for (int a = 0; a < na; a++) if (inner[a]) { pos_of_mode[act[a]] = pos; posmode[pos++] = act[a]; }
-        for (int a = 0; a < na; a++) if (!inner[a]) { pos_of_mode[act[a]] = pos; posmode[pos++] = act[a]; }
-        int64_t NB = 1, NBIn = 1;
+        for (int a = 0; a < na; a++) if (inner[a]) { pos_of_mode[act[a]] = pos; tp.posmode[pos++] = act[a]; }
+        for (int a = 0; a < na; a++) if (!inner[a]) { pos_of_mode[act[a]] = pos; tp.posmode[pos++] = act[a]; }
+        tp.na = na; tp.R = R; tp.NB = 1; tp.NBIn = 1;
         for (int j = 0; j < na; j++) {
-            NB *= LI(posmode[j], lt[posmode[j]]).nb;
-            if (j < R) NBIn *= LI(posmode[j], lt[posmode[j]]).nb;
+            tp.NB *= LI(tp.posmode[j], lt[tp.posmode[j]]).nb;
+            if (j < R) tp.NBIn *= LI(tp.posmode[j], lt[tp.posmode[j]]).nb;
         }
-        // pairs
-        std::vector<FDescPair> prs;
-        std::vector<FDescInd> inds;
-        int gsize = 0;
+        tp.prs.clear(); tp.inds.clear();
+        tp.gsize = 0;
         for (int P = 0; P < np; P++) {
             const int a = T.pair_modes[2 * P], b = T.pair_modes[2 * P + 1];
             const int pa = pos_of_mode[a], pb = pos_of_mode[b];
             const size_t key = ((size_t)P * Lp + lt[a]) * Lp + lt[b];
             if (pa >= 0 && pb >= 0) {
-                FDescPair e{(unsigned char)pa, (unsigned char)pb, 0, 0, T.goff[key], gsize, 0};
-                gsize += LI(a, lt[a]).nq * LI(b, lt[b]).nq;
-                prs.push_back(e);
+                tp.prs.push_back(FDescPair{(unsigned char)pa, (unsigned char)pb, 0, 0, T.goff[key], tp.gsize, 0});
+                tp.gsize += LI(a, lt[a]).nq * LI(b, lt[b]).nq;
             } else if (pa >= 0 || pb >= 0) {
                 const int side = pa >= 0 ? 0 : 1;
                 const int lact = side == 0 ? lt[a] : lt[b], lcol = side == 0 ? lt[b] : lt[a];
-                FDescInd e{(unsigned char)(side == 0 ? pa : pb), 0, 0, 0,
-                           T.ioff[(((size_t)P * 2 + side) * Lp + lact) * Lp + lcol]};
-                inds.push_back(e);
+                tp.inds.push_back(FDescInd{(unsigned char)(side == 0 ? pa : pb), 0, 0, 0,
+                                           T.ioff[(((size_t)P * 2 + side) * Lp + lact) * Lp + lcol]});
             } else {
                 c0 += T.fsc[T.spoff[key]];
             }
         }
-        // slicing depth (the same rule the kernel relies on)
-        const bool grid = !prs.empty();
-        auto stage_of = [&](int s) {
-            int64_t sz = NBIn;
-            for (int j = R + s; j < na; j++) sz *= LI(posmode[j], lt[posmode[j]]).nq;
-            return sz;
-        };
-        int sv = 0;
-        if (grid) {
-            sv = -1;
-            for (int vt = 4; vt >= 1 && sv < 0; vt /= 2)
-                for (int s = 0; s <= na - R && sv < 0; s++)
-                    if ((2 * NB + 2 * stage_of(s)) * vt <= work) sv = s;
-            if (sv < 0) { T.fast = false; T.fdesc.clear(); return ""; }  // generic kernel instead
+        tp.grid = !tp.prs.empty();
+        tp.c0 = c0;
+    };
+    auto stage_of = [&](int t, const TermPlan &tp, int s) {
+        const uint8_t *lt = &T.levels[(size_t)t * T.Dpad];
+        int64_t sz = tp.NBIn;
+        for (int j = tp.R + s; j < tp.na; j++) sz *= LI(tp.posmode[j], lt[tp.posmode[j]]).nq;
+        return sz;
+    };
+    // slicing depth for a work area: the smallest leaving room for 4 (2, 1) vectors
+    auto depth_for = [&](int t, const TermPlan &tp, int64_t work, int smax) {
+        if (2 * tp.NB > work) return -1;
+        if (!tp.grid) return 0;
+        for (int vt = 4; vt >= 1; vt /= 2)
+            for (int s = 0; s <= std::min(smax, tp.na - tp.R); s++)
+                if ((2 * tp.NB + 2 * stage_of(t, tp, s)) * vt <= work) return s;
+        return -1;
+    };
+
+    // pass 1: capacities
+    int gcap = 1, mcap = 1;
+    TermPlan tp;
+    for (int64_t q = 0; q < T.n_terms; q++) {
+        plan_term(T.order[q], tp);
+        gcap = std::max(gcap, tp.gsize);
+        const uint8_t *lt = &T.levels[(size_t)T.order[q] * T.Dpad];
+        int mat = 0;
+        for (int j = 0; j < tp.na; j++) {
+            const LevelInfo &li = LI(tp.posmode[j], lt[tp.posmode[j]]);
+            mat += 2 * li.nb * li.nq + li.nb * li.nb;
         }
-        if (2 * NB > work) { T.fast = false; T.fdesc.clear(); return ""; }
-        // record
-        const int units = 3 + na + (int)prs.size() + ((int)inds.size() + 1) / 2;
+        mcap = std::max(mcap, mat);
+    }
+    const int nbocap = 64;  // sliced blocks larger than this are not used
+    const size_t head = ((size_t)rb * (mcap + gcap + 2 * nbocap) + 15) & ~(size_t)15;
+    const size_t hdr_static = 4 * 1024;  // per-group header in static shared memory (kHdrBytes)
+    const int64_t work_cta = ((int64_t)fbudget - (int64_t)head - 1024) / rb;
+    const int64_t work_warp = (((int64_t)fbudget - 4 * (int64_t)hdr_static) / 4 - (int64_t)head - 16) / rb;
+    if (work_cta < 2 * T.maxnb + 64 || (size_t)work_cta * rb < 16 * (3 + (size_t)kMaxD + 2 * (size_t)np)) {
+        T.fast = false;
+        return "";
+    }
+    T.matcap = std::max(T.matcap, mcap);
+    T.fgcap = gcap;
+    T.fnbocap = nbocap;
+    T.fwork_cta = (int)work_cta;
+    T.fwork_warp = (int)std::max<int64_t>(work_warp, 0);
+    T.fast_cap = T.fwork_cta;
+    // split: the last term that needs the block form ends the prefix
+    int64_t n_big = 0;
+    for (int64_t q = 0; q < T.n_terms; q++) {
+        plan_term(T.order[q], tp);
+        const int sw = work_warp > 0 ? depth_for(T.order[q], tp, work_warp, 1) : -1;
+        bool ok = sw >= 0 && (size_t)work_warp * rb >= 16 * (3 + (size_t)tp.na + tp.prs.size() + (tp.inds.size() + 1) / 2);
+        if (ok && sw > 0) {
+            int64_t nbo = LI(tp.posmode[tp.R], T.levels[(size_t)T.order[q] * T.Dpad + tp.posmode[tp.R]]).nb;
+            ok = nbo <= nbocap;
+        }
+        if (!ok) n_big = q + 1;
+    }
+    T.fn_big = (int)n_big;
+    // pass 2: records
+    T.fdesc.clear();
+    T.fdesc_off.assign(T.n_terms + 1, 0);
+    T.fdesccap = 0;
+    int64_t rank_off = 0;
+    for (int64_t q = 0; q < T.n_terms; q++) {
+        const int t = T.order[q];
+        const uint8_t *lt = &T.levels[(size_t)t * T.Dpad];
+        plan_term(t, tp);
+        const bool big = q < n_big;
+        int sv = depth_for(t, tp, big ? work_cta : work_warp, big ? kMaxD : 1);
+        if (sv < 0) { T.fast = false; T.fdesc.clear(); return ""; }  // generic kernel instead
+        int64_t nbo = 1;
+        for (int j = tp.R; j < tp.R + sv; j++) nbo *= LI(tp.posmode[j], lt[tp.posmode[j]]).nb;
+        if (nbo > nbocap) { T.fast = false; T.fdesc.clear(); return ""; }
+        const int na = tp.na;
+        const int units = 3 + na + (int)tp.prs.size() + ((int)tp.inds.size() + 1) / 2;
         const size_t u0 = T.fdesc.size();
         T.fdesc.resize(u0 + units, int4{0, 0, 0, 0});
         FDescHdr h{};
-        h.m = na; h.R = R; h.NB = (int)NB; h.coef = T.coefs[t];
-        h.s = sv; h.npair = (int)prs.size(); h.nind = (int)inds.size(); h.gsize = gsize;
-        h.c0 = c0; h.rank_off = rank_off;
+        h.m = na; h.R = tp.R; h.NB = (int)tp.NB; h.coef = T.coefs[t];
+        h.s = sv; h.npair = (int)tp.prs.size(); h.nind = (int)tp.inds.size(); h.gsize = tp.gsize;
+        h.c0 = tp.c0; h.rank_off = rank_off;
         put(T.fdesc, u0, 0, h);
         for (int j = 0; j < na; j++) {
-            const int i = posmode[j];
+            const int i = tp.posmode[j];
             const LevelInfo &li = LI(i, lt[i]);
             FDescPos e{(unsigned char)i, (unsigned char)lt[i], (unsigned char)li.nb, (unsigned char)li.nq,
                        li.offB, li.offBW, T.h1off[(size_t)i * Lp + lt[i]]};
             put(T.fdesc, u0 + 3 + j, 0, e);
         }
-        for (size_t q2 = 0; q2 < prs.size(); q2++) put(T.fdesc, u0 + 3 + na + q2, 0, prs[q2]);
-        for (size_t q2 = 0; q2 < inds.size(); q2++)
-            put(T.fdesc, u0 + 3 + na + prs.size() + q2 / 2, 8 * (q2 % 2), inds[q2]);
+        for (size_t q2 = 0; q2 < tp.prs.size(); q2++) put(T.fdesc, u0 + 3 + na + q2, 0, tp.prs[q2]);
+        for (size_t q2 = 0; q2 < tp.inds.size(); q2++)
+            put(T.fdesc, u0 + 3 + na + tp.prs.size() + q2 / 2, 8 * (q2 % 2), tp.inds[q2]);
         T.fdesc_off[q + 1] = (unsigned)(u0 + units);
         T.fdesccap = std::max(T.fdesccap, units);
-        rank_off += NB;
+        rank_off += tp.NB;
     }
     if (T.fdesc.size() >= ((size_t)1 << 32)) return "fast-path records too large";
     T.franks = rank_off;
