@@ -558,9 +558,10 @@ void put(std::vector<int4> &v, size_t unit, size_t byte, const S &x)
 // offsets of their tables, the term constant c0, the active coupled pairs with
 // the offsets of their G tables, the induced single-mode matrices, and the
 // slicing depth for its kernel.  The most expensive terms (a prefix of the
-// processing order) run one per thread block; the others one per warp, four
-// per block, in a quarter of the block's shared memory each.  A term goes to
-// the warp form when it fits that quarter with at most one sliced mode.
+// processing order) run one per thread block; the small ones at its tail run
+// one per warp, four per block, in a quarter of the block's shared memory
+// each (a term goes to the warp form when a chunk of 4 vectors fits that
+// quarter without slicing).
 std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fbudget, int rb)
 {
     HostTables &T = *Tp;
@@ -666,16 +667,14 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
     T.fwork_cta = (int)work_cta;
     T.fwork_warp = (int)std::max<int64_t>(work_warp, 0);
     T.fast_cap = T.fwork_cta;
-    // split: the last term that needs the block form ends the prefix
+    // split: terms that fit a warp's quarter unsliced with a chunk of 4 vectors
+    // run one per warp; the last term that does not ends the block-form prefix
     int64_t n_big = 0;
     for (int64_t q = 0; q < T.n_terms; q++) {
         plan_term(T.order[q], tp);
-        const int sw = work_warp > 0 ? depth_for(T.order[q], tp, work_warp, 1) : -1;
-        bool ok = sw >= 0 && (size_t)work_warp * rb >= 16 * (3 + (size_t)tp.na + tp.prs.size() + (tp.inds.size() + 1) / 2);
-        if (ok && sw > 0) {
-            int64_t nbo = LI(tp.posmode[tp.R], T.levels[(size_t)T.order[q] * T.Dpad + tp.posmode[tp.R]]).nb;
-            ok = nbo <= nbocap;
-        }
+        bool ok = work_warp > 0 &&
+                  (2 * tp.NB + (tp.grid ? 2 * stage_of(T.order[q], tp, 0) : 0)) * 4 <= work_warp &&
+                  (size_t)work_warp * rb >= 16 * (3 + (size_t)tp.na + tp.prs.size() + (tp.inds.size() + 1) / 2);
         if (!ok) n_big = q + 1;
     }
     T.fn_big = (int)n_big;
@@ -689,7 +688,7 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
         const uint8_t *lt = &T.levels[(size_t)t * T.Dpad];
         plan_term(t, tp);
         const bool big = q < n_big;
-        int sv = depth_for(t, tp, big ? work_cta : work_warp, big ? kMaxD : 1);
+        int sv = depth_for(t, tp, big ? work_cta : work_warp, big ? kMaxD : 0);
         if (sv < 0) { T.fast = false; T.fdesc.clear(); return ""; }  // generic kernel instead
         int64_t nbo = 1;
         for (int j = tp.R; j < tp.R + sv; j++) nbo *= LI(tp.posmode[j], lt[tp.posmode[j]]).nb;
