@@ -112,46 +112,45 @@ __device__ void load_record(const KParams &P, int p, int4 *buf, FHdr &H)
     __syncwarp();
 }
 
-// Layout quantities of the term (lane 0, shared memory only).
+// Layout quantities of the term, shared memory only: lane j handles position j.
 __device__ void derive_layout(const KParams &P, int nvec, int work, FHdr &H)
 {
-    const int m = H.m, R = H.R;
+    const int lane = threadIdx.x & 31;
+    const int m = H.m, R = H.R, sv = H.s;
+    if (lane < m) {
+        const int j = lane, nb = H.nb[j], nq = H.nq[j];
+        int off = 0, st = 1, gs = 1, rank = 0;
+        for (int i = 0; i < j; i++) off += 2 * H.nq[i] * H.nb[i] + H.nb[i] * H.nb[i];
+        const int end = j < R ? R : m;
+        for (int i = j + 1; i < end; i++) st *= H.nb[i];
+        for (int i = j + 1; i < m; i++) gs *= H.nq[i];
+        for (int i = 0; i < m; i++) rank += H.mode[i] < H.mode[j];
+        H.oB[j] = off; H.oBW[j] = off + nq * nb; H.oH[j] = off + 2 * nq * nb;
+        H.bmag[j] = rmag(nb); H.qmag[j] = rmag(nq);
+        H.ostride[j] = st; H.smag[j] = rmag(st);
+        H.gstride[j] = gs; H.gmag[j] = rmag(gs);
+        H.bymode[rank] = j;
+    }
+    __syncwarp();
+    if (lane != 0) return;
     H.bad = 0;
     int mat = 0, NBIn = 1;
+    int64_t stage = 1;
+    H.NBO = 1; H.nslice = 1; H.NBrest = 1; H.NGs = 1;
     for (int j = 0; j < m; j++) {
-        H.oB[j] = mat;  mat += H.nq[j] * H.nb[j];
-        H.oBW[j] = mat; mat += H.nb[j] * H.nq[j];
-        H.oH[j] = mat;  mat += H.nb[j] * H.nb[j];
-        H.bmag[j] = rmag(H.nb[j]);
-        H.qmag[j] = rmag(H.nq[j]);
+        mat += 2 * H.nq[j] * H.nb[j] + H.nb[j] * H.nb[j];
         if (j < R) NBIn *= H.nb[j];
+        else if (j < R + sv) { H.NBO *= H.nb[j]; H.nslice *= H.nq[j]; }
+        else { H.NBrest *= H.nb[j]; H.NGs *= H.nq[j]; stage *= H.nq[j]; }
     }
-    if (mat > P.matcap || H.gsize > P.fast.gcap) { H.bad = 1; return; }
+    if (mat > P.matcap || H.gsize > P.fast.gcap || H.NBO > P.fast.nbocap) { H.bad = 1; return; }
     H.NBIn = NBIn; H.NBo = H.NB / NBIn;
-    int st = 1;
-    for (int j = R - 1; j >= 0; j--) { H.ostride[j] = st; H.smag[j] = rmag(st); st *= H.nb[j]; }
-    st = 1;
-    for (int j = m - 1; j >= R; j--) { H.ostride[j] = st; H.smag[j] = rmag(st); st *= H.nb[j]; }
-    // positions in mode order: merge of the inner and outer groups (each sorted)
-    for (int a = 0, i = 0, o = R; a < m; a++) {
-        if (o >= m || (i < R && H.mode[i] < H.mode[o])) H.bymode[a] = i++;
-        else H.bymode[a] = o++;
-    }
-    const int sv = H.s;
-    int64_t stage = NBIn;
-    for (int j = R + sv; j < m; j++) stage *= H.nq[j];
+    stage *= NBIn;
     const int64_t per_vec = 2 * (int64_t)H.NB + (H.grid ? 2 * stage : 0);
     if (per_vec > work) { H.bad = 2; return; }
     int vb = nvec < kMaxVB ? nvec : kMaxVB;
     while (vb > 1 && per_vec * vb > work) vb--;
     H.vb = vb;
-    H.NBO = 1; H.nslice = 1;
-    for (int j = R; j < R + sv; j++) { H.NBO *= H.nb[j]; H.nslice *= H.nq[j]; }
-    if (H.NBO > P.fast.nbocap) { H.bad = 3; return; }
-    H.NBrest = 1; H.NGs = 1;
-    for (int j = R + sv; j < m; j++) { H.NBrest *= H.nb[j]; H.NGs *= H.nq[j]; }
-    int gs = 1;
-    for (int j = m - 1; j >= R + sv; j--) { H.gstride[j] = gs; H.gmag[j] = rmag(gs); gs *= H.nq[j]; }
 }
 
 // M^B in layout order: compact index of every basis function of every term
@@ -163,7 +162,7 @@ __global__ void __launch_bounds__(kFT) k_build_ranks(const KParams P, int *__res
     int4 *buf = reinterpret_cast<int4 *>(smraw);
     if (threadIdx.x < 32) {
         load_record(P, blockIdx.x, buf, H);
-        if (threadIdx.x == 0) derive_layout(P, 1, 1 << 30, H);
+        derive_layout(P, 1, 1 << 30, H);
     }
     __syncthreads();
     const int m = H.m, R = H.R, NBo = H.NBo, Lp = P.L + 1;
@@ -274,55 +273,70 @@ __device__ void reg_phase(const FHdr &H, const T *mats, const T *G, T *Z, const 
             BWm[b][e] = R > 0 ? mats[H.oBW[b] + e] : T(0);
         }
     const int s0 = R + H.s, NGs = H.NGs;
+    // the part of the potential that depends on inner slots only (same for every g)
+    T Vin[SZ];
+#pragma unroll
+    for (int gi = 0; gi < NGI; gi++) Vin[gi] = T(0);
+    bool outer_pairs = false;
+    for (int p = 0; p < H.npair; p++) {
+        const int A = H.pa[p], B = H.pb[p];
+        if (A >= R || B >= R) { outer_pairs = true; continue; }
+#pragma unroll
+        for (int q0 = 0; q0 < R; q0++)
+#pragma unroll
+            for (int q1 = q0 + 1; q1 < R; q1++)
+                if (q0 == A && q1 == B)
+#pragma unroll
+                    for (int gi = 0; gi < NGI; gi++)
+                        Vin[gi] += G[H.pg[p] + ((gi / cpow(NQ1, R - 1 - q0)) % NQ1) * NQ1 +
+                                     (gi / cpow(NQ1, R - 1 - q1)) % NQ1];
+    }
     for (int g = tid; g < NGs; g += GS) {
-        // potential on the inner grid of this outer point, accumulated pair by pair
+        // add the parts that depend on the outer grid point g
         T V[SZ];
-#pragma unroll
-        for (int gi = 0; gi < NGI; gi++) V[gi] = T(0);
         T vO = T(0);
-        for (int p = 0; p < H.npair; p++) {
-            const int A = H.pa[p], B = H.pb[p];
-            auto uo = [&](int j) {
-                if (j < s0) return H.uS[j];
-                const int q = fdiv(g, H.gstride[j], H.gmag[j]);
-                return q - fdiv(q, H.nq[j], H.qmag[j]) * H.nq[j];
-            };
-            if (A >= R && B >= R) {
-                vO += G[H.pg[p] + uo(A) * H.nq[B] + uo(B)];
-            } else if (A >= R) {  // B inner: row u_A of G[u_A][u_B]
-                const T *row = G + H.pg[p] + uo(A) * NQ1;
-                T rv[NQ1];
+        T hsum[RA][NQ1];
 #pragma unroll
-                for (int u = 0; u < NQ1; u++) rv[u] = row[u];
+        for (int b = 0; b < RA; b++)
 #pragma unroll
-                for (int b = 0; b < R; b++)
-                    if (b == B)
+            for (int u = 0; u < NQ1; u++) hsum[b][u] = T(0);
+        unsigned hb = 0;  // inner slots coupled to an outer one
+        if (outer_pairs)
+            for (int p = 0; p < H.npair; p++) {
+                const int A = H.pa[p], B = H.pb[p];
+                if (A < R && B < R) continue;
+                auto uo = [&](int j) {
+                    if (j < s0) return H.uS[j];
+                    const int q = fdiv(g, H.gstride[j], H.gmag[j]);
+                    return q - fdiv(q, H.nq[j], H.qmag[j]) * H.nq[j];
+                };
+                if (A >= R && B >= R) {
+                    vO += G[H.pg[p] + uo(A) * H.nq[B] + uo(B)];
+                } else if (A >= R) {  // B inner: row u_A of G[u_A][u_B]
+                    const T *row = G + H.pg[p] + uo(A) * NQ1;
+                    hb |= 1u << B;
 #pragma unroll
-                        for (int gi = 0; gi < NGI; gi++) V[gi] += rv[(gi / cpow(NQ1, R - 1 - b)) % NQ1];
-            } else if (B >= R) {  // A inner: column u_B of G[u_A][u_B]
-                const int ub = uo(B), nqb = H.nq[B];
-                T cv[NQ1];
+                    for (int b = 0; b < R; b++)
+                        if (b == B)
 #pragma unroll
-                for (int u = 0; u < NQ1; u++) cv[u] = G[H.pg[p] + u * nqb + ub];
+                            for (int u = 0; u < NQ1; u++) hsum[b][u] += row[u];
+                } else {              // A inner: column u_B of G[u_A][u_B]
+                    const int ub = uo(B), nqb = H.nq[B];
+                    hb |= 1u << A;
 #pragma unroll
-                for (int b = 0; b < R; b++)
-                    if (b == A)
+                    for (int b = 0; b < R; b++)
+                        if (b == A)
 #pragma unroll
-                        for (int gi = 0; gi < NGI; gi++) V[gi] += cv[(gi / cpow(NQ1, R - 1 - b)) % NQ1];
-            } else {              // both inner (inner positions follow mode order: A < B)
-#pragma unroll
-                for (int q0 = 0; q0 < R; q0++)
-#pragma unroll
-                    for (int q1 = q0 + 1; q1 < R; q1++)
-                        if (q0 == A && q1 == B)
-#pragma unroll
-                            for (int gi = 0; gi < NGI; gi++)
-                                V[gi] += G[H.pg[p] + ((gi / cpow(NQ1, R - 1 - q0)) % NQ1) * NQ1 +
-                                           (gi / cpow(NQ1, R - 1 - q1)) % NQ1];
+                            for (int u = 0; u < NQ1; u++) hsum[b][u] += G[H.pg[p] + u * nqb + ub];
+                }
             }
-        }
 #pragma unroll
-        for (int gi = 0; gi < NGI; gi++) V[gi] += vO;
+        for (int gi = 0; gi < NGI; gi++) V[gi] = Vin[gi] + vO;
+#pragma unroll
+        for (int b = 0; b < R; b++)
+            if (hb & (1u << b))
+#pragma unroll
+                for (int gi = 0; gi < NGI; gi++) V[gi] += hsum[b][(gi / cpow(NQ1, R - 1 - b)) % NQ1];
         for (int v = 0; v < vb; v++) {
             T va[SZ], vw[SZ];
 #pragma unroll
@@ -393,7 +407,7 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 3 : 2)
 
     if (tid < 32) {
         load_record(P, p0 + pidx, reinterpret_cast<int4 *>(work), H);
-        if (tid == 0) derive_layout(P, nvec, work_cap, H);
+        derive_layout(P, nvec, work_cap, H);
     }
     gsync<GS>();
     if (H.bad) {

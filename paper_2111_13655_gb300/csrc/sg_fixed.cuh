@@ -17,8 +17,20 @@ static __device__ __forceinline__ void fx_add(unsigned long long *acc, unsigned 
 {
     if (mant == 0 || coef == 0) return;
     if (coef < 0) { neg = !neg; coef = -coef; }
-    const unsigned __int128 Pm = (unsigned __int128)mant * (unsigned)coef;  // < 2^85, exact
     const int sh = e2 - E;
+    if (mant < (1ull << 24) && sh >= 0 && sh <= 30) {
+        // FP32 values: the exact product fits 56 bits and, shifted, 86 bits: two
+        // 64-bit halves, digits taken from them directly
+        const unsigned long long pm = mant * (unsigned)coef;       // < 2^56
+        const unsigned long long lo = pm << sh;                    // bits 0..63
+        const unsigned long long hi = sh ? pm >> (64 - sh) : 0ull; // bits 64..127
+        const unsigned long long d[4] = {lo & 0xFFFFFFFFull, lo >> 32, hi & 0xFFFFFFFFull, hi >> 32};
+#pragma unroll
+        for (int i = 0; i < kAccDigits; i++)
+            if (d[i]) atomicAdd(acc + i, neg ? (unsigned long long)(-(long long)d[i]) : d[i]);
+        return;
+    }
+    const unsigned __int128 Pm = (unsigned __int128)mant * (unsigned)coef;  // < 2^85, exact
     unsigned __int128 F;
     if (sh >= 0) {
         if (sh > 126 || (Pm >> (126 - sh)) != 0) {  // would leave the 127-bit range
