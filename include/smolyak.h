@@ -57,6 +57,8 @@ typedef enum {
 
 typedef enum { SG_FP64 = 0, SG_MIXED = 1 } sg_precision;
 
+typedef enum { SG_LANCZOS = 0, SG_DAVIDSON = 1 } sg_eig_method;
+
 /* Primitive basis of one mode: nb(l) = nb_A + nb_B * l functions at level l
  * (the level->size rule N_l = A + B l of Sec. 2), Hermite functions centred at
  * q0 with scale factor `scale` (> 0).  Requires nb_A >= 1, nb_B >= 0. */
@@ -185,6 +187,65 @@ sg_status sg_mode_tables(const sg_ctx *ctx, int mode, int level, int *nb, int *n
  * Synchronous: waits for all work on the current device.
  */
 sg_status sg_device_error(sg_ctx *ctx, int *code);
+
+/*
+ * sg_eigs -- lowest nev eigenpairs of H_S (the time-independent solvers of Sec. 3:
+ * the Davidson method; a Lanczos-type method).  Every operator application is
+ * sg_apply_H on a block of vectors; the basis, its orthogonalisation (block
+ * Gram-Schmidt twice + Cholesky QR), Ritz vectors and residuals are FP64 on
+ * the device; the projected matrix is diagonalised on the host.
+ *   method  SG_DAVIDSON: block Davidson, diagonal preconditioner
+ *           (E_k - theta)^-1 with E_k the harmonic energies of the split modes
+ *           (none when no mode is split), restart at max(3 nev, nev + 6 block)
+ *           vectors.  SG_LANCZOS: block Krylov with full reorthogonalisation and
+ *           Rayleigh-Ritz, at most 320 basis vectors; a block of size >= the
+ *           largest multiplicity resolves degenerate eigenvalues.
+ *   block   1..8 vectors per operator application (<= 0: min(nev, 8)).
+ *   tol     convergence when ||H x - theta x|| <= tol * max(1, |theta|) for the
+ *           nev lowest Ritz pairs.  max_it: iterations (blocks added).
+ *   evals   host, nev (out, ascending); resid: host, nev residual norms (may be NULL);
+ *   evecs   DEVICE, nev * N_cs (out; may be NULL).
+ * Synchronous.  SG_ENOCONV when fewer than nev pairs converged (evals, resid and
+ * evecs then hold the current approximations).  Allocates its workspace
+ * (device memory of about 2 * max(3 nev, nev + 6 block) vectors for Davidson).
+ * With a SG_MIXED context the applications are FP32-accurate; use
+ * sg_eigs_refine with a SG_FP64 context of the same problem to refine.
+ */
+sg_status sg_eigs(sg_ctx *ctx, int nev, int method, int block, double tol, int max_it, double *evals,
+                  double *evecs, double *resid, void *stream);
+
+/*
+ * sg_eigs_refine -- block Davidson started from the nev given vectors (DEVICE,
+ * nev * N_cs, in/out), on ctx's precision; used with a SG_FP64 context to bring
+ * eigenpairs converged with mixed-precision applications to FP64 accuracy.
+ * evals, resid: host (out).  Synchronous.
+ */
+sg_status sg_eigs_refine(sg_ctx *ctx, int nev, double *evecs, double *evals, double *resid, double tol,
+                         int max_it, void *stream);
+
+/*
+ * sg_propagate -- nsteps Chebyshev steps of length dt of i d/dt psi = H_S psi
+ * (the Chebyshev propagator of Sec. 3 and Sec. 5).  Per step:
+ *   psi(t+dt) = e^{-i Ebar dt} sum_{k=0}^{K} (2 - delta_k0) (-i)^k J_k(dE dt) T_k((H - Ebar)/dE) psi(t),
+ * Ebar, dE the centre and half-width of the spectral interval, estimated once
+ * from a 40-vector Krylov run and widened by the extreme Ritz residuals and 5%
+ * of the range.  K = order, reduced to the last k whose Bessel weight J_k is
+ * above 1e-17.  J_k by Miller's backward recurrence.
+ *   psi     DEVICE, 2 * N_cs doubles: real part, then imaginary part (in/out).
+ *   norm_log, energy_log: host, nsteps (may be NULL): <psi|psi> and
+ *           <psi|H|psi>/<psi|psi> at the start of each step.
+ * Synchronous.
+ */
+sg_status sg_propagate(sg_ctx *ctx, double *psi, double dt, int nsteps, int order, double *norm_log,
+                       double *energy_log, void *stream);
+
+/*
+ * sg_product_state -- psi_k = prod_i factors[i * ld + k_i] over the compact basis
+ * (compact order), on the host (out_host: N_cs doubles).  ld >= nb(L) of every
+ * mode.  Builds e.g. the displaced Gaussian (coherent state) of the propagation
+ * examples from its 1D Hermite-function coefficients.
+ */
+sg_status sg_product_state(const sg_ctx *ctx, const double *factors, int ld, double *out_host);
 
 /* Text of the last error of ctx (or of the calling thread's last sg_create
  * when ctx is NULL).  Never NULL; valid until the next call on ctx. */

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsmolyak.so")
 
 SG_OK, SG_EINVAL, SG_ENOMEM, SG_ECUDA, SG_ENOCONV, SG_ETIMEOUT, SG_EBUDGET, SG_EUNSUPPORTED = range(8)
 SG_FP64, SG_MIXED = 0, 1
+SG_LANCZOS, SG_DAVIDSON = 0, 1
 _STATUS = {0: "SG_OK", 1: "SG_EINVAL", 2: "SG_ENOMEM", 3: "SG_ECUDA", 4: "SG_ENOCONV",
            5: "SG_ETIMEOUT", 6: "SG_EBUDGET", 7: "SG_EUNSUPPORTED"}
 
@@ -68,6 +69,10 @@ SIGNATURES = {
     "sg_mode_tables": (_i32, [_vp, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                               _vp, _vp, _vp, _vp]),
     "sg_device_error": (_i32, [_vp, ctypes.POINTER(_i32)]),
+    "sg_eigs": (_i32, [_vp, _i32, _i32, _i32, _dbl, _i32, _vp, _vp, _vp, _vp]),
+    "sg_eigs_refine": (_i32, [_vp, _i32, _vp, _vp, _vp, _dbl, _i32, _vp]),
+    "sg_propagate": (_i32, [_vp, _vp, _dbl, _i32, _i32, _vp, _vp, _vp]),
+    "sg_product_state": (_i32, [_vp, _vp, _i32, _vp]),
     "sg_last_error": (ctypes.c_char_p, [_vp]),
     "sg_destroy": (None, [_vp]),
 }
@@ -261,6 +266,51 @@ def sg_device_error(ctx: Ctx) -> int:
     c = ctypes.c_int()
     _check(lib().sg_device_error(ctx.ptr, ctypes.byref(c)), ctx)
     return c.value
+
+
+def sg_eigs(ctx: Ctx, nev: int, method="davidson", block: int = 0, tol: float = 1e-8, max_it: int = 200,
+            vectors: bool = False, stream=None):
+    """Lowest nev eigenpairs.  Returns (evals, resid, evecs or None, converged)."""
+    import torch
+    m = {"lanczos": SG_LANCZOS, "davidson": SG_DAVIDSON}.get(method, method)
+    ev = np.zeros(nev); rs = np.zeros(nev)
+    vec = torch.empty(nev * ctx.n_cs, dtype=torch.float64, device="cuda") if vectors else None
+    st = lib().sg_eigs(ctx.ptr, nev, int(m), block, tol, max_it, ev.ctypes.data,
+                       vec.data_ptr() if vec is not None else None, rs.ctypes.data, _stream_ptr(stream))
+    if st not in (SG_OK, SG_ENOCONV):
+        _check(st, ctx)
+    return ev, rs, (vec.view(nev, ctx.n_cs) if vec is not None else None), st == SG_OK
+
+
+def sg_eigs_refine(ctx: Ctx, evecs, tol: float = 1e-10, max_it: int = 100, stream=None):
+    """Refine nev eigenpairs from the given device vectors (nev x N_cs, in/out).
+    Returns (evals, resid, converged)."""
+    nev = evecs.numel() // ctx.n_cs
+    _dev_ptr(evecs, nev * ctx.n_cs, "evecs")
+    ev = np.zeros(nev); rs = np.zeros(nev)
+    st = lib().sg_eigs_refine(ctx.ptr, nev, evecs.data_ptr(), ev.ctypes.data, rs.ctypes.data, tol, max_it,
+                              _stream_ptr(stream))
+    if st not in (SG_OK, SG_ENOCONV):
+        _check(st, ctx)
+    return ev, rs, st == SG_OK
+
+
+def sg_propagate(ctx: Ctx, psi, dt: float, nsteps: int, order: int = 64, stream=None):
+    """Chebyshev propagation of psi (device, 2*N_cs: real part then imaginary
+    part, in place).  Returns (norm_log, energy_log) at the start of each step."""
+    _dev_ptr(psi, 2 * ctx.n_cs, "psi")
+    nl = np.zeros(max(nsteps, 1)); el = np.zeros(max(nsteps, 1))
+    _check(lib().sg_propagate(ctx.ptr, psi.data_ptr(), dt, nsteps, order, nl.ctypes.data, el.ctypes.data,
+                              _stream_ptr(stream)), ctx)
+    return nl[:nsteps], el[:nsteps]
+
+
+def sg_product_state(ctx: Ctx, factors) -> np.ndarray:
+    """psi_k = prod_i factors[i][k_i] over the compact basis (host array)."""
+    f = np.ascontiguousarray(np.asarray(factors, np.float64))
+    out = np.zeros(ctx.n_cs)
+    _check(lib().sg_product_state(ctx.ptr, f.ctypes.data, f.shape[1], out.ctypes.data), ctx)
+    return out
 
 
 def sg_last_error(ctx: Ctx = None) -> str:

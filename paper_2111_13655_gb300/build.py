@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsmolyak.so")
-SOURCES = ["sg_setup.cpp", "sg_api.cpp", "sg_apply.cu", "sg_apply_fast.cu"]
+SOURCES = ["sg_setup.cpp", "sg_api.cpp", "sg_apply.cu", "sg_apply_fast.cu", "sg_solvers.cu", "sg_solvers_api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

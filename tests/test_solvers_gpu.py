@@ -1,0 +1,132 @@
+"""Solvers around the Smolyak action (eigenpairs, Chebyshev propagation) on the GPU.
+
+References: closed forms at zero coupling (spectrum sum_i omega_i (k_i + 1/2),
+phases e^{-i E_k t}); dense matrices assembled from the CPU oracle (literal
+Alg. 1) or the masked-Galerkin closed form, diagonalised with numpy.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2111_13655_gb300 as sg
+from oracle import galerkin
+from oracle import oracle as orc
+from paper_2111_13655_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def dense_oracle(p):
+    n = orc.n_compact(p)
+    return orc.apply_H(p, np.eye(n)).T  # column j = H e_j
+
+
+def coherent_factors(ctx, q0_mode0=2.0):
+    """1D Hermite coefficients of a Gaussian displaced by q0 in mode 0 (coherent
+    state, alpha = q0/sqrt(2)), ground state in the other modes."""
+    kw = max(int(ctx.problem.nb_A[i] + ctx.problem.nb_B[i] * ctx.problem.L) for i in range(ctx.problem.D))
+    f = np.zeros((ctx.problem.D, kw))
+    f[:, 0] = 1.0
+    a = q0_mode0 / math.sqrt(2.0)
+    f[0] = [math.exp(-a * a / 2) * a ** k / math.sqrt(math.factorial(k)) for k in range(kw)]
+    return f
+
+
+def test_lanczos_uncoupled_2d_spectrum_with_degeneracies():
+    """D=2 L=6, lambda = 0: the 10 lowest eigenvalues are n1 + n2 + 1 = 1,2,2,3,3,3,4,4,4,4."""
+    p = synth.workload_C1(lam=0.0)
+    with sg.sg_create(p, "fp64") as ctx:
+        ev, rs, _, ok = sg.sg_eigs(ctx, 10, "lanczos", block=4, tol=1e-10, max_it=20)
+    assert ok
+    assert np.max(np.abs(ev - np.array([1, 2, 2, 3, 3, 3, 4, 4, 4, 4.0]))) < 1e-10
+
+
+def test_lanczos_henon_heiles_2d_matches_oracle_matrix():
+    p = synth.workload_C1()
+    ref = np.linalg.eigvalsh(0.5 * (dense_oracle(p) + dense_oracle(p).T))[:10]
+    with sg.sg_create(p, "fp64") as ctx:
+        ev, rs, _, ok = sg.sg_eigs(ctx, 10, "lanczos", block=4, tol=1e-10, max_it=20)
+    assert ok
+    assert np.max(np.abs(ev - ref)) < 1e-10
+
+
+def test_davidson_6d_matches_oracle_matrix():
+    p = synth.workload_C2()
+    H = dense_oracle(p)
+    ref = np.linalg.eigvalsh(0.5 * (H + H.T))[:10]
+    with sg.sg_create(p, "fp64") as ctx:
+        ev, rs, vec, ok = sg.sg_eigs(ctx, 10, "davidson", block=4, tol=1e-9, max_it=300, vectors=True)
+    assert ok
+    assert np.max(np.abs(ev - ref)) < 1e-9
+    assert np.all(rs <= 1e-9 * np.maximum(1.0, np.abs(ev)))
+
+
+def test_mixed_davidson_then_fp64_refinement_reaches_1e8():
+    """D=12 L=4 nq=l+2 (the benchmark's rules at a size with a dense reference):
+    20 lowest eigenvalues by block Davidson (block 8) with FP32 contractions,
+    then refined with FP64 applications to <= 1e-8 of the exact values."""
+    p = synth.workload_C3(L=4)
+    n = orc.n_compact(p)
+    H = galerkin.apply_H(p, np.eye(n)).T
+    ref = np.linalg.eigvalsh(0.5 * (H + H.T))[:20]
+    with sg.sg_create(p, "mixed") as cm, sg.sg_create(p, "fp64") as cd:
+        ev, rs, vec, ok = sg.sg_eigs(cm, 20, "davidson", block=8, tol=1e-5, max_it=300, vectors=True)
+        assert ok
+        mixed_err = np.max(np.abs(ev - ref))
+        ev2, rs2, ok2 = sg.sg_eigs_refine(cd, vec.contiguous().view(-1), tol=1e-10, max_it=200)
+    assert ok2
+    assert mixed_err < 1e-4
+    assert np.max(np.abs(ev2 - ref)) < 1e-8
+
+
+def test_chebyshev_uncoupled_matches_closed_form_phases():
+    """lambda = 0, D=6 L=8: psi_k(t) = psi_k(0) exp(-i E_k t) exactly in the truncated space;
+    norm and energy constant."""
+    om = synth.draw_omega(6, 2)
+    p = synth.chained_henon_heiles(6, 8, om, 0.0)
+    K = orc.enumerate_compact(6, 8)
+    E = (K + 0.5) @ om
+    with sg.sg_create(p, "fp64") as ctx:
+        psi0 = sg.sg_product_state(ctx, coherent_factors(ctx))
+        psi0 /= np.linalg.norm(psi0)
+        psi = torch.from_numpy(np.concatenate([psi0, np.zeros_like(psi0)])).cuda()
+        nl, el = sg.sg_propagate(ctx, psi, 0.1, 20, order=64)
+        out = psi.cpu().numpy()
+    t = 20 * 0.1
+    exact = psi0 * np.exp(-1j * E * t)
+    got = out[:len(psi0)] + 1j * out[len(psi0):]
+    assert np.max(np.abs(got - exact)) < 1e-10
+    assert np.max(np.abs(nl - 1.0)) < 1e-12
+    assert np.max(np.abs(el - el[0])) < 1e-11
+
+
+def test_chebyshev_coupled_2d_matches_exact_propagator():
+    p = synth.workload_C1()
+    H = dense_oracle(p)
+    w, U = np.linalg.eigh(0.5 * (H + H.T))
+    with sg.sg_create(p, "fp64") as ctx:
+        psi0 = sg.sg_product_state(ctx, coherent_factors(ctx, 1.0))
+        psi0 /= np.linalg.norm(psi0)
+        psi = torch.from_numpy(np.concatenate([psi0, np.zeros_like(psi0)])).cuda()
+        nl, el = sg.sg_propagate(ctx, psi, 0.1, 30, order=64)
+        out = psi.cpu().numpy()
+    exact = U @ (np.exp(-1j * w * 3.0) * (U.T @ psi0))
+    got = out[:len(psi0)] + 1j * out[len(psi0):]
+    assert np.max(np.abs(got - exact)) < 1e-10
+    assert np.max(np.abs(nl - 1.0)) < 1e-12
+    assert np.max(np.abs(el - psi0 @ H @ psi0)) < 1e-11
+
+
+def test_chebyshev_6d_conserves_norm_and_energy():
+    """The 6D propagation configuration (order 64, dt 0.1), 50 steps."""
+    p = synth.workload_C2()
+    with sg.sg_create(p, "fp64") as ctx:
+        psi0 = sg.sg_product_state(ctx, coherent_factors(ctx, 2.0))
+        psi0 /= np.linalg.norm(psi0)
+        psi = torch.from_numpy(np.concatenate([psi0, np.zeros_like(psi0)])).cuda()
+        nl, el = sg.sg_propagate(ctx, psi, 0.1, 50, order=64)
+    assert np.max(np.abs(nl - 1.0)) < 1e-11
+    assert np.max(np.abs(el - el[0])) < 1e-10
