@@ -138,6 +138,31 @@ sg_status sg_apply_H_host(sg_ctx *ctx, const double *x_host, double *y_host, int
                           void *stream);
 
 /*
+ * sg_apply_H_noalloc -- the operation of sg_apply_H, with the same arguments
+ * and results, for callers that may not allocate device memory when they
+ * apply H (e.g. a process whose device memory is all held by another
+ * allocator, or a loop that cannot take the synchronisation a cudaMalloc may
+ * bring).  It is not part of the method of the paper, which has no counterpart.
+ *   The fixed-point accumulators and per-vector exponents that sg_apply_H
+ *   keeps in context-owned device memory come here from one array of
+ *   SG_NOALLOC_SCRATCH_BYTES compiled into the library; every GPU that loads
+ *   the library holds it until the process exits.  The call allocates nothing.
+ *   Limits: nvec <= SG_NOALLOC_MAX_NVEC and nvec * N_cs <= SG_NOALLOC_MAX_ELEMS;
+ *   larger requests return SG_EUNSUPPORTED with the limits in sg_last_error.
+ *   The context's device must be the current device (else SG_EINVAL).  The
+ *   first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) and remembers it; make that first call before any
+ *   stream capture.  Each call clears the part of the array it uses on
+ *   `stream` first.  All calls on one device share the array: calls whose GPU
+ *   work overlaps (other streams, threads or contexts) race and give wrong
+ *   results; order them.  x, y: DEVICE, as for sg_apply_H.  Enqueued on `stream`.
+ */
+#define SG_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
+#define SG_NOALLOC_MAX_NVEC 64
+#define SG_NOALLOC_MAX_ELEMS 524272
+sg_status sg_apply_H_noalloc(sg_ctx *ctx, const double *x, double *y, int nvec, void *stream);
+
+/*
  * sg_term_levels -- levels l of terms [t0, t0+nt) in Table-2 order, D ints per
  * term, into levels_host (nt*D ints), and their combination coefficients D_l
  * (Eq. (8)) into coef_host (nt ints, may be NULL).

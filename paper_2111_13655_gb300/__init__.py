@@ -63,6 +63,7 @@ SIGNATURES = {
     "sg_size": (_i32, [_vp, _P64, _P64, _P64, _P64, _P64]),
     "sg_apply_H": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "sg_apply_H_host": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "sg_apply_H_noalloc": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "sg_term_levels": (_i32, [_vp, _i64, _i64, _vp, _vp]),
     "sg_index_map": (_i32, [_vp, _i64, _i64, _vp, _vp, _vp]),
     "sg_compact_rank": (_i32, [_vp, _vp, _i64, _vp]),
@@ -199,6 +200,18 @@ def sg_apply_H(ctx: Ctx, x, y, nvec: int = None, stream=None) -> None:
     xp = _dev_ptr(x, nvec * ctx.n_cs, "x")
     yp = _dev_ptr(y, nvec * ctx.n_cs, "y")
     _check(lib().sg_apply_H(ctx.ptr, xp, yp, int(nvec), _stream_ptr(stream)), ctx)
+
+
+def sg_apply_H_noalloc(ctx: Ctx, x, y, nvec: int = None, stream=None) -> None:
+    """y = H_S x like sg_apply_H, for callers that may not allocate device
+    memory at this point: the apply's scratch comes from a fixed 16 MiB array
+    in the library (nvec <= 64, nvec * N_cs <= 524272).  Calls that overlap on
+    the GPU share that array and race."""
+    if nvec is None:
+        nvec = x.numel() // ctx.n_cs
+    xp = _dev_ptr(x, nvec * ctx.n_cs, "x")
+    yp = _dev_ptr(y, nvec * ctx.n_cs, "y")
+    _check(lib().sg_apply_H_noalloc(ctx.ptr, xp, yp, int(nvec), _stream_ptr(stream)), ctx)
 
 
 def sg_apply_H_host(ctx: Ctx, x_host, y_host, nvec: int = None, stream=None) -> None:

@@ -18,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsmolyak.so")
-SOURCES = ["sg_setup.cpp", "sg_api.cpp", "sg_apply.cu", "sg_apply_fast.cu", "sg_solvers.cu", "sg_solvers_api.cpp"]
+SOURCES = ["sg_setup.cpp", "sg_api.cpp", "sg_apply.cu", "sg_apply_fast.cu", "sg_solvers.cu", "sg_solvers_api.cpp",
+           "sg_apply_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
