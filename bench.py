@@ -39,6 +39,9 @@ WORKLOAD = "chained Henon-Heiles D=12 L=10 nb=l+1 nq=l+2 (N_cs=646646, 646646 te
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # FP64: the nominal GB300 rate (1.25 TFLOP/s); the FMA microbenchmark is reported beside it
 FP64_PEAK_TFLOPS = 1.25
+# kernels of one sg_apply_H at this workload: k_maxabs, k_apply_fast (block form
+# over the large terms), k_apply_fast (warp form over the small terms), k_finalize
+LAUNCHES_PER_APPLY = 4
 
 
 def algorithmic_flops_per_vector(levels: np.ndarray, nbA=1, nbB=1, nqA=2, nqB=1) -> int:
@@ -168,6 +171,45 @@ def run_reference(args):
     return 0
 
 
+class Replicas:
+    """N > 1: one independent replica per rank (no collective on the data path);
+    only the timing is combined: a barrier around each timed region and the
+    maximum of the ranks' times.  `backend` "nccl" on GPUs, "gloo" on CPU."""
+
+    def __init__(self, backend: str):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.dist = None
+        self.device = "cuda" if backend == "nccl" else "cpu"
+        if self.world > 1:
+            import torch.distributed as dist
+            if not dist.is_initialized():
+                dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+    def max_over_ranks(self, value: float) -> float:
+        if self.dist is None:
+            return float(value)
+        import torch
+        t = torch.tensor([float(value)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def replica_throughput(world: int, units_per_rank: int, slowest_seconds: float) -> float:
+    """Whole-job rate: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / slowest_seconds
+
+
 def time_device(ctx, xd, yd, nvec, steps, warmup, flush, torch, sg):
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
@@ -202,18 +244,11 @@ def main():
     import paper_2111_13655_gb300 as sg
     from paper_2111_13655_gb300 import synth
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
+    rep = Replicas("nccl")
+    world, rank = rep.world, rep.rank
+    barrier = rep.barrier
 
     # CPU baseline before any GPU work on rank 0 (the oracle's OpenMP pool
     # starts in this process; no fork happens after CUDA initialisation).
@@ -242,11 +277,7 @@ def main():
             times = time_device(ctx, xd, yd, nvec, steps, warm, flush, torch, sg)
         barrier()
         torch.cuda.synchronize()
-        total_ms = sum(times)
-        if dist is not None:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = rep.max_over_ranks(sum(times))
         derr = sg.sg_device_error(ctx)
         if derr:
             raise RuntimeError(f"device error code {derr} in the {prec} apply")
@@ -256,7 +287,7 @@ def main():
         peak = FP32_PEAK_TFLOPS if prec == "mixed" else FP64_PEAK_TFLOPS
         achieved = f_alg / (statistics.mean(times) * 1e-3) / 1e12
         results[prec] = {
-            "value": world * nvec * steps / (total_ms * 1e-3), "ms_per_step": ms, "steps": steps,
+            "value": replica_throughput(world, nvec * steps, total_ms * 1e-3), "ms_per_step": ms, "steps": steps,
             "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
@@ -275,12 +306,8 @@ def main():
             t0 = time.perf_counter()
             for _ in range(args.steps):
                 sg.sg_apply_H_host(ctx, xh, yh, nvec)
-            e2e_s = time.perf_counter() - t0
-            if dist is not None:
-                t = torch.tensor([e2e_s], device="cuda")
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                e2e_s = float(t.item())
-            results[prec]["e2e"] = {"value": world * nvec * args.steps / e2e_s, "unit": UNIT,
+            e2e_s = rep.max_over_ranks(time.perf_counter() - t0)
+            results[prec]["e2e"] = {"value": replica_throughput(world, nvec * args.steps, e2e_s), "unit": UNIT,
                                     "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(x.nbytes)}
         sg.sg_destroy(ctx)
         del xd, yd, flush
@@ -296,13 +323,12 @@ def main():
                            "vectors_per_step": nvec, "parallelism": f"replicas x{world}",
                            "l2": "flushed between timed steps (256 MB write)"},
                 "latency_ms": m["latency_ms"], "roofline": m["roofline"], "clocks": m["clocks"],
-                "e2e": m["e2e"], "gpu_launches": m["steps"],
+                "e2e": m["e2e"], "gpu_launches": LAUNCHES_PER_APPLY * m["steps"],
                 "fp64": {"value": f["value"], "unit": UNIT, "ms_per_step": f["ms_per_step"], "steps": f["steps"],
                          "latency_ms": f["latency_ms"], "roofline": f["roofline"], "clocks": f["clocks"]},
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    rep.close()
     return 0
 
 
