@@ -163,6 +163,36 @@ sg_status sg_apply_H_host(sg_ctx *ctx, const double *x_host, double *y_host, int
 sg_status sg_apply_H_noalloc(sg_ctx *ctx, const double *x, double *y, int nvec, void *stream);
 
 /*
+ * Batches: y_j = H_S^(j) x_j for many independent problems j in one apply
+ * (Eq. (16) per problem).  The terms of every problem are independent work
+ * (Sec. 3: the term loop of Alg. 1 and its parallel schemes), so the terms of
+ * all problems that share a kernel variant run in one launch per form (block /
+ * warp), ordered by estimated cost over all problems; small problems fill the
+ * gaps that large ones leave.  Problems outside the fast path (potentials with
+ * monomials over three or more modes) get one launch each.
+ *
+ * sg_batch_create -- n (1..65535) contexts made by sg_create on the current
+ *   device, all of one precision (else SG_EINVAL).  The batch borrows their
+ *   device tables: destroy it before any of them.  The contexts' own
+ *   workspaces are not used, so sg_apply_H on a member stays valid.
+ * sg_batch_size -- total N_cs and terms over the problems; kernel launches
+ *   of one sg_apply_H_batch.
+ * sg_apply_H_batch -- x, y: DEVICE, problem after problem, problem j's nvec
+ *   vectors (each N_cs^(j) doubles, column after column) starting at
+ *   nvec * (N_cs^(0) + ... + N_cs^(j-1)).  y is overwritten; x and y must not
+ *   overlap.  1 <= nvec <= 65535.  Results are bitwise those of sg_apply_H
+ *   on each context.  The batch owns its workspace (fixed-point accumulators,
+ *   32 bytes per vector entry), grown on the first call with a larger nvec.
+ *   Enqueued on `stream`.
+ */
+typedef struct sg_batch sg_batch;
+sg_status sg_batch_create(sg_ctx *const *ctxs, int n, sg_batch **out);
+sg_status sg_batch_size(const sg_batch *b, int64_t *n_cs_total, int64_t *n_terms_total, int *launches_per_apply);
+sg_status sg_apply_H_batch(sg_batch *b, const double *x, double *y, int nvec, void *stream);
+const char *sg_batch_last_error(const sg_batch *b);
+void sg_batch_destroy(sg_batch *b);
+
+/*
  * sg_term_levels -- levels l of terms [t0, t0+nt) in Table-2 order, D ints per
  * term, into levels_host (nt*D ints), and their combination coefficients D_l
  * (Eq. (8)) into coef_host (nt ints, may be NULL).

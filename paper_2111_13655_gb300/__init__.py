@@ -75,6 +75,11 @@ SIGNATURES = {
     "sg_propagate": (_i32, [_vp, _vp, _dbl, _i32, _i32, _vp, _vp, _vp]),
     "sg_product_state": (_i32, [_vp, _vp, _i32, _vp]),
     "sg_last_error": (ctypes.c_char_p, [_vp]),
+    "sg_batch_create": (_i32, [_vp, _i32, ctypes.POINTER(_vp)]),
+    "sg_batch_size": (_i32, [_vp, _P64, _P64, ctypes.POINTER(_i32)]),
+    "sg_apply_H_batch": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "sg_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "sg_batch_destroy": (None, [_vp]),
     "sg_destroy": (None, [_vp]),
 }
 
@@ -324,6 +329,58 @@ def sg_product_state(ctx: Ctx, factors) -> np.ndarray:
     out = np.zeros(ctx.n_cs)
     _check(lib().sg_product_state(ctx.ptr, f.ctypes.data, f.shape[1], out.ctypes.data), ctx)
     return out
+
+
+class Batch:
+    """Owner of one sg_batch* over several contexts (kept alive by this object).
+    Vectors of problem j start at nvec * offsets[j] in the batched buffers."""
+
+    def __init__(self, ptr: int, ctxs):
+        self.ptr = ptr
+        self.ctxs = list(ctxs)
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        _check(lib().sg_batch_size(ptr, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        self.n_cs_total, self.n_terms_total, self.launches_per_apply = a.value, b.value, c.value
+        self.offsets = np.concatenate([[0], np.cumsum([c.n_cs for c in self.ctxs])]).astype(np.int64)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        sg_batch_destroy(self)
+
+    def __del__(self):
+        try:
+            sg_batch_destroy(self)
+        except Exception:
+            pass
+
+
+def sg_batch_create(ctxs) -> Batch:
+    """One batched operator over contexts of one device and precision."""
+    arr = (_vp * len(ctxs))(*[c.ptr for c in ctxs])
+    out = _vp()
+    st = lib().sg_batch_create(arr, len(ctxs), ctypes.byref(out))
+    if st != SG_OK:
+        raise SgError(st, "sg_batch_create: contexts must be device contexts of the current device and one "
+                          "precision, 1..65535 of them")
+    return Batch(out.value, ctxs)
+
+
+def sg_apply_H_batch(b: Batch, x, y, nvec: int, stream=None) -> None:
+    """y_j = H_j x_j for every problem j (device float64 tensors of nvec * sum N_cs
+    elements, problem after problem)."""
+    xp = _dev_ptr(x, nvec * b.n_cs_total, "x")
+    yp = _dev_ptr(y, nvec * b.n_cs_total, "y")
+    st = lib().sg_apply_H_batch(b.ptr, xp, yp, int(nvec), _stream_ptr(stream))
+    if st != SG_OK:
+        raise SgError(st, (lib().sg_batch_last_error(b.ptr) or b"").decode(errors="replace"))
+
+
+def sg_batch_destroy(b: Batch) -> None:
+    if b is not None and getattr(b, "ptr", None):
+        lib().sg_batch_destroy(b.ptr)
+        b.ptr = None
 
 
 def sg_last_error(ctx: Ctx = None) -> str:

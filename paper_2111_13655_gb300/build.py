@@ -18,8 +18,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsmolyak.so")
-SOURCES = ["sg_setup.cpp", "sg_api.cpp", "sg_apply.cu", "sg_apply_fast.cu", "sg_solvers.cu", "sg_solvers_api.cpp",
-           "sg_apply_noalloc.cu"]
+# the four fast-path instantiation units take the longest and go first
+SOURCES = ["sg_fast_f32.cu", "sg_fast_f64.cu", "sg_fast_batch_f32.cu", "sg_fast_batch_f64.cu",
+           "sg_setup.cpp", "sg_api.cpp", "sg_apply.cu", "sg_apply_fast.cu", "sg_solvers.cu", "sg_solvers_api.cpp",
+           "sg_apply_noalloc.cu", "sg_batch.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -31,7 +33,7 @@ def nvcc() -> str:
 
 
 def _deps() -> list:
-    inc = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    inc = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     inc.append(os.path.join(ROOT, "include", "smolyak.h"))
     return inc
 
@@ -44,8 +46,6 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
         return obj
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
            "-I", os.path.join(ROOT, "include"), "-c", path, "-o", obj + ".tmp"]
-    if src.endswith(".cpp"):
-        cmd[1:1] = ["-x", "cu"] if False else []
     if verbose_ptxas and src.endswith(".cu"):
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

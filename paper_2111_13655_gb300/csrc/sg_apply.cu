@@ -396,6 +396,24 @@ __global__ void k_maxabs(const double *__restrict__ x, int n, long long *__restr
     if ((threadIdx.x & 31) == 0 && mb) atomicMax(maxbits + v, mb);
 }
 
+// The accumulated integer of one entry times 2^E (E from the vector's max|x|
+// bits; NaN when x held a non-finite value); clears the accumulator words.
+__device__ __forceinline__ double finalize_value(unsigned long long *a, long long mb)
+{
+    unsigned __int128 tot = 0;
+#pragma unroll
+    for (int d = 0; d < kAccDigits; d++) {
+        const __int128 dv = (__int128)(long long)a[d];
+        tot += (unsigned __int128)dv << (32 * d);
+        a[d] = 0ull;
+    }
+    const __int128 st = (__int128)tot;
+    const long long hi = (long long)(st >> 64);
+    const unsigned long long lo = (unsigned long long)tot;
+    const double val = scalbn((double)hi, 64) + (double)lo;
+    return ((mb >> 52) & 0x7FF) == 0x7FF ? __longlong_as_double(0x7FF8000000000000ll) : scalbn(val, lsb_exponent(mb));
+}
+
 // y = (accumulated integer) * 2^E + esplit * x; clears the accumulators
 __global__ void k_finalize(const KParams P, const double *__restrict__ x, double *__restrict__ y,
                            const long long *__restrict__ maxbits, int nvec)
@@ -404,22 +422,49 @@ __global__ void k_finalize(const KParams P, const double *__restrict__ x, double
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int v = (int)(i / P.n_cs);
         const size_t r = i - (size_t)v * P.n_cs;
-        unsigned long long *a = P.acc + i * kAccDigits;
-        unsigned __int128 tot = 0;
-#pragma unroll
-        for (int d = 0; d < kAccDigits; d++) {
-            const __int128 dv = (__int128)(long long)a[d];
-            tot += (unsigned __int128)dv << (32 * d);
-            a[d] = 0ull;
+        y[i] = finalize_value(P.acc + i * kAccDigits, maxbits[v]) + P.esplit[r] * x[i];
+    }
+}
+
+// Many problems (vectors problem after problem, problem j from nvec * cs_prefix[j]):
+// per-vector max|x| bits into maxbits[j * nvec + v]; blockIdx.z = problem.
+__global__ void k_maxabs_batch(const double *__restrict__ x, const long long *__restrict__ cs_prefix, int nvec,
+                               long long *__restrict__ maxbits)
+{
+    const int j = blockIdx.z, v = blockIdx.y;
+    const long long c0 = cs_prefix[j];
+    const long long n = cs_prefix[j + 1] - c0;
+    const double *xv = x + (size_t)nvec * c0 + (size_t)v * n;
+    long long mb = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long b = __double_as_longlong(xv[i]) & 0x7FFFFFFFFFFFFFFFll;
+        mb = b > mb ? b : mb;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long other = __shfl_xor_sync(0xffffffffu, mb, o);
+        mb = other > mb ? other : mb;
+    }
+    if ((threadIdx.x & 31) == 0 && mb) atomicMax(maxbits + (size_t)j * nvec + v, mb);
+}
+
+// Many problems: y = (accumulated integer) * 2^E + esplit_j * x, entry by entry
+// over all problems' vectors; clears the accumulators.
+__global__ void k_finalize_batch(const KParams *__restrict__ kps, const long long *__restrict__ cs_prefix,
+                                 int nprob, const double *__restrict__ x, double *__restrict__ y,
+                                 unsigned long long *acc, const long long *__restrict__ maxbits, int nvec)
+{
+    const size_t total = (size_t)nvec * (size_t)cs_prefix[nprob];
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nprob - 1;  // last problem whose block starts at or before g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((size_t)nvec * (size_t)cs_prefix[mid] <= g) lo = mid; else hi = mid - 1;
         }
-        const __int128 st = (__int128)tot;
-        const long long hi = (long long)(st >> 64);
-        const unsigned long long lo = (unsigned long long)tot;
-        const double val = scalbn((double)hi, 64) + (double)lo;
-        const long long mb = maxbits[v];
-        const double out = ((mb >> 52) & 0x7FF) == 0x7FF ? __longlong_as_double(0x7FF8000000000000ll)
-                                                          : scalbn(val, lsb_exponent(mb));
-        y[i] = out + P.esplit[r] * x[i];
+        const size_t n = (size_t)(cs_prefix[lo + 1] - cs_prefix[lo]);
+        const size_t i = g - (size_t)nvec * (size_t)cs_prefix[lo];
+        const int v = (int)(i / n);
+        const size_t r = i - (size_t)v * n;
+        y[g] = finalize_value(acc + g * kAccDigits, maxbits[(size_t)lo * nvec + v]) + kps[lo].esplit[r] * x[g];
     }
 }
 
@@ -488,6 +533,40 @@ cudaError_t launch_apply(const KParams &kp, bool fp32, const double *x, double *
     const size_t total = (size_t)nvec * kp.n_cs;
     const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 16);
     k_finalize<<<blocks, 256, 0, stream>>>(kp, x, y, maxbits, nvec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_terms(const KParams &kp, bool fp32, const double *x, const long long *maxbits, int nvec,
+                               cudaStream_t stream)
+{
+    if (kp.fast.enabled) return launch_apply_fast(kp, fp32, x, nvec, maxbits, stream);
+    if (kp.n_terms == 0) return cudaSuccess;
+    const size_t smem = apply_smem_bytes(kp, fp32);
+    dim3 grid((unsigned)kp.n_terms);
+    if (fp32)
+        k_apply<float><<<grid, kThreads, smem, stream>>>(kp, x, maxbits, nvec);
+    else
+        k_apply<double><<<grid, kThreads, smem, stream>>>(kp, x, maxbits, nvec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_maxabs_batch(const double *x, const long long *cs_prefix, int nprob, int64_t max_ncs, int nvec,
+                                long long *maxbits, cudaStream_t stream)
+{
+    cudaError_t e = cudaMemsetAsync(maxbits, 0, sizeof(long long) * (size_t)nprob * nvec, stream);
+    if (e != cudaSuccess) return e;
+    const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (max_ncs + 255) / 256));
+    k_maxabs_batch<<<dim3(bx, nvec, nprob), 256, 0, stream>>>(x, cs_prefix, nvec, maxbits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batch(const KParams *kps, const long long *cs_prefix, int nprob, int64_t total_cs,
+                                  const double *x, double *y, unsigned long long *acc, const long long *maxbits,
+                                  int nvec, cudaStream_t stream)
+{
+    const size_t total = (size_t)nvec * (size_t)total_cs;
+    const unsigned blocks = (unsigned)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, 152 * 16));
+    k_finalize_batch<<<blocks, 256, 0, stream>>>(kps, cs_prefix, nprob, x, y, acc, maxbits, nvec);
     return cudaGetLastError();
 }
 

@@ -1,157 +1,11 @@
-// Smolyak operator action, fast path (sm_103a): potentials whose monomials
-// touch at most two modes (the Henon-Heiles family of Sec. 4, Eq. (18)).
-//
-// One thread block per Smolyak term, terms ordered most-expensive first.  The
-// term operator (Alg. 1 of arXiv 2111.13655 with the grid operator split as
-// described in build_fast_tables) is
-//     y_l = c0 x_l + sum_j H1_j x_l + (x B^T W) diag(V_l) (x B) x_l,
-// V_l(u) = sum over the term's active coupled pairs of G_p(u_a, u_b).
-// The basis->grid (Eq. (15)) and grid->basis (Eq. (14)) transfers run mode by
-// mode.
-//
-// Layout of a term tensor: [i][v][o] -- i runs over the "inner" slots (up to
-// RMAX slots of level 1, the slowest positions), v over a chunk of vectors,
-// o over the "outer" slots in mode order (last fastest).  Outer slots are
-// contracted breadth-first in shared memory with the 1D matrix in registers,
-// one (fibre, vector) per thread; the inner slots, the potential and their
-// back-transfer run in registers, one outer grid point per thread, the
-// potential evaluated once for all vectors of the chunk.  Vectors are batched
-// inside every phase, so block-wide barriers are shared by the whole chunk.
-// The compress-add of D_l * y_l into the compact result is the exact
-// fixed-point sum of sg_fixed.cuh.
-#include <algorithm>
-#include <cstdint>
-
-#include "sg_fixed.cuh"
-#include "sg_internal.h"
+// Fast path of the Smolyak operator action: per-context set-up kernels and
+// the host entry points; the term kernels are in sg_fast.cuh, instantiated by
+// sg_fast_f32.cu and sg_fast_f64.cu.
+#include "sg_fast.cuh"
 
 namespace sg {
 
 namespace {
-
-constexpr int kFT = 128;   // threads per term block
-constexpr int kMaxVB = 8;  // vectors per chunk
-
-struct FHdr {
-    int m, R, NB, NBo, grid, bad, coef;
-    int s, vb, NBO, NBrest, NBIn, nslice, NGs;
-    int npair, nind, gsize;
-    double c0;
-    long long rank_off;
-    int mode[kMaxD], nb[kMaxD], nq[kMaxD];               // by layout position
-    int ostride[kMaxD];                                  // stride of a position inside its block (i or o)
-    unsigned smag[kMaxD], bmag[kMaxD];                   // reciprocals of ostride and nb
-    int oB[kMaxD], oBW[kMaxD], oH[kMaxD];                // shared-memory offsets of B, B^T W, H1
-    int gstride[kMaxD];                                  // outer grid strides inside a slice
-    unsigned gmag[kMaxD], qmag[kMaxD];                   // reciprocals of gstride and nq
-    int bymode[kMaxD];                                   // positions sorted by mode
-    int gB[kMaxD], gBW[kMaxD], gH1[kMaxD];               // global offsets of B, B^T W, H1 base
-    int uS[kMaxD];                                       // slice indices of the sliced positions
-    int pg[kMaxPairs], pgg[kMaxPairs], ioffs[kMaxPairs]; // G offsets (shared, global), induced offsets
-    unsigned char pa[kMaxPairs], pb[kMaxPairs], ipos[kMaxPairs];
-};
-constexpr int kHdrBytes = 4096;  // per-group header budget the host plans with
-static_assert(sizeof(FHdr) <= kHdrBytes, "term header too large");
-
-template <int GS>
-__device__ __forceinline__ void gsync()
-{
-    if (GS == 32) __syncwarp(); else __syncthreads();
-}
-
-// floor(x / d) for x * d < 2^32, via a 32-bit reciprocal (mag = ceil(2^32 / d), d > 1)
-__device__ __forceinline__ unsigned rmag(unsigned d) { return d <= 1 ? 0u : 0xFFFFFFFFu / d + 1u; }
-__device__ __forceinline__ int fdiv(int x, int d, unsigned mag)
-{
-    return d == 1 ? x : (int)__umulhi((unsigned)x, mag);
-}
-
-__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
-
-template <typename T> struct FTab;
-template <> struct FTab<double> {
-    static __device__ const double *f(const KParams &P) { return P.fast.tabd; }
-    static __device__ const double *t(const KParams &P) { return P.tabd; }
-};
-template <> struct FTab<float> {
-    static __device__ const float *f(const KParams &P) { return P.fast.tabf; }
-    static __device__ const float *t(const KParams &P) { return P.tabf; }
-};
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Per-term set-up from the term's record (built on the host): warp 0 copies
-// the record to shared memory and parses it, lane 0 derives the layout.
-__device__ void load_record(const KParams &P, int p, int4 *buf, FHdr &H)
-{
-    const int lane = threadIdx.x & 31;
-    const unsigned lo = P.fast.desc_off[p], hi = P.fast.desc_off[p + 1];
-    for (unsigned u = lo + lane; u < hi; u += 32) buf[u - lo] = P.fast.desc[u];
-    __syncwarp();
-    const FDescHdr *hd = reinterpret_cast<const FDescHdr *>(buf);
-    const int m = hd->m, np = hd->npair, ni = hd->nind;
-    const FDescPos *ps = reinterpret_cast<const FDescPos *>(buf + 3);
-    const FDescPair *pr = reinterpret_cast<const FDescPair *>(buf + 3 + m);
-    const FDescInd *in = reinterpret_cast<const FDescInd *>(buf + 3 + m + np);
-    for (int j = lane; j < m; j += 32) {
-        H.mode[j] = ps[j].mode; H.nb[j] = ps[j].nb; H.nq[j] = ps[j].nq;
-        H.gB[j] = ps[j].offB; H.gBW[j] = ps[j].offBW; H.gH1[j] = ps[j].offH1;
-    }
-    for (int q = lane; q < np; q += 32) { H.pa[q] = pr[q].pa; H.pb[q] = pr[q].pb; H.pg[q] = pr[q].gsm; H.pgg[q] = pr[q].goff; }
-    for (int q = lane; q < ni; q += 32) { H.ipos[q] = in[q].pos; H.ioffs[q] = in[q].ioff; }
-    if (lane == 0) {
-        H.m = m; H.R = hd->R; H.NB = hd->NB; H.coef = hd->coef; H.s = hd->s;
-        H.npair = np; H.nind = ni; H.gsize = hd->gsize; H.c0 = hd->c0; H.rank_off = hd->rank_off;
-        H.grid = np > 0;
-    }
-    __syncwarp();
-}
-
-// Layout quantities of the term, shared memory only: lane j handles position j.
-__device__ void derive_layout(const KParams &P, int nvec, int work, FHdr &H)
-{
-    const int lane = threadIdx.x & 31;
-    const int m = H.m, R = H.R, sv = H.s;
-    if (lane < m) {
-        const int j = lane, nb = H.nb[j], nq = H.nq[j];
-        int off = 0, st = 1, gs = 1, rank = 0;
-        for (int i = 0; i < j; i++) off += 2 * H.nq[i] * H.nb[i] + H.nb[i] * H.nb[i];
-        const int end = j < R ? R : m;
-        for (int i = j + 1; i < end; i++) st *= H.nb[i];
-        for (int i = j + 1; i < m; i++) gs *= H.nq[i];
-        for (int i = 0; i < m; i++) rank += H.mode[i] < H.mode[j];
-        H.oB[j] = off; H.oBW[j] = off + nq * nb; H.oH[j] = off + 2 * nq * nb;
-        H.bmag[j] = rmag(nb); H.qmag[j] = rmag(nq);
-        H.ostride[j] = st; H.smag[j] = rmag(st);
-        H.gstride[j] = gs; H.gmag[j] = rmag(gs);
-        H.bymode[rank] = j;
-    }
-    __syncwarp();
-    if (lane != 0) return;
-    H.bad = 0;
-    int mat = 0, NBIn = 1;
-    int64_t stage = 1;
-    H.NBO = 1; H.nslice = 1; H.NBrest = 1; H.NGs = 1;
-    for (int j = 0; j < m; j++) {
-        mat += 2 * H.nq[j] * H.nb[j] + H.nb[j] * H.nb[j];
-        if (j < R) NBIn *= H.nb[j];
-        else if (j < R + sv) { H.NBO *= H.nb[j]; H.nslice *= H.nq[j]; }
-        else { H.NBrest *= H.nb[j]; H.NGs *= H.nq[j]; stage *= H.nq[j]; }
-    }
-    if (mat > P.matcap || H.gsize > P.fast.gcap || H.NBO > P.fast.nbocap) { H.bad = 1; return; }
-    H.NBIn = NBIn; H.NBo = H.NB / NBIn;
-    stage *= NBIn;
-    const int64_t per_vec = 2 * (int64_t)H.NB + (H.grid ? 2 * stage : 0);
-    if (per_vec > work) { H.bad = 2; return; }
-    int vb = nvec < kMaxVB ? nvec : kMaxVB;
-    while (vb > 1 && per_vec * vb > work) vb--;
-    H.vb = vb;
-}
 
 // M^B in layout order: compact index of every basis function of every term
 // (built once per context; the same partial-rank arithmetic as the generic kernel).
@@ -182,443 +36,6 @@ __global__ void __launch_bounds__(kFT) k_build_ranks(const KParams P, int *__res
     }
 }
 
-// out[a][r][c] = sum_k M[r][k] in[a][k][c], matrix in registers, one fibre (a, c) per thread
-template <typename T, int N, int RR, int GS>
-__device__ __forceinline__ void fcontract_t(const T *__restrict__ in, T *__restrict__ out, int A, int C,
-                                            const T *__restrict__ M, int tid)
-{
-    T mr[RR * N];
-#pragma unroll
-    for (int i = 0; i < RR * N; i++) mr[i] = M[i];
-    const int total = A * C;
-    const unsigned mag = rmag(C);
-    for (int f = tid; f < total; f += GS) {
-        const int a = fdiv(f, C, mag), c = f - a * C;
-        const T *ip = in + a * N * C + c;
-        T *op = out + a * RR * C + c;
-        T xv[N];
-#pragma unroll
-        for (int k = 0; k < N; k++) xv[k] = ip[k * C];
-#pragma unroll
-        for (int r = 0; r < RR; r++) {
-            T acc = T(0);
-#pragma unroll
-            for (int k = 0; k < N; k++) acc = fma_t(mr[r * N + k], xv[k], acc);
-            op[r * C] = acc;
-        }
-    }
-}
-
-template <typename T, int GS>
-__device__ void fcontract_rt(const T *__restrict__ in, T *__restrict__ out, int A, int n, int r, int C,
-                             const T *__restrict__ M, int tid)
-{
-    const int total = A * r * C;
-    for (int e = tid; e < total; e += GS) {
-        const int c = e % C, tq = e / C, rr = tq % r, a = tq / r;
-        const T *ip = in + (a * n) * C + c;
-        const T *mp = M + rr * n;
-        T acc = T(0);
-        for (int k = 0; k < n; k++) acc += mp[k] * ip[k * C];
-        out[e] = acc;
-    }
-}
-
-template <typename T, int GS>
-__device__ void fcontract(const T *in, T *out, int A, int n, int r, int C, const T *M, int tid)
-{
-#define SG_FC(NN, RRR) case (NN) * 64 + (RRR): fcontract_t<T, NN, RRR, GS>(in, out, A, C, M, tid); return;
-    switch (n * 64 + r) {
-        SG_FC(2, 2) SG_FC(2, 3) SG_FC(3, 2) SG_FC(3, 3) SG_FC(3, 4) SG_FC(4, 3) SG_FC(4, 4) SG_FC(4, 5)
-        SG_FC(5, 4) SG_FC(5, 5) SG_FC(5, 6) SG_FC(6, 5) SG_FC(6, 6) SG_FC(6, 7) SG_FC(7, 6)
-        default: fcontract_rt<T, GS>(in, out, A, n, r, C, M, tid); return;
-    }
-#undef SG_FC
-}
-
-__host__ __device__ constexpr int cpow(int b, int e) { return e <= 0 ? 1 : b * cpow(b, e - 1); }
-
-// one register stage: out[p][u][q] = sum_k M[u][k] in[p][k][q]
-template <typename T, int SZ, int PP, int N, int RR, int Q, int MS>
-__device__ __forceinline__ void rstage(const T (&in)[SZ], T (&out)[SZ], const T (&M)[MS])
-{
-#pragma unroll
-    for (int p = 0; p < PP; p++)
-#pragma unroll
-        for (int u = 0; u < RR; u++)
-#pragma unroll
-            for (int q = 0; q < Q; q++) {
-                T acc = T(0);
-#pragma unroll
-                for (int k = 0; k < N; k++) acc = fma_t(M[u * N + k], in[(p * N + k) * Q + q], acc);
-                out[(p * RR + u) * Q + q] = acc;
-            }
-}
-
-// Register phase: for every outer grid point g of the slice and every vector
-// of the chunk, the inner slots basis -> grid, times the potential, grid ->
-// basis, in place in Z[i][v][g].
-template <typename T, int R, int NB1, int NQ1, bool UNI, int GS>
-__device__ void reg_phase(const FHdr &H, const T *mats, const T *G, T *Z, const int vb, const int tid)
-{
-    constexpr int NBI = cpow(NB1, R), NGI = cpow(NQ1, R), SZ = NGI;
-    constexpr int RA = R > 0 ? R : 1;
-    constexpr int NM = UNI ? 1 : RA;
-    T Bm[NM][NQ1 * NB1], BWm[NM][NB1 * NQ1];
-#pragma unroll
-    for (int b = 0; b < NM; b++)
-#pragma unroll
-        for (int e = 0; e < NQ1 * NB1; e++) {
-            Bm[b][e] = R > 0 ? mats[H.oB[b] + e] : T(0);
-            BWm[b][e] = R > 0 ? mats[H.oBW[b] + e] : T(0);
-        }
-    const int s0 = R + H.s, NGs = H.NGs;
-    // the part of the potential that depends on inner slots only (same for every g)
-    T Vin[SZ];
-#pragma unroll
-    for (int gi = 0; gi < NGI; gi++) Vin[gi] = T(0);
-    bool outer_pairs = false;
-    for (int p = 0; p < H.npair; p++) {
-        const int A = H.pa[p], B = H.pb[p];
-        if (A >= R || B >= R) { outer_pairs = true; continue; }
-#pragma unroll
-        for (int q0 = 0; q0 < R; q0++)
-#pragma unroll
-            for (int q1 = q0 + 1; q1 < R; q1++)
-                if (q0 == A && q1 == B)
-#pragma unroll
-                    for (int gi = 0; gi < NGI; gi++)
-                        Vin[gi] += G[H.pg[p] + ((gi / cpow(NQ1, R - 1 - q0)) % NQ1) * NQ1 +
-                                     (gi / cpow(NQ1, R - 1 - q1)) % NQ1];
-    }
-    for (int g = tid; g < NGs; g += GS) {
-        // add the parts that depend on the outer grid point g
-        T V[SZ];
-        T vO = T(0);
-        T hsum[RA][NQ1];
-#pragma unroll
-        for (int b = 0; b < RA; b++)
-#pragma unroll
-            for (int u = 0; u < NQ1; u++) hsum[b][u] = T(0);
-        unsigned hb = 0;  // inner slots coupled to an outer one
-        if (outer_pairs)
-            for (int p = 0; p < H.npair; p++) {
-                const int A = H.pa[p], B = H.pb[p];
-                if (A < R && B < R) continue;
-                auto uo = [&](int j) {
-                    if (j < s0) return H.uS[j];
-                    const int q = fdiv(g, H.gstride[j], H.gmag[j]);
-                    return q - fdiv(q, H.nq[j], H.qmag[j]) * H.nq[j];
-                };
-                if (A >= R && B >= R) {
-                    vO += G[H.pg[p] + uo(A) * H.nq[B] + uo(B)];
-                } else if (A >= R) {  // B inner: row u_A of G[u_A][u_B]
-                    const T *row = G + H.pg[p] + uo(A) * NQ1;
-                    hb |= 1u << B;
-#pragma unroll
-                    for (int b = 0; b < R; b++)
-                        if (b == B)
-#pragma unroll
-                            for (int u = 0; u < NQ1; u++) hsum[b][u] += row[u];
-                } else {              // A inner: column u_B of G[u_A][u_B]
-                    const int ub = uo(B), nqb = H.nq[B];
-                    hb |= 1u << A;
-#pragma unroll
-                    for (int b = 0; b < R; b++)
-                        if (b == A)
-#pragma unroll
-                            for (int u = 0; u < NQ1; u++) hsum[b][u] += G[H.pg[p] + u * nqb + ub];
-                }
-            }
-#pragma unroll
-        for (int gi = 0; gi < NGI; gi++) V[gi] = Vin[gi] + vO;
-#pragma unroll
-        for (int b = 0; b < R; b++)
-            if (hb & (1u << b))
-#pragma unroll
-                for (int gi = 0; gi < NGI; gi++) V[gi] += hsum[b][(gi / cpow(NQ1, R - 1 - b)) % NQ1];
-        for (int v = 0; v < vb; v++) {
-            T va[SZ], vw[SZ];
-#pragma unroll
-            for (int i = 0; i < NBI; i++) va[i] = Z[(i * vb + v) * NGs + g];
-            if constexpr (R == 0) {
-                va[0] *= V[0];
-            } else if constexpr (R == 1) {
-                rstage<T, SZ, 1, NB1, NQ1, 1>(va, vw, Bm[0]);
-#pragma unroll
-                for (int gi = 0; gi < NGI; gi++) vw[gi] *= V[gi];
-                rstage<T, SZ, 1, NQ1, NB1, 1>(vw, va, BWm[0]);
-            } else if constexpr (R == 2) {
-                rstage<T, SZ, 1, NB1, NQ1, NB1>(va, vw, Bm[0]);
-                rstage<T, SZ, NQ1, NB1, NQ1, 1>(vw, va, Bm[UNI ? 0 : 1]);
-#pragma unroll
-                for (int gi = 0; gi < NGI; gi++) va[gi] *= V[gi];
-                rstage<T, SZ, NQ1, NQ1, NB1, 1>(va, vw, BWm[UNI ? 0 : 1]);
-                rstage<T, SZ, 1, NQ1, NB1, NB1>(vw, va, BWm[0]);
-            } else if constexpr (R == 3) {
-                rstage<T, SZ, 1, NB1, NQ1, NB1 * NB1>(va, vw, Bm[0]);
-                rstage<T, SZ, NQ1, NB1, NQ1, NB1>(vw, va, Bm[UNI ? 0 : 1]);
-                rstage<T, SZ, NQ1 * NQ1, NB1, NQ1, 1>(va, vw, Bm[UNI ? 0 : 2]);
-#pragma unroll
-                for (int gi = 0; gi < NGI; gi++) vw[gi] *= V[gi];
-                rstage<T, SZ, NQ1 * NQ1, NQ1, NB1, 1>(vw, va, BWm[UNI ? 0 : 2]);
-                rstage<T, SZ, NQ1, NQ1, NB1, NB1>(va, vw, BWm[UNI ? 0 : 1]);
-                rstage<T, SZ, 1, NQ1, NB1, NB1 * NB1>(vw, va, BWm[0]);
-            }
-#pragma unroll
-            for (int i = 0; i < NBI; i++) Z[(i * vb + v) * NGs + g] = va[i];
-        }
-    }
-}
-
-// Shared-memory partition of one term group: matrices, G tables, slice
-// weights (head), then the work area for X, Y and the two grid buffers.
-__host__ __device__ inline size_t part_head_bytes(const KParams &P, size_t rb)
-{
-    return (((size_t)P.matcap + P.fast.gcap + 2 * (size_t)P.fast.nbocap) * rb + 15) & ~(size_t)15;
-}
-__host__ __device__ inline size_t part_bytes(const KParams &P, size_t rb, int work)
-{
-    return (part_head_bytes(P, rb) + (size_t)work * rb + 15) & ~(size_t)15;
-}
-
-// GS threads process one term: GS = 128 (one block per term, the largest
-// terms) or GS = 32 (one warp per term, four terms per block, no block-wide
-// barriers).  Terms [p0, p0 + pcount) of the processing order.
-template <typename T, int NB1, int NQ1, int RMAX, bool UNI, int GS>
-__global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 3 : 2)
-    k_apply_fast(const KParams P, const double *__restrict__ x, const long long *__restrict__ maxbits, int nvec,
-                 int p0, int pcount, int work_cap)
-{
-    constexpr int NG = kFT / GS;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ FHdr Hs[NG];
-    const int grp = threadIdx.x / GS, tid = threadIdx.x % GS;
-    FHdr &H = Hs[grp];
-    const int pidx = blockIdx.x * NG + grp;
-    if (pidx >= pcount) return;
-    const size_t rb = sizeof(T);
-    unsigned char *base = smraw + (size_t)grp * part_bytes(P, rb, work_cap);
-    T *mats = reinterpret_cast<T *>(base);
-    T *gtab = mats + P.matcap;
-    T *WoF = gtab + P.fast.gcap;
-    T *WoB = WoF + P.fast.nbocap;
-    T *work = reinterpret_cast<T *>(base + part_head_bytes(P, rb));
-
-    if (tid < 32) {
-        load_record(P, p0 + pidx, reinterpret_cast<int4 *>(work), H);
-        derive_layout(P, nvec, work_cap, H);
-    }
-    gsync<GS>();
-    if (H.bad) {
-        if (tid == 0 && P.err) atomicCAS(P.err, 0, 110 + H.bad);
-        return;
-    }
-    const T *tab = FTab<T>::t(P);
-    const T *ftab = FTab<T>::f(P);
-    const int m = H.m, R = H.R, NB = H.NB, NBo = H.NBo;
-    const int *rk = P.fast.ranks + H.rank_off;
-
-    // per-position matrices: B, B^T W (grid part) and H1 = base + induced; G tables of the active pairs
-    for (int j = 0; j < m; j++) {
-        const int nb = H.nb[j], nq = H.nq[j];
-        if (H.grid)
-            for (int e = tid; e < nb * nq; e += GS) {
-                mats[H.oB[j] + e] = tab[H.gB[j] + e];
-                mats[H.oBW[j] + e] = tab[H.gBW[j] + e];
-            }
-        for (int e = tid; e < nb * nb; e += GS) {
-            T hv = ftab[H.gH1[j] + e];
-            for (int q = 0; q < H.nind; q++)
-                if (H.ipos[q] == j) hv += ftab[H.ioffs[q] + e];
-            mats[H.oH[j] + e] = hv;
-        }
-    }
-    for (int p = 0; p < H.npair; p++) {
-        const int sz = H.nq[H.pa[p]] * H.nq[H.pb[p]];
-        for (int e = tid; e < sz; e += GS) gtab[H.pg[p] + e] = ftab[H.pgg[p] + e];
-    }
-    gsync<GS>();
-
-    for (int v0 = 0; v0 < nvec; v0 += H.vb) {
-        const int vb = min(H.vb, nvec - v0);
-        T *X = work, *Y = work + NB * vb, *bufA = Y + NB * vb;
-        // gather: X[i][v][o]
-        for (int e = tid; e < NB; e += GS) {
-            const int i = e / NBo, o = e - i * NBo;
-            const int r = __ldg(rk + e);
-            for (int v = 0; v < vb; v++) X[(i * vb + v) * NBo + o] = (T)__ldg(x + (size_t)(v0 + v) * P.n_cs + r);
-        }
-        gsync<GS>();
-        // basis part: Y = c0 X + sum_j H1_j x_j X, all vectors of the chunk per element
-        for (int e = tid; e < NB; e += GS) {
-            const int i = e / NBo, o = e - i * NBo;
-            const int base0 = i * vb * NBo + o;
-            T acc[kMaxVB];
-#pragma unroll
-            for (int v = 0; v < kMaxVB; v++) acc[v] = v < vb ? (T)H.c0 * X[base0 + v * NBo] : T(0);
-            for (int j = 0; j < m; j++) {
-                const int src = j < R ? i : o;
-                const int q = fdiv(src, H.ostride[j], H.smag[j]);
-                const int nbj = H.nb[j], kj = q - fdiv(q, nbj, H.bmag[j]) * nbj;
-                const int st = j < R ? H.ostride[j] * vb * NBo : H.ostride[j];
-                const T *xp = X + base0 - kj * st;
-                const T *Hr = mats + H.oH[j] + kj * nbj;
-                for (int kp = 0; kp < nbj; kp++) {
-                    const T hv = Hr[kp];
-#pragma unroll
-                    for (int v = 0; v < kMaxVB; v++)
-                        if (v < vb) acc[v] = fma_t(hv, xp[kp * st + v * NBo], acc[v]);
-                }
-            }
-#pragma unroll
-            for (int v = 0; v < kMaxVB; v++)
-                if (v < vb) Y[base0 + v * NBo] = acc[v];
-        }
-        gsync<GS>();
-        if (H.grid) {
-            const int ps = R + H.s;
-            const int NBIv = H.NBIn * vb;
-            T *bufB = bufA + (size_t)H.NBIn * H.NGs * vb;
-            for (int sl = 0; sl < H.nslice; sl++) {
-                T *cur, *oth, *spare;
-                if (H.s > 0) {
-                    if (tid == 0) {
-                        int rem = sl;
-                        for (int j = ps - 1; j >= R; j--) { H.uS[j] = rem % H.nq[j]; rem /= H.nq[j]; }
-                    }
-                    gsync<GS>();
-                    for (int ko = tid; ko < H.NBO; ko += GS) {
-                        int rem = ko;
-                        T wf = T(1), wb = T(1);
-                        for (int j = ps - 1; j >= R; j--) {
-                            const int kj = rem % H.nb[j];
-                            rem /= H.nb[j];
-                            wf *= mats[H.oB[j] + H.uS[j] * H.nb[j] + kj];
-                            wb *= mats[H.oBW[j] + kj * H.nq[j] + H.uS[j]];
-                        }
-                        WoF[ko] = wf; WoB[ko] = wb;
-                    }
-                    gsync<GS>();
-                    // Xs[iv][rest] = sum_ko WoF[ko] X[iv][ko][rest]
-                    for (int e = tid; e < NBIv * H.NBrest; e += GS) {
-                        const int iv = e / H.NBrest, rr = e - iv * H.NBrest;
-                        const T *xp = X + (size_t)iv * NBo + rr;
-                        T acc = T(0);
-                        for (int ko = 0; ko < H.NBO; ko++) acc += WoF[ko] * xp[ko * H.NBrest];
-                        bufA[e] = acc;
-                    }
-                    gsync<GS>();
-                    cur = bufA; oth = bufB; spare = bufA;
-                } else {
-                    cur = X; oth = bufA; spare = bufB;  // X is not needed after the basis part
-                }
-                // outer basis -> grid (ping-pong between the two grid buffers)
-                int A = NBIv;
-                for (int j = ps; j < m; j++) {
-                    int C = 1;
-                    for (int i2 = j + 1; i2 < m; i2++) C *= H.nb[i2];
-                    fcontract<T, GS>(cur, oth, A, H.nb[j], H.nq[j], C, mats + H.oB[j], tid);
-                    A *= H.nq[j];
-                    T *freed = (cur == X) ? spare : cur;
-                    cur = oth; oth = freed;
-                    gsync<GS>();
-                }
-                if (cur == X) oth = bufA;
-                // inner slots and potential, in registers
-                switch (R) {
-                    case 0: reg_phase<T, 0, NB1, NQ1, UNI, GS>(H, mats, gtab, cur, vb, tid); break;
-                    case 1: if constexpr (RMAX >= 1) reg_phase<T, 1, NB1, NQ1, UNI, GS>(H, mats, gtab, cur, vb, tid); break;
-                    case 2: if constexpr (RMAX >= 2) reg_phase<T, 2, NB1, NQ1, UNI, GS>(H, mats, gtab, cur, vb, tid); break;
-                    case 3: if constexpr (RMAX >= 3) reg_phase<T, 3, NB1, NQ1, UNI, GS>(H, mats, gtab, cur, vb, tid); break;
-                    default: break;
-                }
-                gsync<GS>();
-                // outer grid -> basis, reverse order
-                for (int j = m - 1; j >= ps; j--) {
-                    int Aj = NBIv, C = 1;
-                    for (int i2 = ps; i2 < j; i2++) Aj *= H.nq[i2];
-                    for (int i2 = j + 1; i2 < m; i2++) C *= H.nb[i2];
-                    fcontract<T, GS>(cur, oth, Aj, H.nq[j], H.nb[j], C, mats + H.oBW[j], tid);
-                    T *tp = cur; cur = oth; oth = tp;
-                    gsync<GS>();
-                }
-                // Y[iv][ko][rest] += WoB[ko] cur[iv][rest]
-                if (H.s > 0) {
-                    for (int e = tid; e < NB * vb; e += GS) {
-                        const int rr = e % H.NBrest, t2 = e / H.NBrest, ko = t2 % H.NBO, iv = t2 / H.NBO;
-                        Y[e] += WoB[ko] * cur[iv * H.NBrest + rr];
-                    }
-                } else {
-                    for (int e = tid; e < NB * vb; e += GS) Y[e] += cur[e];
-                }
-                gsync<GS>();
-            }
-        }
-        // exact compress-add of D_l * y_l
-        for (int e = tid; e < NB; e += GS) {
-            const int i = e / NBo, o = e - i * NBo;
-            const int r = __ldg(rk + e);
-            for (int v = 0; v < vb; v++) {
-                unsigned long long *acc = P.acc + ((size_t)(v0 + v) * P.n_cs + r) * kAccDigits;
-                fx::fx_add_real(acc, Y[(i * vb + v) * NBo + o], H.coef, fx::lsb_exponent(maxbits[v0 + v]),
-                                P.err);
-            }
-        }
-        gsync<GS>();
-    }
-}
-
-struct LaunchArgs {
-    const double *x;
-    int nvec;
-    const long long *maxbits;
-    cudaStream_t stream;
-    bool configure;
-};
-
-template <typename T, int NB1, int NQ1, int RMAX, bool UNI>
-cudaError_t launch_t(const KParams &kp, const LaunchArgs &a)
-{
-    const size_t rb = sizeof(T);
-    const size_t smem_cta = part_bytes(kp, rb, kp.fast.work_cta);
-    const size_t smem_warp = (size_t)(kFT / 32) * part_bytes(kp, rb, kp.fast.work_warp);
-    if (a.configure) {
-        cudaError_t e = cudaFuncSetAttribute(k_apply_fast<T, NB1, NQ1, RMAX, UNI, kFT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cta);
-        if (e != cudaSuccess || kp.fast.work_warp <= 0) return e;
-        return cudaFuncSetAttribute(k_apply_fast<T, NB1, NQ1, RMAX, UNI, 32>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_warp);
-    }
-    const int nbig = kp.fast.n_big, nrest = (int)kp.n_terms - nbig;
-    if (nbig > 0)
-        k_apply_fast<T, NB1, NQ1, RMAX, UNI, kFT><<<(unsigned)nbig, kFT, smem_cta, a.stream>>>(
-            kp, a.x, a.maxbits, a.nvec, 0, nbig, kp.fast.work_cta);
-    if (nrest > 0) {
-        const unsigned blocks = (unsigned)((nrest + kFT / 32 - 1) / (kFT / 32));
-        k_apply_fast<T, NB1, NQ1, RMAX, UNI, 32><<<blocks, kFT, smem_warp, a.stream>>>(
-            kp, a.x, a.maxbits, a.nvec, nbig, nrest, kp.fast.work_warp);
-    }
-    return cudaGetLastError();
-}
-
-template <typename T, bool UNI>
-cudaError_t dispatch_u(const KParams &kp, const LaunchArgs &a)
-{
-    // the register-slot count must be fast_rmax(...) (the host built the records with it)
-    constexpr bool F32 = sizeof(T) == 4;
-    const int nb1 = kp.fast.nb1, nq1 = kp.fast.nq1;
-    if (nb1 == 2 && nq1 == 3) return launch_t<T, 2, 3, F32 ? 3 : 1, UNI>(kp, a);
-    if (nb1 == 2 && nq1 == 2) return launch_t<T, 2, 2, F32 ? 3 : 1, UNI>(kp, a);
-    if (nb1 == 3 && nq1 == 3) return launch_t<T, 3, 3, F32 ? 2 : 1, UNI>(kp, a);
-    return launch_t<T, 1, 1, 0, UNI>(kp, a);
-}
-
-template <typename T>
-cudaError_t dispatch(const KParams &kp, const LaunchArgs &a)
-{
-    return kp.fast.uni1 ? dispatch_u<T, true>(kp, a) : dispatch_u<T, false>(kp, a);
-}
 
 }  // namespace
 
@@ -626,6 +43,37 @@ size_t fast_smem_bytes(const KParams &kp, bool fp32)
 {
     const size_t rb = fp32 ? 4 : 8;
     return std::max(part_bytes(kp, rb, kp.fast.work_cta), (size_t)(kFT / 32) * part_bytes(kp, rb, kp.fast.work_warp));
+}
+
+size_t fast_part_bytes(const KParams &kp, bool fp32, bool warp_form)
+{
+    return part_bytes(kp, fp32 ? 4 : 8, warp_form ? kp.fast.work_warp : kp.fast.work_cta);
+}
+
+static FastBatchLaunch batch_args(const FastBatchGroup &g, const double *x, unsigned long long *acc,
+                                  const long long *maxbits, const long long *cs_prefix, int nvec,
+                                  cudaStream_t stream, bool configure)
+{
+    FastBatchLaunch a{};
+    a.kps = g.kps;
+    for (int f = 0; f < 2; f++) { a.items[f] = g.items[f]; a.count[f] = g.count[f]; a.part[f] = g.part[f]; }
+    a.x = x; a.acc = acc; a.maxbits = maxbits; a.cs_prefix = cs_prefix; a.nvec = nvec;
+    a.stream = stream; a.configure = configure;
+    return a;
+}
+
+cudaError_t configure_fast_batch(const KParams &kp_any, bool fp32, const FastBatchGroup &g)
+{
+    const FastBatchLaunch a = batch_args(g, nullptr, nullptr, nullptr, nullptr, 0, 0, true);
+    return fp32 ? fast_batch_launch_f32(kp_any, a) : fast_batch_launch_f64(kp_any, a);
+}
+
+cudaError_t launch_fast_batch(const KParams &kp_any, bool fp32, const FastBatchGroup &g, const double *x,
+                              unsigned long long *acc, const long long *maxbits, const long long *cs_prefix,
+                              int nvec, cudaStream_t stream)
+{
+    const FastBatchLaunch a = batch_args(g, x, acc, maxbits, cs_prefix, nvec, stream, false);
+    return fp32 ? fast_batch_launch_f32(kp_any, a) : fast_batch_launch_f64(kp_any, a);
 }
 
 cudaError_t launch_build_ranks(const KParams &kp, int *ranks, cudaStream_t stream)
@@ -638,16 +86,16 @@ cudaError_t launch_build_ranks(const KParams &kp, int *ranks, cudaStream_t strea
 
 cudaError_t configure_fast_kernels(const KParams &kp, bool fp32)
 {
-    LaunchArgs a{nullptr, 0, nullptr, 0, true};
-    return fp32 ? dispatch<float>(kp, a) : dispatch<double>(kp, a);
+    FastLaunch a{nullptr, 0, nullptr, 0, true};
+    return fp32 ? fast_launch_f32(kp, a) : fast_launch_f64(kp, a);
 }
 
 cudaError_t launch_apply_fast(const KParams &kp, bool fp32, const double *x, int nvec,
                               const long long *maxbits, cudaStream_t stream)
 {
     if (kp.n_terms == 0) return cudaSuccess;
-    LaunchArgs a{x, nvec, maxbits, stream, false};
-    return fp32 ? dispatch<float>(kp, a) : dispatch<double>(kp, a);
+    FastLaunch a{x, nvec, maxbits, stream, false};
+    return fp32 ? fast_launch_f32(kp, a) : fast_launch_f64(kp, a);
 }
 
 }  // namespace sg

@@ -1,0 +1,218 @@
+// Many Smolyak problems per apply (declared in include/smolyak.h): the terms
+// of all problems of one kernel variant go to the device in one launch per
+// form (block / warp), ordered by estimated cost over all problems, so a
+// batch of small and large problems keeps every SM busy until the end.
+#include <algorithm>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "sg_internal.h"
+
+struct sg_batch {
+    std::vector<sg_ctx *> ctxs;
+    int device = 0;
+    bool fp32 = false;
+    std::vector<long long> cs_prefix;  // host copy
+    int64_t n_terms = 0, max_ncs = 0;
+    const long long *d_cs_prefix = nullptr;
+    const sg::KParams *d_kps = nullptr;
+    struct Group {
+        sg::KParams kp_any;
+        sg::FastBatchGroup g;
+    };
+    std::vector<Group> groups;
+    std::vector<int> generic;          // problems outside the fast path: one launch each
+    std::vector<void *> allocations;
+    unsigned long long *acc = nullptr;
+    long long *maxbits = nullptr;
+    int acc_nvec = 0;
+    std::string last_error;
+};
+
+namespace {
+
+sg_status bfail(sg_batch *b, sg_status st, const std::string &msg)
+{
+    if (b) b->last_error = msg;
+    return st;
+}
+
+template <typename T>
+sg_status bupload(sg_batch *b, const std::vector<T> &v, const T **dst)
+{
+    void *p = nullptr;
+    const size_t bytes = std::max<size_t>(1, v.size()) * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return bfail(b, SG_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    b->allocations.push_back(p);
+    if (!v.empty() && (e = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bfail(b, SG_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+    *dst = static_cast<const T *>(p);
+    return SG_OK;
+}
+
+void free_all(sg_batch *b)
+{
+    for (void *p : b->allocations) cudaFree(p);
+    b->allocations.clear();
+    if (b->acc) cudaFree(b->acc);
+    if (b->maxbits) cudaFree(b->maxbits);
+    b->acc = nullptr;
+    b->maxbits = nullptr;
+}
+
+}  // namespace
+
+extern "C" sg_status sg_batch_create(sg_ctx *const *ctxs, int n, sg_batch **out)
+{
+    if (!out) return SG_EINVAL;
+    *out = nullptr;
+    if (!ctxs || n < 1 || n > 65535) return SG_EINVAL;
+    sg_batch *b = new (std::nothrow) sg_batch;
+    if (!b) return SG_ENOMEM;
+    for (int j = 0; j < n; j++) {
+        sg_ctx *c = ctxs[j];
+        if (!c || !c->has_device) { delete b; return SG_EINVAL; }
+        if (j > 0 && (c->device != b->device || c->fp32 != b->fp32)) { delete b; return SG_EINVAL; }
+        b->device = c->device;
+        b->fp32 = c->fp32;
+        b->ctxs.push_back(c);
+    }
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != b->device) { delete b; return SG_EINVAL; }
+
+    b->cs_prefix.assign(n + 1, 0);
+    std::vector<sg::KParams> kps(n);
+    for (int j = 0; j < n; j++) {
+        const sg_ctx *c = ctxs[j];
+        b->cs_prefix[j + 1] = b->cs_prefix[j] + c->host.n_cs;
+        b->max_ncs = std::max<int64_t>(b->max_ncs, c->host.n_cs);
+        b->n_terms += c->host.n_terms;
+        kps[j] = c->kp;
+        kps[j].acc = nullptr;  // the batch kernels take the batch's accumulators explicitly
+    }
+
+    // problems of one fast-kernel variant share a launch
+    std::map<std::tuple<int, int, int>, std::vector<int>> by_variant;
+    for (int j = 0; j < n; j++) {
+        const sg::KParams &kp = ctxs[j]->kp;
+        if (kp.fast.enabled) by_variant[{kp.fast.nb1, kp.fast.nq1, kp.fast.uni1}].push_back(j);
+        else b->generic.push_back(j);
+    }
+    sg_status st;
+    if ((st = bupload(b, kps, &b->d_kps)) != SG_OK || (st = bupload(b, b->cs_prefix, &b->d_cs_prefix)) != SG_OK) {
+        free_all(b);
+        delete b;
+        return st;
+    }
+    for (auto &kv : by_variant) {
+        sg_batch::Group G{};
+        G.kp_any = ctxs[kv.second[0]]->kp;
+        G.g.kps = b->d_kps;
+        for (int f = 0; f < 2; f++) {
+            struct Item { int64_t cost; int j, p; };
+            std::vector<Item> it;
+            size_t part = 0;
+            for (int j : kv.second) {
+                const sg::HostTables &T = ctxs[j]->host;
+                const int nb = ctxs[j]->kp.fast.n_big;
+                const int64_t p0 = f == 0 ? 0 : nb, p1 = f == 0 ? nb : T.n_terms;
+                if (p1 > p0) part = std::max(part, sg::fast_part_bytes(ctxs[j]->kp, b->fp32, f == 1));
+                for (int64_t p = p0; p < p1; p++) it.push_back({T.pcost[p], j, (int)p});
+            }
+            std::stable_sort(it.begin(), it.end(), [](const Item &a, const Item &c) { return a.cost > c.cost; });
+            std::vector<int2> items(it.size());
+            for (size_t q = 0; q < it.size(); q++) items[q] = make_int2(it[q].j, it[q].p);
+            if (it.size() > (size_t)0x7FFFFFFF) { free_all(b); delete b; return SG_EUNSUPPORTED; }
+            G.g.count[f] = (int)it.size();
+            G.g.part[f] = (int)part;
+            if ((st = bupload(b, items, &G.g.items[f])) != SG_OK) { free_all(b); delete b; return st; }
+        }
+        cudaError_t e = sg::configure_fast_batch(G.kp_any, b->fp32, G.g);
+        if (e != cudaSuccess) { free_all(b); delete b; return SG_ECUDA; }
+        b->groups.push_back(G);
+    }
+    *out = b;
+    return SG_OK;
+}
+
+extern "C" sg_status sg_batch_size(const sg_batch *b, int64_t *n_cs_total, int64_t *n_terms_total,
+                                   int *launches_per_apply)
+{
+    if (!b) return SG_EINVAL;
+    if (n_cs_total) *n_cs_total = b->cs_prefix.back();
+    if (n_terms_total) *n_terms_total = b->n_terms;
+    if (launches_per_apply) {
+        int l = 2;  // max|x| and finalisation
+        for (const auto &G : b->groups) l += (G.g.count[0] > 0) + (G.g.count[1] > 0);
+        for (int j : b->generic) {
+            const sg::KParams &kp = b->ctxs[j]->kp;
+            l += kp.n_terms > 0;
+        }
+        *launches_per_apply = l;
+    }
+    return SG_OK;
+}
+
+extern "C" sg_status sg_apply_H_batch(sg_batch *b, const double *x, double *y, int nvec, void *stream)
+{
+    if (!b) return SG_EINVAL;
+    if (!x || !y) return bfail(b, SG_EINVAL, "x or y is NULL");
+    if (nvec < 1) return bfail(b, SG_EINVAL, "nvec must be >= 1");
+    const int nprob = (int)b->ctxs.size();
+    const size_t total = (size_t)b->cs_prefix.back() * (size_t)nvec;
+    if ((x < y + total) && (y < x + total)) return bfail(b, SG_EINVAL, "x and y overlap");
+    if ((size_t)nprob * nvec > 65535u * 65535u) return bfail(b, SG_EUNSUPPORTED, "too many vectors");
+    if (nvec > 65535) return bfail(b, SG_EUNSUPPORTED, "nvec > 65535");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (nvec > b->acc_nvec) {
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return bfail(b, SG_ECUDA, std::string("stream synchronize: ") + cudaGetErrorString(e));
+        if (b->acc) cudaFree(b->acc);
+        if (b->maxbits) cudaFree(b->maxbits);
+        b->acc = nullptr;
+        b->maxbits = nullptr;
+        b->acc_nvec = 0;
+        const size_t words = total * sg::kAccDigits;
+        if ((e = cudaMalloc(&b->acc, words * sizeof(unsigned long long))) != cudaSuccess ||
+            (e = cudaMalloc(&b->maxbits, sizeof(long long) * (size_t)nprob * nvec)) != cudaSuccess)
+            return bfail(b, SG_ENOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+        if ((e = cudaMemsetAsync(b->acc, 0, words * sizeof(unsigned long long), s)) != cudaSuccess)
+            return bfail(b, SG_ECUDA, std::string("workspace memset: ") + cudaGetErrorString(e));
+        b->acc_nvec = nvec;
+    }
+    if ((e = sg::launch_maxabs_batch(x, b->d_cs_prefix, nprob, b->max_ncs, nvec, b->maxbits, s)) != cudaSuccess)
+        return bfail(b, SG_ECUDA, std::string("max|x| launch: ") + cudaGetErrorString(e));
+    for (const auto &G : b->groups)
+        if ((e = sg::launch_fast_batch(G.kp_any, b->fp32, G.g, x, b->acc, b->maxbits, b->d_cs_prefix, nvec, s)) !=
+            cudaSuccess)
+            return bfail(b, SG_ECUDA, std::string("batched term launch: ") + cudaGetErrorString(e));
+    for (int j : b->generic) {
+        sg::KParams kp = b->ctxs[j]->kp;
+        const size_t off = (size_t)nvec * (size_t)b->cs_prefix[j];
+        kp.acc = b->acc + off * sg::kAccDigits;
+        if ((e = sg::launch_apply_terms(kp, b->fp32, x + off, b->maxbits + (size_t)j * nvec, nvec, s)) !=
+            cudaSuccess)
+            return bfail(b, SG_ECUDA, std::string("term launch: ") + cudaGetErrorString(e));
+    }
+    if ((e = sg::launch_finalize_batch(b->d_kps, b->d_cs_prefix, nprob, b->cs_prefix.back(), x, y, b->acc,
+                                       b->maxbits, nvec, s)) != cudaSuccess)
+        return bfail(b, SG_ECUDA, std::string("finalise launch: ") + cudaGetErrorString(e));
+    return SG_OK;
+}
+
+extern "C" const char *sg_batch_last_error(const sg_batch *b)
+{
+    return b ? b->last_error.c_str() : "";
+}
+
+extern "C" void sg_batch_destroy(sg_batch *b)
+{
+    if (!b) return;
+    free_all(b);
+    delete b;
+}

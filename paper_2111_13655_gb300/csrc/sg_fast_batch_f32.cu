@@ -1,0 +1,14 @@
+// Instantiates the fast-path term kernels for FP32 contractions, many problems per launch.
+#include "sg_fast.cuh"
+
+namespace sg {
+
+cudaError_t fast_batch_launch_f32(const KParams &kp_any, const FastBatchLaunch &a)
+{
+    return for_variant<float>(kp_any, [&](auto v) {
+        using V = decltype(v);
+        return batch_t<float, V::NB1, V::NQ1, V::RMAX, V::UNI>(a);
+    });
+}
+
+}  // namespace sg

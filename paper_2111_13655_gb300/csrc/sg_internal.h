@@ -139,6 +139,7 @@ struct HostTables {
     std::vector<uint8_t> levels;     // [n_terms][Dpad]
     std::vector<int> coefs;          // [n_terms]
     std::vector<int> order;          // processing order (Table-2 indices)
+    std::vector<int64_t> pcost;      // estimated cost of the p-th processed term
     std::vector<int> rank_tab;       // [D][L+1][kw]
     std::vector<uint8_t> lmin_tab;   // [D][kw]
     std::vector<LevelInfo> lvl;      // [D][L+1]
@@ -182,6 +183,30 @@ size_t fast_smem_bytes(const KParams &kp, bool fp32);
 cudaError_t configure_fast_kernels(const KParams &kp, bool fp32);
 cudaError_t launch_apply_fast(const KParams &kp, bool fp32, const double *x, int nvec,
                               const long long *maxbits, cudaStream_t stream);
+
+// Many problems per apply (sg_batch.cpp): the term kernels of one problem
+// without the max|x| and finalisation passes; those two over all problems.
+cudaError_t launch_apply_terms(const KParams &kp, bool fp32, const double *x, const long long *maxbits, int nvec,
+                               cudaStream_t stream);
+cudaError_t launch_maxabs_batch(const double *x, const long long *cs_prefix, int nprob, int64_t max_ncs, int nvec,
+                                long long *maxbits, cudaStream_t stream);
+cudaError_t launch_finalize_batch(const KParams *kps, const long long *cs_prefix, int nprob, int64_t total_cs,
+                                  const double *x, double *y, unsigned long long *acc, const long long *maxbits,
+                                  int nvec, cudaStream_t stream);
+// Shared-memory partition of one term group of the fast kernels (block form or warp form).
+size_t fast_part_bytes(const KParams &kp, bool fp32, bool warp_form);
+// Fast-path kernels over many problems of one kernel variant; items are
+// (problem, processing position) pairs in cost order.
+struct FastBatchGroup {
+    const KParams *kps;       // device, one per problem of the batch
+    const int2 *items[2];     // device: [0] block form, [1] warp form
+    int count[2];
+    int part[2];              // bytes per term group
+};
+cudaError_t configure_fast_batch(const KParams &kp_any, bool fp32, const FastBatchGroup &g);
+cudaError_t launch_fast_batch(const KParams &kp_any, bool fp32, const FastBatchGroup &g, const double *x,
+                              unsigned long long *acc, const long long *maxbits, const long long *cs_prefix,
+                              int nvec, cudaStream_t stream);
 
 }  // namespace sg
 

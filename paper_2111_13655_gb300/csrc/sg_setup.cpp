@@ -366,6 +366,8 @@ std::string build_tables(const Problem &p, int smem_budget, int rb, HostTables *
     std::iota(T.order.begin(), T.order.end(), 0);
     std::stable_sort(T.order.begin(), T.order.end(),
                      [&](int a, int b) { return cost[a] > cost[b]; });
+    T.pcost.resize(T.n_terms);
+    for (int64_t q = 0; q < T.n_terms; q++) T.pcost[q] = cost[T.order[q]];
 
     if (T.fast) {
         // fast kernel: matrices, G tables, slice weights and ranks, then a work

@@ -144,3 +144,38 @@ def workload_C3(seed: int = 3, lam: float = HH_LAMBDA, L: int = 10, D: int = 12)
     """D=12 chained Henon-Heiles, omega_i ~ U[0.8,1.2], nb=l+1, nq=l+2, L=10."""
     return chained_henon_heiles(D, L, draw_omega(D, seed), lam, (1, 1), (2, 1),
                                 name=f"HH D={D} L={L} nb=l+1 nq=l+2")
+
+
+def coherent_factors(q0: Sequence[float], kw: int) -> np.ndarray:
+    """1D Hermite-function coefficients c_n = exp(-a^2/2) a^n / sqrt(n!), a = q0/sqrt(2),
+    n < kw, of a unit Gaussian displaced to q0 in each mode (a coherent state),
+    shape (D, kw).  The product state over the compact basis is built by the
+    library (sg_product_state) or the oracle's compact enumeration."""
+    q0 = np.asarray(q0, np.float64)
+    a = q0 / np.sqrt(2.0)
+    out = np.empty((len(q0), kw))
+    for i, ai in enumerate(a):
+        c = np.empty(kw)
+        c[0] = np.exp(-0.5 * ai * ai)
+        for k in range(1, kw):
+            c[k] = c[k - 1] * ai / np.sqrt(k)
+        out[i] = c
+    return out
+
+
+def workload_C4(n: int = 256, seed: int = 4, Ds=(4, 6, 8, 10, 12), Ls=(6, 7, 8, 9, 10),
+                lam: float = HH_LAMBDA):
+    """Batch of n independent wavepacket problems: D uniform in Ds, L uniform in
+    Ls, chained Henon-Heiles with omega_i ~ U[0.8,1.2], nb = nq = l+1, and a
+    Gaussian wavepacket centred at q0_i ~ U[0,2] in every mode.
+    Returns a list of (Problem, q0) pairs."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for j in range(n):
+        D = int(g.choice(Ds))
+        L = int(g.choice(Ls))
+        om = g.uniform(0.8, 1.2, size=D)
+        q0 = g.uniform(0.0, 2.0, size=D)
+        out.append((chained_henon_heiles(D, L, om, lam, (1, 1), (1, 1),
+                                         name=f"HH D={D} L={L} nb=nq=l+1 (batch item {j})"), q0))
+    return out
