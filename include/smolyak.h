@@ -187,10 +187,71 @@ sg_status sg_apply_H_noalloc(sg_ctx *ctx, const double *x, double *y, int nvec, 
  */
 typedef struct sg_batch sg_batch;
 sg_status sg_batch_create(sg_ctx *const *ctxs, int n, sg_batch **out);
+
 sg_status sg_batch_size(const sg_batch *b, int64_t *n_cs_total, int64_t *n_terms_total, int *launches_per_apply);
 sg_status sg_apply_H_batch(sg_batch *b, const double *x, double *y, int nvec, void *stream);
 const char *sg_batch_last_error(const sg_batch *b);
 void sg_batch_destroy(sg_batch *b);
+
+/*
+ * Propagation server: continuous batching of Chebyshev propagation requests
+ * (the propagator of sg_propagate: Sec. 3, Sec. 5) of different D, L and
+ * basis sizes on one device.  Single-threaded: the caller submits requests
+ * and drives the engine with sg_server_progress; all calls on one server from
+ * one host thread at a time, with the server's device current.
+ *
+ * Each engine iteration retires finished requests, admits queued requests
+ * first come first served while their planned device memory fits the budget,
+ * then applies H_S to every active request's current Chebyshev vector in one
+ * sg_apply_H_batch and advances every recurrence by one term in one fused
+ * kernel.  Requests that arrive while others run join at the next iteration.
+ * A request's results are bitwise the same alone and in any mix (its applies,
+ * updates and logged sums do not depend on the other requests).
+ *
+ * sg_server_create -- precision of every request's contexts; hbm_budget_bytes:
+ *   the planned device memory of the active requests never exceeds it
+ *   (context tables, M^B, batch items, four state vectors, batch and context
+ *   workspaces, logs).  Transient set-up buffers of an admission (the
+ *   spectral-bound Krylov run, about 80 vectors) are not counted.
+ * sg_server_submit -- copies the request (the caller's arrays may be freed on
+ *   return), plans it on the host, and queues it; *id identifies it.
+ *   SG_EBUDGET if the request alone needs more than the budget.
+ *   Initial state: psi0 (host, 2 * N_cs doubles: real part, imaginary part;
+ *   N_cs from sg_plan + sg_size, compact order) or, if psi0 is NULL, the real
+ *   product state of `factors` (as sg_product_state, leading dimension ld).
+ *   Logs: <psi|psi> and <psi|H psi>/<psi|psi> at the start of each step.
+ * sg_server_progress -- runs up to max_iters engine iterations (fewer if
+ *   nothing is active); returns the numbers of active and queued requests.
+ *   Synchronous.
+ * sg_server_query -- state (sg_request_state), N_cs and steps done of a request.
+ * sg_server_result -- a finished request's psi (host, 2 * N_cs), logs (host,
+ *   nsteps each), times[0] = admission - submission, times[1] = completion -
+ *   submission (seconds, steady clock); any output may be NULL.
+ * sg_server_stats -- engine iterations, real-vector applications of H_S so far
+ *   (2 per active request per iteration), planned bytes of the active requests.
+ */
+typedef struct sg_server sg_server;
+typedef enum { SG_REQ_QUEUED = 0, SG_REQ_ACTIVE = 1, SG_REQ_DONE = 2, SG_REQ_FAILED = 3 } sg_request_state;
+typedef struct {
+    int D, L;
+    const sg_basis *basis;     /* D entries */
+    const sg_grid *grids;      /* D entries */
+    const sg_hamiltonian *H;
+    const double *psi0;        /* host, 2 * N_cs, or NULL */
+    const double *factors;     /* host, D * ld, used when psi0 is NULL */
+    int ld;
+    double dt;
+    int nsteps, order;         /* steps of length dt; Chebyshev order (reduced as in sg_propagate) */
+} sg_prop_request;
+sg_status sg_server_create(sg_precision prec, int64_t hbm_budget_bytes, sg_server **out);
+sg_status sg_server_submit(sg_server *s, const sg_prop_request *req, int64_t *id);
+sg_status sg_server_progress(sg_server *s, int max_iters, int *n_active, int *n_queued);
+sg_status sg_server_query(const sg_server *s, int64_t id, int *state, int64_t *n_cs, int *steps_done);
+sg_status sg_server_result(sg_server *s, int64_t id, double *psi_host, double *norm_log, double *energy_log,
+                           double *times);
+sg_status sg_server_stats(const sg_server *s, int64_t *iterations, int64_t *applications, int64_t *bytes_in_use);
+const char *sg_server_last_error(const sg_server *s);
+void sg_server_destroy(sg_server *s);
 
 /*
  * sg_term_levels -- levels l of terms [t0, t0+nt) in Table-2 order, D ints per

@@ -51,6 +51,12 @@ class _Ham(ctypes.Structure):
     _fields_ = [("omega", ctypes.c_void_p), ("V", _Poly)]
 
 
+class _PropRequest(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_int), ("L", ctypes.c_int), ("basis", ctypes.c_void_p), ("grids", ctypes.c_void_p),
+                ("H", ctypes.c_void_p), ("psi0", ctypes.c_void_p), ("factors", ctypes.c_void_p),
+                ("ld", ctypes.c_int), ("dt", ctypes.c_double), ("nsteps", ctypes.c_int), ("order", ctypes.c_int)]
+
+
 _lib = None
 _lock = threading.Lock()
 _vp, _i64, _i32, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
@@ -80,6 +86,14 @@ SIGNATURES = {
     "sg_apply_H_batch": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "sg_batch_last_error": (ctypes.c_char_p, [_vp]),
     "sg_batch_destroy": (None, [_vp]),
+    "sg_server_create": (_i32, [_i32, _i64, ctypes.POINTER(_vp)]),
+    "sg_server_submit": (_i32, [_vp, _vp, _P64]),
+    "sg_server_progress": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "sg_server_query": (_i32, [_vp, _i64, ctypes.POINTER(_i32), _P64, ctypes.POINTER(_i32)]),
+    "sg_server_result": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp]),
+    "sg_server_stats": (_i32, [_vp, _P64, _P64, _P64]),
+    "sg_server_last_error": (ctypes.c_char_p, [_vp]),
+    "sg_server_destroy": (None, [_vp]),
     "sg_destroy": (None, [_vp]),
 }
 
@@ -381,6 +395,99 @@ def sg_batch_destroy(b: Batch) -> None:
     if b is not None and getattr(b, "ptr", None):
         lib().sg_batch_destroy(b.ptr)
         b.ptr = None
+
+
+SG_REQ_QUEUED, SG_REQ_ACTIVE, SG_REQ_DONE, SG_REQ_FAILED = range(4)
+
+
+class Server:
+    """Propagation server on the current CUDA device (continuous batching of
+    Chebyshev propagation requests; see sg_server_* in include/smolyak.h)."""
+
+    def __init__(self, precision="fp64", hbm_budget_bytes: int = 150 * 10**9):
+        out = _vp()
+        st = lib().sg_server_create(_precision(precision), int(hbm_budget_bytes), ctypes.byref(out))
+        if st != SG_OK:
+            raise SgError(st, "sg_server_create failed")
+        self.ptr = out.value
+        self.nsteps = {}
+        self.n_cs = {}
+
+    def _err(self, st):
+        if st != SG_OK:
+            raise SgError(st, (lib().sg_server_last_error(self.ptr) or b"").decode(errors="replace"))
+
+    def submit(self, problem, dt: float, nsteps: int, order: int = 64, psi0=None, factors=None) -> int:
+        """Queue a propagation of psi0 (complex, N_cs, or a (2, N_cs) real/imaginary
+        array) or of the real product state of `factors` (D x ld)."""
+        basis, grids, ham, keep = _marshal(problem)
+        req = _PropRequest(problem.D, problem.L, ctypes.addressof(basis), ctypes.addressof(grids),
+                           ctypes.addressof(ham), None, None, 0, float(dt), int(nsteps), int(order))
+        if psi0 is not None:
+            a = np.asarray(psi0)
+            a = np.concatenate([a.real, a.imag]) if np.iscomplexobj(a) else a.reshape(-1)
+            a = np.ascontiguousarray(a, np.float64)
+            keep.append(a)
+            req.psi0 = a.ctypes.data
+        else:
+            f = np.ascontiguousarray(np.asarray(factors, np.float64))
+            keep.append(f)
+            req.factors, req.ld = f.ctypes.data, f.shape[1]
+        rid = ctypes.c_int64()
+        self._err(lib().sg_server_submit(self.ptr, ctypes.byref(req), ctypes.byref(rid)))
+        st, n, _ = self.query(rid.value)
+        self.nsteps[rid.value], self.n_cs[rid.value] = int(nsteps), n
+        return rid.value
+
+    def progress(self, max_iters: int = 1):
+        """Runs up to max_iters engine iterations; returns (active, queued)."""
+        a, q = ctypes.c_int(), ctypes.c_int()
+        self._err(lib().sg_server_progress(self.ptr, int(max_iters), ctypes.byref(a), ctypes.byref(q)))
+        return a.value, q.value
+
+    def query(self, rid: int):
+        """(state, N_cs, steps done) of a request."""
+        st, n, k = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int()
+        self._err(lib().sg_server_query(self.ptr, int(rid), ctypes.byref(st), ctypes.byref(n), ctypes.byref(k)))
+        return st.value, n.value, k.value
+
+    def result(self, rid: int):
+        """(psi complex N_cs, norm_log, energy_log, (queue_s, latency_s)) of a finished request."""
+        n, ns = self.n_cs[rid], self.nsteps[rid]
+        psi = np.zeros(2 * n)
+        nl, el, tm = np.zeros(max(ns, 1)), np.zeros(max(ns, 1)), np.zeros(2)
+        self._err(lib().sg_server_result(self.ptr, int(rid), psi.ctypes.data, nl.ctypes.data, el.ctypes.data,
+                                         tm.ctypes.data))
+        return psi[:n] + 1j * psi[n:], nl[:ns], el[:ns], (float(tm[0]), float(tm[1]))
+
+    def stats(self):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._err(lib().sg_server_stats(self.ptr, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"iterations": a.value, "applications": b.value, "bytes_in_use": c.value}
+
+    def run(self, chunk: int = 64):
+        """Drives the engine until no request is active or queued."""
+        while True:
+            a, q = self.progress(chunk)
+            if a == 0 and q == 0:
+                return
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            lib().sg_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sg_last_error(ctx: Ctx = None) -> str:

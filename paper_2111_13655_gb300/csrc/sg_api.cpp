@@ -149,6 +149,24 @@ sg_status plan(int D, int L, const sg_basis *basis, const sg_grid *grids,
 
 }  // namespace
 
+namespace sg {
+
+int64_t planned_device_bytes(const sg_ctx *ctx)
+{
+    const HostTables &T = ctx->host;
+    const Problem &p = ctx->prob;
+    auto b = [](const auto &v) { return (int64_t)v.size() * (int64_t)sizeof(v[0]); };
+    int64_t bytes = b(T.levels) + b(T.coefs) + b(T.order) + b(T.rank_tab) + b(T.lmin_tab) + b(T.lvl) +
+                    b(T.tabd) * 3 / 2 + b(p.mcoef) + b(p.mnfac) + b(p.mfoff) + b(p.mfmode) + b(p.mfpow) +
+                    b(T.harm_mono) + b(T.esplit);
+    if (T.fast)
+        bytes += b(T.pair_modes) + b(T.h1off) + b(T.goff) + b(T.ioff) + b(T.soff) + b(T.spoff) + b(T.fsc) +
+                 b(T.ftab) * 3 / 2 + b(T.fdesc) + b(T.fdesc_off) + T.franks * (int64_t)sizeof(int);
+    return bytes;
+}
+
+}  // namespace sg
+
 extern "C" {
 
 sg_status sg_plan(int D, int L, const sg_basis *basis, const sg_grid *grids,

@@ -1,0 +1,468 @@
+// Propagation server (declared in include/smolyak.h): continuous batching of
+// Chebyshev propagation requests of different D, L and basis sizes.
+//
+// Each engine iteration
+//   1. retires requests whose last step has ended (psi and logs to the host),
+//   2. admits queued requests, first come first served, while their planned
+//      device memory fits the budget (context tables, M^B, state vectors,
+//      batch workspace): builds the context, the spectral interval and the
+//      Chebyshev weights,
+//   3. on any change of the active set, rebuilds the batch over the active
+//      contexts and moves the surviving states to the new layout,
+//   4. applies H_S to every active request's current Chebyshev vector in one
+//      sg_apply_H_batch (all requests' terms in one launch per kernel form),
+//   5. advances every request's recurrence by one term in one fused kernel.
+// A request's arithmetic is the same whatever else is in the batch (batched
+// applies are bitwise those of the request's own context, the update is
+// elementwise, the logged sums run over the request's own entries in a fixed
+// order), so its results do not depend on the mix.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <deque>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sg_internal.h"
+
+namespace {
+
+double now_s()
+{
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Req {
+    int64_t id = 0;
+    int state = SG_REQ_QUEUED;
+    // problem (deep copy of the request)
+    int D = 0, L = 0;
+    std::vector<sg_basis> basis;
+    std::vector<sg_grid> grids;
+    std::vector<double> omega, coef;
+    std::vector<int> nfac, mode, power;
+    std::vector<double> psi0;  // 2 * n_cs: real part, imaginary part
+    double dt = 0;
+    int nsteps = 0, order = 0;
+    int64_t n_cs = 0, bytes = 0;
+    // while active
+    sg_ctx *ctx = nullptr;
+    double ebar = 0, de = 1, cph = 1, sph = 0;
+    std::vector<double> c;     // (2 - delta_k0) J_k, k = 0..K
+    int K = 1, step = 0, k = 0;
+    double *d_log = nullptr;   // [nsteps][norm, energy]
+    bool fresh = false;        // psi0 not yet in the state buffers
+    int64_t off = 0;           // complex-entry offset in the current layout
+    // results
+    std::vector<double> psi, log;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    std::string error;
+};
+
+}  // namespace
+
+struct sg_server {
+    sg_precision prec = SG_FP64;
+    int device = 0;
+    int64_t budget = 0, used = 0;
+    cudaStream_t stream = nullptr;
+    int64_t next_id = 1;
+    std::map<int64_t, Req *> all;
+    std::deque<Req *> queue;
+    std::vector<Req *> active;
+    sg_batch *batch = nullptr;
+    bool dirty = false;
+    // state buffers over the active requests (batch layout, nvec = 2)
+    double *X = nullptr, *Y = nullptr, *P = nullptr, *A = nullptr;
+    int64_t total = 0;
+    sg::ChebItem *d_items = nullptr;
+    sg::ChebLog *d_logs = nullptr;
+    long long *d_prefix = nullptr;
+    int64_t iterations = 0, applications = 0;
+    std::string last_error;
+};
+
+namespace {
+
+sg_status sfail(sg_server *s, sg_status st, const std::string &m)
+{
+    s->last_error = m;
+    return st;
+}
+
+void free_state(sg_server *s)
+{
+    for (double **p : {&s->X, &s->Y, &s->P, &s->A})
+        if (*p) { cudaFree(*p); *p = nullptr; }
+    if (s->d_items) cudaFree(s->d_items);
+    if (s->d_logs) cudaFree(s->d_logs);
+    if (s->d_prefix) cudaFree(s->d_prefix);
+    s->d_items = nullptr;
+    s->d_logs = nullptr;
+    s->d_prefix = nullptr;
+    s->total = 0;
+}
+
+void release(sg_server *s, Req *r)
+{
+    if (r->ctx) sg_destroy(r->ctx);
+    r->ctx = nullptr;
+    if (r->d_log) cudaFree(r->d_log);
+    r->d_log = nullptr;
+    s->used -= r->bytes;
+}
+
+sg_status make_ctx(Req *r, sg_precision prec, bool device, sg_ctx **out)
+{
+    sg_poly V{(int)r->coef.size(), r->coef.data(), r->nfac.data(), r->mode.data(), r->power.data()};
+    sg_hamiltonian H{r->omega.data(), V};
+    return device ? sg_create(r->D, r->L, r->basis.data(), r->grids.data(), &H, prec, out)
+                  : sg_plan(r->D, r->L, r->basis.data(), r->grids.data(), &H, prec, out);
+}
+
+// Spectral interval, Chebyshev weights and per-step constants of an admitted request.
+sg_status prepare(sg_server *s, Req *r)
+{
+    double emin = 0, emax = 0;
+    sg_status st = sg::chebyshev_bounds(r->ctx, s->stream, &emin, &emax);
+    if (st != SG_OK) return st;
+    r->ebar = 0.5 * (emax + emin);
+    r->de = 0.5 * (emax - emin);
+    const std::vector<double> J = sg::bessel_j(r->order, r->de * r->dt);
+    int kend = r->order;  // skip terms whose Bessel weight is below double precision
+    while (kend > 1 && kend > r->de * r->dt && std::fabs(J[kend]) < 1e-17) kend--;
+    r->K = kend;
+    r->c.assign(kend + 1, 0.0);
+    for (int k = 0; k <= kend; k++) r->c[k] = (k == 0 ? 1.0 : 2.0) * J[k];
+    r->cph = std::cos(r->ebar * r->dt);
+    r->sph = -std::sin(r->ebar * r->dt);
+    return SG_OK;
+}
+
+// New layout over the active requests; copies the surviving states and uploads new ones.
+sg_status relayout(sg_server *s)
+{
+    cudaError_t e;
+    if (s->batch) { sg_batch_destroy(s->batch); s->batch = nullptr; }
+    std::vector<long long> prefix(s->active.size() + 1, 0);
+    for (size_t j = 0; j < s->active.size(); j++) prefix[j + 1] = prefix[j] + s->active[j]->n_cs;
+    const int64_t total = prefix.back();
+    double *nb[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (total > 0) {
+        for (double *&p : nb)
+            if ((e = cudaMalloc(&p, sizeof(double) * 2 * (size_t)total)) != cudaSuccess) {
+                for (double *q : nb) if (q) cudaFree(q);
+                return sfail(s, SG_ENOMEM, std::string("server state cudaMalloc: ") + cudaGetErrorString(e));
+            }
+    }
+    double *old[4] = {s->X, s->Y, s->P, s->A};
+    for (size_t j = 0; j < s->active.size(); j++) {
+        Req *r = s->active[j];
+        const size_t bytes = sizeof(double) * 2 * (size_t)r->n_cs;
+        const int64_t no = prefix[j];
+        if (r->fresh) {
+            e = cudaMemcpyAsync(nb[0] + 2 * no, r->psi0.data(), bytes, cudaMemcpyHostToDevice, s->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // psi0 may be released next
+            if (e != cudaSuccess) return sfail(s, SG_ECUDA, std::string("psi0 upload: ") + cudaGetErrorString(e));
+            r->fresh = false;
+            std::vector<double>().swap(r->psi0);
+        } else {
+            for (int b : {0, 2, 3})
+                if ((e = cudaMemcpyAsync(nb[b] + 2 * no, old[b] + 2 * r->off, bytes, cudaMemcpyDeviceToDevice,
+                                         s->stream)) != cudaSuccess)
+                    return sfail(s, SG_ECUDA, std::string("state move: ") + cudaGetErrorString(e));
+        }
+        r->off = no;
+    }
+    if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
+        return sfail(s, SG_ECUDA, std::string("relayout sync: ") + cudaGetErrorString(e));
+    free_state(s);
+    s->X = nb[0]; s->Y = nb[1]; s->P = nb[2]; s->A = nb[3];
+    s->total = total;
+    const size_t na = std::max<size_t>(1, s->active.size());
+    if ((e = cudaMalloc(&s->d_items, sizeof(sg::ChebItem) * na)) != cudaSuccess ||
+        (e = cudaMalloc(&s->d_logs, sizeof(sg::ChebLog) * na)) != cudaSuccess ||
+        (e = cudaMalloc(&s->d_prefix, sizeof(long long) * (na + 1))) != cudaSuccess)
+        return sfail(s, SG_ENOMEM, std::string("server tables cudaMalloc: ") + cudaGetErrorString(e));
+    if ((e = cudaMemcpy(s->d_prefix, prefix.data(), sizeof(long long) * prefix.size(), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return sfail(s, SG_ECUDA, std::string("prefix upload: ") + cudaGetErrorString(e));
+    if (!s->active.empty()) {
+        std::vector<sg_ctx *> ctxs;
+        for (Req *r : s->active) ctxs.push_back(r->ctx);
+        sg_status st = sg_batch_create(ctxs.data(), (int)ctxs.size(), &s->batch);
+        if (st != SG_OK) return sfail(s, st, "sg_batch_create over the active requests failed");
+    }
+    s->dirty = false;
+    return SG_OK;
+}
+
+void retire(sg_server *s)
+{
+    std::vector<Req *> keep;
+    for (Req *r : s->active) {
+        if (r->step < r->nsteps) { keep.push_back(r); continue; }
+        r->psi.resize(2 * (size_t)r->n_cs);
+        r->log.resize(2 * (size_t)r->nsteps);
+        cudaError_t e = cudaMemcpy(r->psi.data(), s->X + 2 * r->off, sizeof(double) * r->psi.size(),
+                                   cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && r->nsteps > 0)
+            e = cudaMemcpy(r->log.data(), r->d_log, sizeof(double) * r->log.size(), cudaMemcpyDeviceToHost);
+        int derr = 0;
+        if (e == cudaSuccess) sg_device_error(r->ctx, &derr);
+        r->state = (e == cudaSuccess && derr == 0) ? SG_REQ_DONE : SG_REQ_FAILED;
+        if (e != cudaSuccess) r->error = cudaGetErrorString(e);
+        else if (derr) r->error = "device error " + std::to_string(derr);
+        r->t_done = now_s();
+        release(s, r);
+        s->dirty = true;
+    }
+    s->active.swap(keep);
+}
+
+sg_status admit(sg_server *s)
+{
+    while (!s->queue.empty() && s->used + s->queue.front()->bytes <= s->budget) {
+        Req *r = s->queue.front();
+        s->queue.pop_front();
+        r->t_admit = now_s();
+        if (r->nsteps == 0) {  // nothing to propagate: the result is the initial state
+            r->psi.swap(r->psi0);
+            r->state = SG_REQ_DONE;
+            r->t_done = now_s();
+            continue;
+        }
+        s->used += r->bytes;
+        sg_status st = make_ctx(r, s->prec, true, &r->ctx);
+        if (st == SG_OK) st = prepare(s, r);
+        cudaError_t e = cudaSuccess;
+        if (st == SG_OK) {
+            e = cudaMalloc(&r->d_log, sizeof(double) * 2 * (size_t)r->nsteps);
+            if (e != cudaSuccess) st = SG_ENOMEM;
+        }
+        if (st != SG_OK) {
+            r->state = SG_REQ_FAILED;
+            r->error = r->ctx ? sg_last_error(r->ctx) : sg_last_error(nullptr);
+            if (r->error.empty() && e != cudaSuccess) r->error = cudaGetErrorString(e);
+            r->t_done = now_s();
+            release(s, r);
+            continue;
+        }
+        r->state = SG_REQ_ACTIVE;
+        r->fresh = true;
+        r->step = 0;
+        r->k = 0;
+        s->active.push_back(r);
+        s->dirty = true;
+    }
+    return SG_OK;
+}
+
+// One batched application and recurrence update over the active requests.
+sg_status iterate(sg_server *s)
+{
+    cudaError_t e;
+    const int na = (int)s->active.size();
+    sg_status st = sg_apply_H_batch(s->batch, s->X, s->Y, 2, s->stream);
+    if (st != SG_OK) return sfail(s, st, std::string("batched apply: ") + sg_batch_last_error(s->batch));
+    std::vector<sg::ChebItem> items(na);
+    std::vector<sg::ChebLog> logs;
+    for (int j = 0; j < na; j++) {
+        Req *r = s->active[j];
+        if (r->k == 0) logs.push_back({(long long)r->off, (long long)r->n_cs, r->d_log + 2 * (size_t)r->step});
+        const int kn = r->k + 1;
+        sg::ChebItem &it = items[j];
+        it.ebar = r->ebar;
+        it.inv_de = 1.0 / r->de;
+        it.c0 = r->c[0];
+        it.c_new = r->c[kn];
+        it.cph = r->cph;
+        it.sph = r->sph;
+        it.q = kn & 3;
+        it.first = r->k == 0;
+        it.finish = kn == r->K;
+        it.pad = 0;
+    }
+    if (!logs.empty()) {
+        if ((e = cudaMemcpyAsync(s->d_logs, logs.data(), sizeof(sg::ChebLog) * logs.size(), cudaMemcpyHostToDevice,
+                                 s->stream)) != cudaSuccess ||
+            (e = sg::launch_cheb_log(s->d_logs, (int)logs.size(), s->X, s->Y, s->stream)) != cudaSuccess)
+            return sfail(s, SG_ECUDA, std::string("log: ") + cudaGetErrorString(e));
+    }
+    if ((e = cudaMemcpyAsync(s->d_items, items.data(), sizeof(sg::ChebItem) * na, cudaMemcpyHostToDevice,
+                             s->stream)) != cudaSuccess ||
+        (e = sg::launch_cheb_update(s->d_items, s->d_prefix, na, s->total, s->X, s->Y, s->P, s->A, s->stream)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
+        return sfail(s, SG_ECUDA, std::string("update: ") + cudaGetErrorString(e));
+    std::swap(s->X, s->P);
+    for (Req *r : s->active) {
+        if (r->k + 1 == r->K) { r->k = 0; r->step++; }
+        else r->k++;
+    }
+    s->iterations++;
+    s->applications += 2 * (int64_t)na;
+    return SG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sg_status sg_server_create(sg_precision prec, int64_t hbm_budget_bytes, sg_server **out)
+{
+    if (!out) return SG_EINVAL;
+    *out = nullptr;
+    if ((prec != SG_FP64 && prec != SG_MIXED) || hbm_budget_bytes <= 0) return SG_EINVAL;
+    sg_server *s = new (std::nothrow) sg_server;
+    if (!s) return SG_ENOMEM;
+    s->prec = prec;
+    s->budget = hbm_budget_bytes;
+    if (cudaGetDevice(&s->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete s;
+        return SG_ECUDA;
+    }
+    *out = s;
+    return SG_OK;
+}
+
+sg_status sg_server_submit(sg_server *s, const sg_prop_request *q, int64_t *id)
+{
+    if (!s) return SG_EINVAL;
+    if (!q || !id || !q->basis || !q->grids || !q->H || !q->H->omega || q->nsteps < 0 || q->order < 1 ||
+        !std::isfinite(q->dt) || (!q->psi0 && !q->factors))
+        return sfail(s, SG_EINVAL, "sg_server_submit: invalid request");
+    Req *r = new (std::nothrow) Req;
+    if (!r) return SG_ENOMEM;
+    r->D = q->D;
+    r->L = q->L;
+    if (r->D < 1 || r->D > sg::kMaxD) { delete r; return sfail(s, SG_EINVAL, "sg_server_submit: D out of range"); }
+    r->basis.assign(q->basis, q->basis + r->D);
+    r->grids.assign(q->grids, q->grids + r->D);
+    r->omega.assign(q->H->omega, q->H->omega + r->D);
+    const sg_poly &V = q->H->V;
+    int nf = 0;
+    for (int m = 0; m < V.nterms; m++) nf += V.nfac[m];
+    r->coef.assign(V.coef, V.coef + V.nterms);
+    r->nfac.assign(V.nfac, V.nfac + V.nterms);
+    r->mode.assign(V.mode, V.mode + nf);
+    r->power.assign(V.power, V.power + nf);
+    r->dt = q->dt;
+    r->nsteps = q->nsteps;
+    r->order = q->order;
+    sg_ctx *plan = nullptr;
+    sg_status st = make_ctx(r, s->prec, false, &plan);
+    if (st != SG_OK) {
+        delete r;
+        return sfail(s, st, std::string("sg_server_submit: ") + sg_last_error(nullptr));
+    }
+    int64_t n_cs = 0, n_terms = 0;
+    sg_size(plan, &n_cs, &n_terms, nullptr, nullptr, nullptr);
+    r->n_cs = n_cs;
+    r->psi0.assign(2 * (size_t)n_cs, 0.0);
+    if (q->psi0) std::copy(q->psi0, q->psi0 + 2 * n_cs, r->psi0.begin());
+    else st = sg_product_state(plan, q->factors, q->ld, r->psi0.data());
+    // tables + M^B + batch items + 4 state vectors, the batch workspace (2
+    // vectors x 4 fixed-point words), the context's own one-vector workspace
+    // (left by the spectral-bound run) + logs
+    r->bytes = sg::planned_device_bytes(plan) + 8 * n_terms + 2 * n_cs * (4 * 8 + 32) + 32 * n_cs +
+               16 * (int64_t)r->nsteps + ((int64_t)1 << 20);
+    sg_destroy(plan);
+    if (st != SG_OK) { delete r; return sfail(s, st, "sg_server_submit: bad initial-state factors"); }
+    if (r->bytes > s->budget) {
+        const int64_t b = r->bytes;
+        delete r;
+        return sfail(s, SG_EBUDGET, "sg_server_submit: request needs " + std::to_string(b) +
+                                        " bytes of device memory, over the budget");
+    }
+    r->id = s->next_id++;
+    r->t_submit = now_s();
+    s->all[r->id] = r;
+    s->queue.push_back(r);
+    *id = r->id;
+    return SG_OK;
+}
+
+sg_status sg_server_progress(sg_server *s, int max_iters, int *n_active, int *n_queued)
+{
+    if (!s || max_iters < 0) return SG_EINVAL;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != s->device)
+        return sfail(s, SG_EINVAL, "sg_server_progress: the server's device is not current");
+    sg_status st = SG_OK;
+    for (int it = 0; it < max_iters; it++) {
+        retire(s);
+        admit(s);
+        if (s->dirty && (st = relayout(s)) != SG_OK) break;
+        if (s->active.empty()) break;
+        if ((st = iterate(s)) != SG_OK) break;
+    }
+    if (st == SG_OK) retire(s);
+    if (n_active) *n_active = (int)s->active.size();
+    if (n_queued) *n_queued = (int)s->queue.size();
+    return st;
+}
+
+sg_status sg_server_query(const sg_server *s, int64_t id, int *state, int64_t *n_cs, int *steps_done)
+{
+    if (!s) return SG_EINVAL;
+    auto f = s->all.find(id);
+    if (f == s->all.end()) return SG_EINVAL;
+    const Req *r = f->second;
+    if (state) *state = r->state;
+    if (n_cs) *n_cs = r->n_cs;
+    if (steps_done) *steps_done = r->step;
+    return SG_OK;
+}
+
+sg_status sg_server_result(sg_server *s, int64_t id, double *psi_host, double *norm_log, double *energy_log,
+                           double *times)
+{
+    if (!s) return SG_EINVAL;
+    auto f = s->all.find(id);
+    if (f == s->all.end()) return sfail(s, SG_EINVAL, "sg_server_result: unknown id");
+    Req *r = f->second;
+    if (r->state == SG_REQ_FAILED) return sfail(s, SG_ECUDA, "request failed: " + r->error);
+    if (r->state != SG_REQ_DONE) return sfail(s, SG_EINVAL, "sg_server_result: request not finished");
+    if (psi_host) std::copy(r->psi.begin(), r->psi.end(), psi_host);
+    for (int k = 0; k < r->nsteps; k++) {
+        if (norm_log) norm_log[k] = r->log[2 * (size_t)k];
+        if (energy_log) energy_log[k] = r->log[2 * (size_t)k + 1];
+    }
+    if (times) {
+        times[0] = r->t_admit - r->t_submit;
+        times[1] = r->t_done - r->t_submit;
+    }
+    return SG_OK;
+}
+
+sg_status sg_server_stats(const sg_server *s, int64_t *iterations, int64_t *applications, int64_t *bytes_in_use)
+{
+    if (!s) return SG_EINVAL;
+    if (iterations) *iterations = s->iterations;
+    if (applications) *applications = s->applications;
+    if (bytes_in_use) *bytes_in_use = s->used;
+    return SG_OK;
+}
+
+const char *sg_server_last_error(const sg_server *s)
+{
+    return s ? s->last_error.c_str() : "";
+}
+
+void sg_server_destroy(sg_server *s)
+{
+    if (!s) return;
+    for (Req *r : s->active) release(s, r);
+    if (s->batch) sg_batch_destroy(s->batch);
+    free_state(s);
+    for (auto &kv : s->all) delete kv.second;
+    if (s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+}  // extern "C"

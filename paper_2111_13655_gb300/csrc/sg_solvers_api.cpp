@@ -247,6 +247,53 @@ int block_eigs(Solver &S, int nev, int b, bool davidson, double tol, int max_it,
     return nconv;
 }
 
+// Spectral interval of H_S for the Chebyshev propagator: a 40-vector Krylov
+// run (Rayleigh-Ritz), the extreme Ritz values widened by their residual norms
+// and by 5% of the range.  Deterministic (fixed start vector, ordered sums).
+void spectral_bounds(Solver &S, double &emin, double &emax)
+{
+    const int64_t n = S.n;
+    const int ks = (int)std::min<int64_t>(n, 40);
+    {
+        DBuf V((size_t)(ks + 1) * n), W((size_t)(ks + 1) * n), Xr(2 * (size_t)n), HXr(2 * (size_t)n);
+        S.random_block(V.p, 1, 0xc4eb00ull);
+        S.orthonormalise(V.p, 1);
+        std::vector<double> Tm;
+        int k = 0;
+        for (int it = 0; it < ks; it++) {
+            S.apply(V.p + (size_t)k * n, W.p + (size_t)k * n, 1);
+            std::vector<double> C = S.gram(V.p, k + 1, W.p + (size_t)k * n, 1);
+            std::vector<double> Tn((size_t)(k + 1) * (k + 1));
+            for (int i = 0; i < k; i++)
+                for (int j = 0; j < k; j++) Tn[(size_t)i * (k + 1) + j] = Tm[(size_t)i * k + j];
+            for (int i = 0; i <= k; i++) Tn[(size_t)i * (k + 1) + k] = Tn[(size_t)k * (k + 1) + i] = C[i];
+            Tm.swap(Tn);
+            k++;
+            if (k >= ks) break;
+            ck(cudaMemcpyAsync(V.p + (size_t)k * n, W.p + (size_t)(k - 1) * n, sizeof(double) * n,
+                               cudaMemcpyDeviceToDevice, S.s), "krylov copy");
+            S.orth_against(V.p, k, V.p + (size_t)k * n, 1);
+            if (S.orthonormalise(V.p + (size_t)k * n, 1) == 0) break;
+        }
+        std::vector<double> th, Z;
+        sym_eig(k, Tm, th, Z);
+        double rlo = 0, rhi = 0;
+        for (int end = 0; end < 2; end++) {
+            const int j = end == 0 ? 0 : k - 1;
+            std::vector<double> z(k);
+            for (int i = 0; i < k; i++) z[i] = Z[(size_t)i * k + j];
+            S.combine(V.p, k, z, 1, 1.0, 0.0, Xr.p);
+            S.combine(W.p, k, z, 1, 1.0, 0.0, HXr.p);
+            ck(dev_axpby(n, -th[j], Xr.p, 1.0, HXr.p, S.s), "bound resid");
+            const double rr = S.norms(HXr.p, 1)[0];
+            (end == 0 ? rlo : rhi) = rr;
+        }
+        const double range = th[k - 1] - th[0];
+        emin = th[0] - rlo - 0.05 * range;
+        emax = th[k - 1] + rhi + 0.05 * range;
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -334,49 +381,8 @@ sg_status sg_propagate(sg_ctx *ctx, double *psi, double dt, int nsteps, int orde
     try {
         Solver S(ctx, (cudaStream_t)stream, 48);
         const int64_t n = S.n;
-        // spectral bounds from a 40-step Krylov run (Rayleigh-Ritz), widened by the
-        // extreme residuals and 5% of the range
-        const int ks = (int)std::min<int64_t>(n, 40);
-        std::vector<double> ev(ks), rs(ks);
         double emin, emax;
-        {
-            DBuf V((size_t)(ks + 1) * n), W((size_t)(ks + 1) * n), Xr(2 * (size_t)n), HXr(2 * (size_t)n);
-            S.random_block(V.p, 1, 0xc4eb00ull);
-            S.orthonormalise(V.p, 1);
-            std::vector<double> Tm;
-            int k = 0;
-            for (int it = 0; it < ks; it++) {
-                S.apply(V.p + (size_t)k * n, W.p + (size_t)k * n, 1);
-                std::vector<double> C = S.gram(V.p, k + 1, W.p + (size_t)k * n, 1);
-                std::vector<double> Tn((size_t)(k + 1) * (k + 1));
-                for (int i = 0; i < k; i++)
-                    for (int j = 0; j < k; j++) Tn[(size_t)i * (k + 1) + j] = Tm[(size_t)i * k + j];
-                for (int i = 0; i <= k; i++) Tn[(size_t)i * (k + 1) + k] = Tn[(size_t)k * (k + 1) + i] = C[i];
-                Tm.swap(Tn);
-                k++;
-                if (k >= ks) break;
-                ck(cudaMemcpyAsync(V.p + (size_t)k * n, W.p + (size_t)(k - 1) * n, sizeof(double) * n,
-                                   cudaMemcpyDeviceToDevice, S.s), "krylov copy");
-                S.orth_against(V.p, k, V.p + (size_t)k * n, 1);
-                if (S.orthonormalise(V.p + (size_t)k * n, 1) == 0) break;
-            }
-            std::vector<double> th, Z;
-            sym_eig(k, Tm, th, Z);
-            double rlo = 0, rhi = 0;
-            for (int end = 0; end < 2; end++) {
-                const int j = end == 0 ? 0 : k - 1;
-                std::vector<double> z(k);
-                for (int i = 0; i < k; i++) z[i] = Z[(size_t)i * k + j];
-                S.combine(V.p, k, z, 1, 1.0, 0.0, Xr.p);
-                S.combine(W.p, k, z, 1, 1.0, 0.0, HXr.p);
-                ck(dev_axpby(n, -th[j], Xr.p, 1.0, HXr.p, S.s), "bound resid");
-                const double rr = S.norms(HXr.p, 1)[0];
-                (end == 0 ? rlo : rhi) = rr;
-            }
-            const double range = th[k - 1] - th[0];
-            emin = th[0] - rlo - 0.05 * range;
-            emax = th[k - 1] + rhi + 0.05 * range;
-        }
+        spectral_bounds(S, emin, emax);
         const double Ebar = 0.5 * (emax + emin), dE = 0.5 * (emax - emin);
         const std::vector<double> J = bessel_j(order, dE * dt);
         int kend = order;  // skip terms whose Bessel weight is below double precision
@@ -436,3 +442,20 @@ sg_status sg_propagate(sg_ctx *ctx, double *psi, double dt, int nsteps, int orde
 }
 
 }  // extern "C"
+
+namespace sg {
+
+sg_status chebyshev_bounds(sg_ctx *ctx, cudaStream_t stream, double *emin, double *emax)
+{
+    try {
+        Solver S(ctx, stream, 48);
+        spectral_bounds(S, *emin, *emax);
+        ck(cudaStreamSynchronize(S.s), "bounds sync");
+    } catch (const SolverError &e) {
+        ctx->last_error = e.msg;
+        return e.st;
+    }
+    return SG_OK;
+}
+
+}  // namespace sg
