@@ -210,6 +210,56 @@ def replica_throughput(world: int, units_per_rank: int, slowest_seconds: float) 
     return world * units_per_rank / slowest_seconds
 
 
+def run_serving(args, sg, synth, torch):
+    """Poisson stream of propagation requests through the server (mixed
+    precision, continuous batching) against the same requests run one at a
+    time with sg_propagate in FP64."""
+    items = synth.workload_C5(args.serve_requests, seed=5, Ds=tuple(range(6, args.serve_dmax + 1)),
+                              Ls=tuple(range(4, args.serve_lmax + 1)), steps=(20, args.serve_steps_max))
+    arrivals = np.cumsum(np.random.Generator(np.random.PCG64(55)).exponential(1.0 / args.serve_rate, len(items)))
+    factors = [synth.coherent_factors(q0, p.L + 1) for p, q0, _ in items]
+    srv = sg.Server("mixed", hbm_budget_bytes=150 * 10**9)
+    ids = []
+    t0 = time.perf_counter()
+    i = 0
+    while True:
+        now = time.perf_counter() - t0
+        while i < len(items) and arrivals[i] <= now:
+            p, q0, ns = items[i]
+            ids.append(srv.submit(p, 0.1, ns, order=64, factors=factors[i]))
+            i += 1
+        a, q = srv.progress(16)
+        if a == 0 and q == 0:
+            if i == len(items):
+                break
+            time.sleep(max(0.0, arrivals[i] - (time.perf_counter() - t0)))
+    makespan = time.perf_counter() - t0
+    lat = np.array([srv.result(r)[3][1] for r in ids])
+    apps = srv.stats()["applications"]
+    srv.close()
+    # the same requests, one at a time, FP64 sg_propagate
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for (p, q0, ns), f in zip(items, factors):
+        with sg.sg_create(p, "fp64") as ctx:
+            psi = sg.sg_product_state(ctx, f)
+            d = torch.from_numpy(np.concatenate([psi, np.zeros_like(psi)])).cuda()
+            sg.sg_propagate(ctx, d, 0.1, ns, order=64)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t1
+    desc = (f"{len(items)} chained Henon-Heiles propagation requests, D uniform in 6..{args.serve_dmax}, "
+            f"L uniform in 4..{args.serve_lmax}, nb=nq=l+1, steps uniform in 20..{args.serve_steps_max}, "
+            f"order 64, dt 0.1, Poisson arrivals at {args.serve_rate:g} req/s, budget 150 GB")
+    return {"workload": desc, "precision": "mixed (server, continuous batching)",
+            "applications_per_s": apps / makespan, "requests_per_s": len(items) / makespan,
+            "makespan_s": makespan, "latency_s": {"p50": float(np.percentile(lat, 50)),
+                                                  "p99": float(np.percentile(lat, 99))},
+            "per_request_fp64": {"applications_per_s": apps / t_seq, "requests_per_s": len(items) / t_seq,
+                                 "seconds": t_seq,
+                                 "note": "same requests in arrival order, sg_propagate FP64, one at a time; "
+                                         "applications counted as in the server run"}}
+
+
 def time_device(ctx, xd, yd, nvec, steps, warmup, flush, torch, sg):
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
@@ -236,6 +286,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-dmax", type=int, default=20)
+    ap.add_argument("--serve-lmax", type=int, default=6)
+    ap.add_argument("--serve-steps-max", type=int, default=100)
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -313,6 +369,10 @@ def main():
         del xd, yd, flush
         torch.cuda.empty_cache()
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = run_serving(args, sg, synth, torch)
+
     if rank == 0:
         m = results["mixed"]
         f = results["fp64"]
@@ -326,7 +386,7 @@ def main():
                 "e2e": m["e2e"], "gpu_launches": LAUNCHES_PER_APPLY * m["steps"],
                 "fp64": {"value": f["value"], "unit": UNIT, "ms_per_step": f["ms_per_step"], "steps": f["steps"],
                          "latency_ms": f["latency_ms"], "roofline": f["roofline"], "clocks": f["clocks"]},
-                "cpu_baseline": cpu}
+                "cpu_baseline": cpu, "serving": serving}
         print(json.dumps(line), flush=True)
     rep.close()
     return 0

@@ -193,25 +193,20 @@ cudaError_t launch_maxabs_batch(const double *x, const long long *cs_prefix, int
 cudaError_t launch_finalize_batch(const KParams *kps, const long long *cs_prefix, int nprob, int64_t total_cs,
                                   const double *x, double *y, unsigned long long *acc, const long long *maxbits,
                                   int nvec, cudaStream_t stream);
-// Propagation server (sg_server_api.cpp, sg_server.cu).  One Chebyshev update of a
-// request after Y = H X: forms T_{k_new} (k_new = 1 from T_0 when `first`),
-// adds c_new (-i)^q T_{k_new} to the partial sum, and on the step's last term
-// (`finish`) writes e^{-i Ebar dt} * sum instead.
-struct ChebItem {
+// Propagation server (sg_server_api.cpp, sg_server.cu): device state of one
+// active request's Chebyshev recurrence.  One iteration after Y = H X logs
+// norm and energy for requests at k = 0, forms T_{k+1} (T_1 from T_0 when
+// k = 0), adds c_{k+1} (-i)^{k+1} T_{k+1} to the partial sum and, on the
+// step's last term (k + 1 = K), writes e^{-i Ebar dt} * sum; then k, step advance.
+struct ChebState {
+    int k, K, step, nsteps;
     double ebar, inv_de;   // (H - ebar) * inv_de maps the spectrum into [-1, 1]
-    double c0, c_new;      // (2 - delta_k0) J_k(dE dt) for k = 0 and k = k_new
     double cph, sph;       // e^{-i Ebar dt} = cph + i sph
-    int q;                 // k_new mod 4
-    int first, finish;
-    int pad;
+    const double *c;       // device: (2 - delta_k0) J_k(dE dt), k = 0..K
+    double *log;           // device: [nsteps][norm, energy]
 };
-struct ChebLog {
-    long long off, n;      // the request's complex entries start at off (of the batch layout)
-    double *out;           // device: [norm, energy]
-};
-cudaError_t launch_cheb_update(const ChebItem *items, const long long *prefix, int nitems, int64_t total,
-                               const double *X, const double *Y, double *P, double *A, cudaStream_t s);
-cudaError_t launch_cheb_log(const ChebLog *logs, int nlogs, const double *X, const double *Y, cudaStream_t s);
+cudaError_t launch_cheb_iteration(ChebState *st, const long long *prefix, int nitems, int64_t total,
+                                  const double *X, const double *Y, double *P, double *A, cudaStream_t s);
 // Chebyshev spectral interval of a context's H_S (Krylov, as sg_propagate); synchronous.
 sg_status chebyshev_bounds(sg_ctx *ctx, cudaStream_t stream, double *emin, double *emax);
 // J_0..J_kmax at x (Miller's backward recurrence).

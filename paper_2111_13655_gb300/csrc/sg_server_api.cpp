@@ -18,6 +18,7 @@
 // order), so its results do not depend on the mix.
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <deque>
 #include <map>
@@ -54,6 +55,7 @@ struct Req {
     std::vector<double> c;     // (2 - delta_k0) J_k, k = 0..K
     int K = 1, step = 0, k = 0;
     double *d_log = nullptr;   // [nsteps][norm, energy]
+    double *d_c = nullptr;     // device copy of c
     bool fresh = false;        // psi0 not yet in the state buffers
     int64_t off = 0;           // complex-entry offset in the current layout
     // results
@@ -78,9 +80,13 @@ struct sg_server {
     // state buffers over the active requests (batch layout, nvec = 2)
     double *X = nullptr, *Y = nullptr, *P = nullptr, *A = nullptr;
     int64_t total = 0;
-    sg::ChebItem *d_items = nullptr;
-    sg::ChebLog *d_logs = nullptr;
+    sg::ChebState *d_state = nullptr;
     long long *d_prefix = nullptr;
+    // two engine iterations (roles X -> P, then back), replayed between changes of
+    // the active set; one graph per assignment of the two buffers to X
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+    const double *graph_x[2] = {nullptr, nullptr};
     int64_t iterations = 0, applications = 0;
     std::string last_error;
 };
@@ -97,13 +103,18 @@ void free_state(sg_server *s)
 {
     for (double **p : {&s->X, &s->Y, &s->P, &s->A})
         if (*p) { cudaFree(*p); *p = nullptr; }
-    if (s->d_items) cudaFree(s->d_items);
-    if (s->d_logs) cudaFree(s->d_logs);
+    if (s->d_state) cudaFree(s->d_state);
     if (s->d_prefix) cudaFree(s->d_prefix);
-    s->d_items = nullptr;
-    s->d_logs = nullptr;
+    s->d_state = nullptr;
     s->d_prefix = nullptr;
     s->total = 0;
+    for (int g = 0; g < 2; g++) {
+        if (s->graph_exec[g]) cudaGraphExecDestroy(s->graph_exec[g]);
+        if (s->graph[g]) cudaGraphDestroy(s->graph[g]);
+        s->graph_exec[g] = nullptr;
+        s->graph[g] = nullptr;
+        s->graph_x[g] = nullptr;
+    }
 }
 
 void release(sg_server *s, Req *r)
@@ -111,7 +122,9 @@ void release(sg_server *s, Req *r)
     if (r->ctx) sg_destroy(r->ctx);
     r->ctx = nullptr;
     if (r->d_log) cudaFree(r->d_log);
+    if (r->d_c) cudaFree(r->d_c);
     r->d_log = nullptr;
+    r->d_c = nullptr;
     s->used -= r->bytes;
 }
 
@@ -183,13 +196,20 @@ sg_status relayout(sg_server *s)
     s->X = nb[0]; s->Y = nb[1]; s->P = nb[2]; s->A = nb[3];
     s->total = total;
     const size_t na = std::max<size_t>(1, s->active.size());
-    if ((e = cudaMalloc(&s->d_items, sizeof(sg::ChebItem) * na)) != cudaSuccess ||
-        (e = cudaMalloc(&s->d_logs, sizeof(sg::ChebLog) * na)) != cudaSuccess ||
+    std::vector<sg::ChebState> state(s->active.size());
+    for (size_t j = 0; j < s->active.size(); j++) {
+        const Req *r = s->active[j];
+        state[j] = sg::ChebState{r->k, r->K, r->step, r->nsteps, r->ebar, 1.0 / r->de, r->cph, r->sph,
+                                 r->d_c, r->d_log};
+    }
+    if ((e = cudaMalloc(&s->d_state, sizeof(sg::ChebState) * na)) != cudaSuccess ||
         (e = cudaMalloc(&s->d_prefix, sizeof(long long) * (na + 1))) != cudaSuccess)
         return sfail(s, SG_ENOMEM, std::string("server tables cudaMalloc: ") + cudaGetErrorString(e));
     if ((e = cudaMemcpy(s->d_prefix, prefix.data(), sizeof(long long) * prefix.size(), cudaMemcpyHostToDevice)) !=
-        cudaSuccess)
-        return sfail(s, SG_ECUDA, std::string("prefix upload: ") + cudaGetErrorString(e));
+            cudaSuccess ||
+        (!state.empty() && (e = cudaMemcpy(s->d_state, state.data(), sizeof(sg::ChebState) * state.size(),
+                                           cudaMemcpyHostToDevice)) != cudaSuccess))
+        return sfail(s, SG_ECUDA, std::string("server tables upload: ") + cudaGetErrorString(e));
     if (!s->active.empty()) {
         std::vector<sg_ctx *> ctxs;
         for (Req *r : s->active) ctxs.push_back(r->ctx);
@@ -202,13 +222,19 @@ sg_status relayout(sg_server *s)
 
 void retire(sg_server *s)
 {
+    bool any = false;
+    for (const Req *r : s->active) any |= r->step >= r->nsteps;
+    if (!any) return;
+    // the iterations run asynchronously on the server's (non-blocking) stream
+    const cudaError_t es = cudaStreamSynchronize(s->stream);
     std::vector<Req *> keep;
     for (Req *r : s->active) {
         if (r->step < r->nsteps) { keep.push_back(r); continue; }
         r->psi.resize(2 * (size_t)r->n_cs);
         r->log.resize(2 * (size_t)r->nsteps);
-        cudaError_t e = cudaMemcpy(r->psi.data(), s->X + 2 * r->off, sizeof(double) * r->psi.size(),
-                                   cudaMemcpyDeviceToHost);
+        cudaError_t e = es;
+        if (e == cudaSuccess)
+            e = cudaMemcpy(r->psi.data(), s->X + 2 * r->off, sizeof(double) * r->psi.size(), cudaMemcpyDeviceToHost);
         if (e == cudaSuccess && r->nsteps > 0)
             e = cudaMemcpy(r->log.data(), r->d_log, sizeof(double) * r->log.size(), cudaMemcpyDeviceToHost);
         int derr = 0;
@@ -241,6 +267,9 @@ sg_status admit(sg_server *s)
         cudaError_t e = cudaSuccess;
         if (st == SG_OK) {
             e = cudaMalloc(&r->d_log, sizeof(double) * 2 * (size_t)r->nsteps);
+            if (e == cudaSuccess) e = cudaMalloc(&r->d_c, sizeof(double) * r->c.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(r->d_c, r->c.data(), sizeof(double) * r->c.size(), cudaMemcpyHostToDevice);
             if (e != cudaSuccess) st = SG_ENOMEM;
         }
         if (st != SG_OK) {
@@ -261,51 +290,70 @@ sg_status admit(sg_server *s)
     return SG_OK;
 }
 
-// One batched application and recurrence update over the active requests.
-sg_status iterate(sg_server *s)
+// One engine iteration with the current roles of X and P: Y = H X over all
+// active requests, then logs, recurrence update (into P) and state advance.
+sg_status enqueue_iteration(sg_server *s, double *X, double *P)
+{
+    sg_status st = sg_apply_H_batch(s->batch, X, s->Y, 2, s->stream);
+    if (st != SG_OK) return sfail(s, st, std::string("batched apply: ") + sg_batch_last_error(s->batch));
+    cudaError_t e = sg::launch_cheb_iteration(s->d_state, s->d_prefix, (int)s->active.size(), s->total, X, s->Y, P,
+                                              s->A, s->stream);
+    if (e != cudaSuccess) return sfail(s, SG_ECUDA, std::string("recurrence update: ") + cudaGetErrorString(e));
+    return SG_OK;
+}
+
+// Runs n iterations over the current active set (none of which passes a
+// request's last step): pairs of iterations as one graph launch, a last odd
+// one launched directly.  Asynchronous.
+sg_status iterate(sg_server *s, int64_t n)
 {
     cudaError_t e;
-    const int na = (int)s->active.size();
-    sg_status st = sg_apply_H_batch(s->batch, s->X, s->Y, 2, s->stream);
-    if (st != SG_OK) return sfail(s, st, std::string("batched apply: ") + sg_batch_last_error(s->batch));
-    std::vector<sg::ChebItem> items(na);
-    std::vector<sg::ChebLog> logs;
-    for (int j = 0; j < na; j++) {
-        Req *r = s->active[j];
-        if (r->k == 0) logs.push_back({(long long)r->off, (long long)r->n_cs, r->d_log + 2 * (size_t)r->step});
-        const int kn = r->k + 1;
-        sg::ChebItem &it = items[j];
-        it.ebar = r->ebar;
-        it.inv_de = 1.0 / r->de;
-        it.c0 = r->c[0];
-        it.c_new = r->c[kn];
-        it.cph = r->cph;
-        it.sph = r->sph;
-        it.q = kn & 3;
-        it.first = r->k == 0;
-        it.finish = kn == r->K;
-        it.pad = 0;
+    sg_status st;
+    int64_t done = 0;
+    int slot = s->graph_x[0] == s->X ? 0 : (s->graph_x[1] == s->X ? 1 : -1);
+    if (slot < 0 && n >= 3) {
+        if (!s->graph_x[0] && !s->graph_x[1]) {
+            // the first iteration sizes the batch workspace outside any capture
+            if ((st = enqueue_iteration(s, s->X, s->P)) != SG_OK) return st;
+            std::swap(s->X, s->P);
+            done = 1;
+        }
+        slot = s->graph_x[0] ? 1 : 0;
+        if ((e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return sfail(s, SG_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+        sg_status s1 = enqueue_iteration(s, s->X, s->P);
+        sg_status s2 = s1 == SG_OK ? enqueue_iteration(s, s->P, s->X) : s1;
+        e = cudaStreamEndCapture(s->stream, &s->graph[slot]);
+        if (s2 != SG_OK) return s2;
+        if (e != cudaSuccess) return sfail(s, SG_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+        if ((e = cudaGraphInstantiate(&s->graph_exec[slot], s->graph[slot], 0)) != cudaSuccess)
+            return sfail(s, SG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        s->graph_x[slot] = s->X;
     }
-    if (!logs.empty()) {
-        if ((e = cudaMemcpyAsync(s->d_logs, logs.data(), sizeof(sg::ChebLog) * logs.size(), cudaMemcpyHostToDevice,
-                                 s->stream)) != cudaSuccess ||
-            (e = sg::launch_cheb_log(s->d_logs, (int)logs.size(), s->X, s->Y, s->stream)) != cudaSuccess)
-            return sfail(s, SG_ECUDA, std::string("log: ") + cudaGetErrorString(e));
+    for (; slot >= 0 && done + 2 <= n; done += 2)
+        if ((e = cudaGraphLaunch(s->graph_exec[slot], s->stream)) != cudaSuccess)
+            return sfail(s, SG_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    for (; done < n; done++) {
+        if ((st = enqueue_iteration(s, s->X, s->P)) != SG_OK) return st;
+        std::swap(s->X, s->P);
     }
-    if ((e = cudaMemcpyAsync(s->d_items, items.data(), sizeof(sg::ChebItem) * na, cudaMemcpyHostToDevice,
-                             s->stream)) != cudaSuccess ||
-        (e = sg::launch_cheb_update(s->d_items, s->d_prefix, na, s->total, s->X, s->Y, s->P, s->A, s->stream)) !=
-            cudaSuccess ||
-        (e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
-        return sfail(s, SG_ECUDA, std::string("update: ") + cudaGetErrorString(e));
-    std::swap(s->X, s->P);
-    for (Req *r : s->active) {
-        if (r->k + 1 == r->K) { r->k = 0; r->step++; }
-        else r->k++;
-    }
-    s->iterations++;
-    s->applications += 2 * (int64_t)na;
+    for (Req *r : s->active)
+        for (int64_t i = 0; i < n; i++) {
+            if (r->k + 1 == r->K) { r->k = 0; r->step++; }
+            else r->k++;
+        }
+    s->iterations += n;
+    s->applications += 2 * (int64_t)s->active.size() * n;
     return SG_OK;
+}
+
+// Iterations until the first active request finishes its last step.
+int64_t until_first_finish(const sg_server *s)
+{
+    int64_t m = INT64_MAX;
+    for (const Req *r : s->active)
+        m = std::min<int64_t>(m, (int64_t)(r->nsteps - r->step - 1) * r->K + (r->K - r->k));
+    return m;
 }
 
 }  // namespace
@@ -394,13 +442,18 @@ sg_status sg_server_progress(sg_server *s, int max_iters, int *n_active, int *n_
     if (cudaGetDevice(&cur) != cudaSuccess || cur != s->device)
         return sfail(s, SG_EINVAL, "sg_server_progress: the server's device is not current");
     sg_status st = SG_OK;
-    for (int it = 0; it < max_iters; it++) {
+    int64_t done = 0;
+    while (done < max_iters) {
         retire(s);
         admit(s);
         if (s->dirty && (st = relayout(s)) != SG_OK) break;
         if (s->active.empty()) break;
-        if ((st = iterate(s)) != SG_OK) break;
+        const int64_t n = std::min<int64_t>(max_iters - done, until_first_finish(s));
+        if ((st = iterate(s, n)) != SG_OK) break;
+        done += n;
     }
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (st == SG_OK && e != cudaSuccess) st = sfail(s, SG_ECUDA, std::string("progress: ") + cudaGetErrorString(e));
     if (st == SG_OK) retire(s);
     if (n_active) *n_active = (int)s->active.size();
     if (n_queued) *n_queued = (int)s->queue.size();
@@ -457,6 +510,7 @@ const char *sg_server_last_error(const sg_server *s)
 void sg_server_destroy(sg_server *s)
 {
     if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
     for (Req *r : s->active) release(s, r);
     if (s->batch) sg_batch_destroy(s->batch);
     free_state(s);

@@ -179,3 +179,23 @@ def workload_C4(n: int = 256, seed: int = 4, Ds=(4, 6, 8, 10, 12), Ls=(6, 7, 8, 
         out.append((chained_henon_heiles(D, L, om, lam, (1, 1), (1, 1),
                                          name=f"HH D={D} L={L} nb=nq=l+1 (batch item {j})"), q0))
     return out
+
+
+def workload_C5(n: int, seed: int = 5, Ds=tuple(range(6, 21)), Ls=(4, 5, 6, 7, 8), steps=(20, 500),
+                lam: float = HH_LAMBDA):
+    """Stream of n propagation requests: D uniform in Ds, L uniform in Ls,
+    chained Henon-Heiles with omega_i ~ U[0.8,1.2], nb = nq = l+1, a Gaussian
+    wavepacket displaced by 2.0 in mode 0, steps uniform in [steps[0], steps[1]]
+    (order 64, dt 0.1).  Returns a list of (Problem, q0, nsteps)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for j in range(n):
+        D = int(g.choice(Ds))
+        L = int(g.choice(Ls))
+        om = g.uniform(0.8, 1.2, size=D)
+        nsteps = int(g.integers(steps[0], steps[1] + 1))
+        q0 = np.zeros(D)
+        q0[0] = 2.0
+        out.append((chained_henon_heiles(D, L, om, lam, (1, 1), (1, 1),
+                                         name=f"HH D={D} L={L} nb=nq=l+1 (request {j})"), q0, nsteps))
+    return out
