@@ -260,6 +260,68 @@ def run_serving(args, sg, synth, torch):
                                          "applications counted as in the server run"}}
 
 
+def run_batched(args, sg, synth, torch):
+    """Many independent wavepacket problems per apply (sg_apply_H_batch) against
+    the same problems applied one after another (sg_apply_H each), mixed and
+    FP64.  Complex wavepackets: two real vectors per instance."""
+    import concurrent.futures as cf
+    items = synth.workload_C4(n=args.batch_instances, seed=4)
+    nvec = 2
+    out = {"workload": f"{len(items)} chained Henon-Heiles wavepackets, D uniform in {{4,6,8,10,12}}, "
+                       f"L uniform in 6..10, nb=nq=l+1, Gaussian centres q0 ~ U[0,2] per mode, "
+                       f"complex (2 real vectors) each",
+           "unit": UNIT}
+    stream = torch.cuda.current_stream()
+    dev = torch.cuda.current_device()
+    for prec in ("mixed", "fp64"):
+        def make(it):
+            torch.cuda.set_device(dev)
+            return sg.sg_create(it[0], prec)
+        with cf.ThreadPoolExecutor(8) as ex:
+            ctxs = list(ex.map(make, items))
+        b = sg.sg_batch_create(ctxs)
+        xs = []
+        for (p, q0), c in zip(items, ctxs):
+            psi = sg.sg_product_state(c, synth.coherent_factors(q0, p.L + 1))
+            psi /= np.linalg.norm(psi)
+            xs.append(np.concatenate([psi, np.roll(psi, 1)]))
+        x = torch.from_numpy(np.concatenate(xs)).cuda()
+        y = torch.empty_like(x)
+        offs = [nvec * int(o) for o in b.offsets]
+        xv = [x[offs[j]:offs[j + 1]] for j in range(len(ctxs))]
+        yv = [y[offs[j]:offs[j + 1]] for j in range(len(ctxs))]
+        res = {}
+        for mode in ("batched", "per_instance"):
+            def step():
+                if mode == "batched":
+                    sg.sg_apply_H_batch(b, x, y, nvec, stream)
+                else:
+                    for c, a, o in zip(ctxs, xv, yv):
+                        sg.sg_apply_H(c, a, o, nvec, stream)
+            for _ in range(3):
+                step()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.batch_steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.batch_steps
+            res[mode] = {"value": len(ctxs) * nvec / (ms * 1e-3), "ms_per_apply": ms}
+        res["launches_per_apply"] = b.launches_per_apply
+        for c in ctxs:
+            if sg.sg_device_error(c):
+                raise RuntimeError(f"device error in the batched {prec} apply")
+        sg.sg_batch_destroy(b)
+        for c in ctxs:
+            sg.sg_destroy(c)
+        del x, y, xv, yv
+        torch.cuda.empty_cache()
+        out[prec] = res
+    return out
+
+
 def time_device(ctx, xd, yd, nvec, steps, warmup, flush, torch, sg):
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
@@ -292,6 +354,9 @@ def main():
     ap.add_argument("--serve-lmax", type=int, default=6)
     ap.add_argument("--serve-steps-max", type=int, default=100)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--batch-instances", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -372,6 +437,9 @@ def main():
     serving = None
     if rank == 0 and not args.no_serving:
         serving = run_serving(args, sg, synth, torch)
+    batched = None
+    if rank == 0 and not args.no_batched:
+        batched = run_batched(args, sg, synth, torch)
 
     if rank == 0:
         m = results["mixed"]
@@ -386,7 +454,7 @@ def main():
                 "e2e": m["e2e"], "gpu_launches": LAUNCHES_PER_APPLY * m["steps"],
                 "fp64": {"value": f["value"], "unit": UNIT, "ms_per_step": f["ms_per_step"], "steps": f["steps"],
                          "latency_ms": f["latency_ms"], "roofline": f["roofline"], "clocks": f["clocks"]},
-                "cpu_baseline": cpu, "serving": serving}
+                "cpu_baseline": cpu, "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     rep.close()
     return 0

@@ -503,11 +503,26 @@ size_t apply_smem_bytes(const KParams &kp, bool fp32)
            4 * (size_t)kp.maxnb;
 }
 
+// The limit is a property of the kernel, shared by every context: it is set to
+// the most the device allows beside the kernel's static shared memory (not to
+// one context's need, which could lower it under another context's launches).
+template <typename K>
+static cudaError_t set_smem_limit(K kernel, size_t need)
+{
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const long long lim = (long long)optin - (long long)fa.sharedSizeBytes;
+    if (lim <= 0 || (long long)need > lim) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+}
+
 cudaError_t configure_kernels(size_t smem, bool fp32)
 {
-    if (fp32)
-        return cudaFuncSetAttribute(k_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaFuncSetAttribute(k_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return fp32 ? set_smem_limit(k_apply<float>, smem) : set_smem_limit(k_apply<double>, smem);
 }
 
 cudaError_t launch_apply(const KParams &kp, bool fp32, const double *x, double *y, int nvec,

@@ -614,6 +614,23 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 3 : 2)
                                           smraw + (size_t)grp * part, Hs[grp], tid);
 }
 
+// Sets a kernel's dynamic shared-memory limit to the most the device allows
+// beside the kernel's static shared memory (a property of the kernel, shared
+// by every context, so never one context's own need); fails if `need` is more.
+template <typename K>
+cudaError_t set_smem_limit(K kernel, size_t need)
+{
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const long long lim = (long long)optin - (long long)fa.sharedSizeBytes;
+    if (lim <= 0 || (long long)need > lim) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+}
+
 template <typename T, int NB1, int NQ1, int RMAX, bool UNI>
 cudaError_t launch_t(const KParams &kp, const FastLaunch &a)
 {
@@ -621,11 +638,9 @@ cudaError_t launch_t(const KParams &kp, const FastLaunch &a)
     const size_t smem_cta = part_bytes(kp, rb, kp.fast.work_cta);
     const size_t smem_warp = (size_t)(kFT / 32) * part_bytes(kp, rb, kp.fast.work_warp);
     if (a.configure) {
-        cudaError_t e = cudaFuncSetAttribute(k_apply_fast<T, NB1, NQ1, RMAX, UNI, kFT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cta);
-        if (e != cudaSuccess || kp.fast.work_warp <= 0) return e;
-        return cudaFuncSetAttribute(k_apply_fast<T, NB1, NQ1, RMAX, UNI, 32>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_warp);
+        cudaError_t e = set_smem_limit(k_apply_fast<T, NB1, NQ1, RMAX, UNI, kFT>, smem_cta);
+        if (e != cudaSuccess) return e;
+        return set_smem_limit(k_apply_fast<T, NB1, NQ1, RMAX, UNI, 32>, smem_warp);
     }
     const int nbig = kp.fast.n_big, nrest = (int)kp.n_terms - nbig;
     if (nbig > 0)
@@ -644,11 +659,9 @@ cudaError_t batch_t(const FastBatchLaunch &a)
 {
     constexpr int NG = kFT / 32;
     if (a.configure) {
-        cudaError_t e = cudaFuncSetAttribute(k_apply_fast_batch<T, NB1, NQ1, RMAX, UNI, kFT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, a.part[0]);
+        cudaError_t e = set_smem_limit(k_apply_fast_batch<T, NB1, NQ1, RMAX, UNI, kFT>, (size_t)a.part[0]);
         if (e != cudaSuccess) return e;
-        return cudaFuncSetAttribute(k_apply_fast_batch<T, NB1, NQ1, RMAX, UNI, 32>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, NG * a.part[1]);
+        return set_smem_limit(k_apply_fast_batch<T, NB1, NQ1, RMAX, UNI, 32>, (size_t)NG * a.part[1]);
     }
     if (a.count[0] > 0)
         k_apply_fast_batch<T, NB1, NQ1, RMAX, UNI, kFT><<<(unsigned)a.count[0], kFT, (size_t)a.part[0], a.stream>>>(
