@@ -71,6 +71,16 @@ def exactness_violations(p):
 
 def apply_H(p, x: np.ndarray) -> np.ndarray:
     """y = H_S x through the masked Galerkin matrix (raises if not exact)."""
+    return _masked_galerkin(p, x=x)
+
+
+def matrix(p):
+    """The masked Galerkin matrix itself as scipy.sparse CSR (raises if not exact)."""
+    return _masked_galerkin(p, x=None)
+
+
+def _masked_galerkin(p, x=None):
+    """Applies the masked Galerkin matrix to x, or (x None) assembles it."""
     bad = exactness_violations(p)
     if bad:
         raise ValueError(f"masked Galerkin form not exact for this problem: {bad[:4]}")
@@ -84,10 +94,16 @@ def apply_H(p, x: np.ndarray) -> np.ndarray:
     assert np.all(np.diff(keys) > 0)
     lm = np.stack([_lmin(int(p.nb_A[i]), int(p.nb_B[i]), K[:, i]) for i in range(D)], axis=1)
 
-    x = np.asarray(x, np.float64)
-    squeeze = x.ndim == 1
-    X = x.reshape(1, -1) if squeeze else x
-    Y = np.zeros_like(X)
+    assemble = x is None
+    if assemble:
+        parts = []   # (rows, cols, vals)
+        X = Y = None
+        squeeze = False
+    else:
+        x = np.asarray(x, np.float64)
+        squeeze = x.ndim == 1
+        X = x.reshape(1, -1) if squeeze else x
+        Y = np.zeros_like(X)
     nmat = kmax + 8
     Qm = [_position_matrix(nmat + 4, float(p.q0[i]), float(p.scale[i])) for i in range(D)]
     D2m = [_d2_matrix(nmat + 4, float(p.scale[i])) for i in range(D)]
@@ -123,7 +139,10 @@ def apply_H(p, x: np.ndarray) -> np.ndarray:
             found &= keys[pos_c] == kp_keys
             rows = np.nonzero(ok)[0][found]
             cols = pos_c[found]
-            Y[:, rows] += val[rows] * X[:, cols]
+            if assemble:
+                parts.append((rows, cols, val[rows]))
+            else:
+                Y[:, rows] += val[rows] * X[:, cols]
 
     off = 0
     for m in range(p.nmono):
@@ -136,9 +155,17 @@ def apply_H(p, x: np.ndarray) -> np.ndarray:
         off += int(p.nfac[m])
         if ops:
             add_product(float(p.coef[m]), ops)
+        elif assemble:
+            parts.append((np.arange(N), np.arange(N), np.full(N, float(p.coef[m]))))
         else:
             Y += float(p.coef[m]) * X
     for j in range(D):
         if p.omega[j] != 0.0:
             add_product(-0.5 * float(p.omega[j]), {j: (D2m[j], 2)})
+    if assemble:
+        import scipy.sparse as sp
+        r = np.concatenate([a for a, _, _ in parts]) if parts else np.zeros(0, np.int64)
+        c = np.concatenate([b for _, b, _ in parts]) if parts else np.zeros(0, np.int64)
+        v = np.concatenate([w for _, _, w in parts]) if parts else np.zeros(0)
+        return sp.csr_matrix((v, (r, c)), shape=(N, N))   # duplicates are summed
     return Y.reshape(-1) if squeeze else Y

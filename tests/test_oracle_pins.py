@@ -219,3 +219,15 @@ def test_thread_count_does_not_change_result_beyond_rounding():
     n = orc.n_compact(p)
     x = synth.random_vectors(n, 1, 1)
     assert rel(orc.apply_H(p, x, threads=1), orc.apply_H(p, x, threads=3)) < 1e-14
+
+
+def test_masked_galerkin_matrix_is_its_apply_and_symmetric():
+    """The assembled masked-Galerkin matrix (used for the stored D=12 L=10
+    eigenvalues) is the same operator as its apply path, and symmetric (P8)."""
+    from oracle import galerkin
+    p = synth.workload_C3(L=4, D=5)
+    M = galerkin.matrix(p)
+    x = np.random.default_rng(3).standard_normal((2, M.shape[0]))
+    y = galerkin.apply_H(p, x)
+    assert np.abs((M @ x.T).T - y).max() <= 1e-13 * np.abs(y).max()
+    assert abs(M - M.T).max() <= 1e-14
