@@ -39,6 +39,10 @@ WORKLOAD = "chained Henon-Heiles D=12 L=10 nb=l+1 nq=l+2 (N_cs=646646, 646646 te
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # FP64: the nominal GB300 rate (1.25 TFLOP/s); the FMA microbenchmark is reported beside it
 FP64_PEAK_TFLOPS = 1.25
+# DRAM bytes per launch of the mixed block-form term kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum), from the ncu capture summarised in
+# profiles/k_apply_fast_block_mixed_D12_L10.md; reset to None when that kernel changes
+TRAFFIC_BYTES_MIXED = 1.929025e9 + 0.729796e9
 # kernels of one sg_apply_H at this workload: k_maxabs, k_apply_fast (block form
 # over the large terms), k_apply_fast (warp form over the small terms), k_finalize
 LAUNCHES_PER_APPLY = 4
@@ -411,7 +415,8 @@ def main():
             "value": replica_throughput(world, nvec * steps, total_ms * 1e-3), "ms_per_step": ms, "steps": steps,
             "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": TRAFFIC_BYTES_MIXED if prec == "mixed" else None,
                          "flops_per_launch": f_alg,
                          "peak_note": ("FP32 CUDA cores, derived: 152 SM x 128 lanes x 2 x 2.07 GHz"
                                        if prec == "mixed" else "FP64, nominal GB300 rate")},

@@ -573,7 +573,7 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
 // Terms [p0, p0 + pcount) of one problem's processing order; NG = 128 / GS
 // term groups per block.
 template <typename T, int NB1, int NQ1, int RMAX, bool UNI, int GS>
-__global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? SG_F32_MINBLOCKS : SG_F64_MINBLOCKS)
     k_apply_fast(const KParams P, const double *__restrict__ x, const long long *__restrict__ maxbits, int nvec,
                  int p0, int pcount, int work_cap)
 {
@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 3 : 2)
 // kAccDigits for the accumulators) and j * nvec.  Every group's shared-memory
 // partition is `part` bytes, the largest over the problems.
 template <typename T, int NB1, int NQ1, int RMAX, bool UNI, int GS>
-__global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? SG_F32_MINBLOCKS : SG_F64_MINBLOCKS)
     k_apply_fast_batch(const KParams *__restrict__ kps, const int2 *__restrict__ items, int count,
                        const double *__restrict__ x, unsigned long long *acc,
                        const long long *__restrict__ maxbits, const long long *__restrict__ cs_prefix, int nvec,
@@ -687,9 +687,9 @@ cudaError_t for_variant_u(const KParams &kp, F &&f)
 {
     constexpr bool F32 = sizeof(T) == 4;
     const int nb1 = kp.fast.nb1, nq1 = kp.fast.nq1;
-    if (nb1 == 2 && nq1 == 3) return f(Variant<T, 2, 3, F32 ? 3 : 1, UNI>{});
-    if (nb1 == 2 && nq1 == 2) return f(Variant<T, 2, 2, F32 ? 3 : 1, UNI>{});
-    if (nb1 == 3 && nq1 == 3) return f(Variant<T, 3, 3, F32 ? 2 : 1, UNI>{});
+    if (nb1 == 2 && nq1 == 3) return f(Variant<T, 2, 3, F32 ? SG_F32_RMAX2 : 1, UNI>{});
+    if (nb1 == 2 && nq1 == 2) return f(Variant<T, 2, 2, F32 ? SG_F32_RMAX2 : 1, UNI>{});
+    if (nb1 == 3 && nq1 == 3) return f(Variant<T, 3, 3, F32 ? SG_F32_RMAX3 : 1, UNI>{});
     return f(Variant<T, 1, 1, 0, UNI>{});
 }
 

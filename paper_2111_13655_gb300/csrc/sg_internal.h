@@ -39,10 +39,33 @@ constexpr int kMaxPairs = 64;  // coupled mode pairs handled by the fast path
 
 // Number of level-1 slots the fast kernel keeps in registers ("inner" slots);
 // the host descriptor builder and the kernel dispatch both use this.
+// Tuning of the fast kernels (FP32 / FP64): register-slot counts for level-1
+// slots of 2 functions and of 3 functions, the shared-memory budget per block
+// that the host plans terms with, and the resident blocks per SM the kernels
+// are compiled for.
+#ifndef SG_F32_RMAX2
+#define SG_F32_RMAX2 2
+#endif
+#ifndef SG_F32_RMAX3
+#define SG_F32_RMAX3 2
+#endif
+#ifndef SG_F32_SMEM_KB
+#define SG_F32_SMEM_KB 52
+#endif
+#ifndef SG_F32_MINBLOCKS
+#define SG_F32_MINBLOCKS 4
+#endif
+#ifndef SG_F64_SMEM_KB
+#define SG_F64_SMEM_KB 106
+#endif
+#ifndef SG_F64_MINBLOCKS
+#define SG_F64_MINBLOCKS 2
+#endif
+
 inline int fast_rmax(bool fp32, int nb1, int nq1)
 {
-    if (nb1 == 2 && (nq1 == 3 || nq1 == 2)) return fp32 ? 3 : 1;
-    if (nb1 == 3 && nq1 == 3) return fp32 ? 2 : 1;
+    if (nb1 == 2 && (nq1 == 3 || nq1 == 2)) return fp32 ? SG_F32_RMAX2 : 1;
+    if (nb1 == 3 && nq1 == 3) return fp32 ? SG_F32_RMAX3 : 1;
     return 0;
 }
 

@@ -372,7 +372,7 @@ std::string build_tables(const Problem &p, int smem_budget, int rb, HostTables *
     if (T.fast) {
         // fast kernel: matrices, G tables, slice weights and ranks, then a work
         // area for X, Y and two grid buffers (sized per term and vector chunk)
-        const int fbudget = std::min(smem_budget, rb == 4 ? 70 * 1024 : 106 * 1024);
+        const int fbudget = std::min(smem_budget, rb == 4 ? SG_F32_SMEM_KB * 1024 : SG_F64_SMEM_KB * 1024);
         std::string de = build_fast_descs(p, rb == 4, &T, fbudget, rb);
         if (!de.empty()) return de;
     }
