@@ -161,7 +161,8 @@ int64_t planned_device_bytes(const sg_ctx *ctx)
                     b(T.harm_mono) + b(T.esplit);
     if (T.fast)
         bytes += b(T.pair_modes) + b(T.h1off) + b(T.goff) + b(T.ioff) + b(T.soff) + b(T.spoff) + b(T.fsc) +
-                 b(T.ftab) * 3 / 2 + b(T.fdesc) + b(T.fdesc_off) + T.franks * (int64_t)sizeof(int);
+                 b(T.ftab) * 3 / 2 + b(T.fdesc) + b(T.fdesc_off) + T.franks * (int64_t)sizeof(int) +
+                 b(T.fimg) / (ctx->fp32 ? 2 : 1) + b(T.fimg_off);
     return bytes;
 }
 
@@ -224,7 +225,11 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
                     (st = upload(ctx, T.ftab, &kp.fast.tabd)) != SG_OK ||
                     (st = upload(ctx, ftabf, &kp.fast.tabf)) != SG_OK ||
                     (st = upload(ctx, T.fdesc, &kp.fast.desc)) != SG_OK ||
-                    (st = upload(ctx, T.fdesc_off, &kp.fast.desc_off)) != SG_OK))) {
+                    (st = upload(ctx, T.fdesc_off, &kp.fast.desc_off)) != SG_OK ||
+                    (st = upload(ctx, T.fimg_off, &kp.fast.img_off)) != SG_OK ||
+                    (ctx->fp32 ? (st = upload(ctx, std::vector<float>(T.fimg.begin(), T.fimg.end()),
+                                              &kp.fast.imgf)) != SG_OK
+                               : (st = upload(ctx, T.fimg, &kp.fast.imgd)) != SG_OK)))) {
         g_create_error = ctx->last_error;
         free_all(ctx);
         delete ctx;

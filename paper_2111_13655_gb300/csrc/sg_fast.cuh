@@ -69,6 +69,7 @@ constexpr int kMaxVB = 8;  // vectors per chunk
 struct FHdr {
     int m, R, NB, NBo, grid, bad, coef;
     int s, vb, NBO, NBrest, NBIn, nslice, NGs;
+    int matsz;                                           // elements of the B, B^T W, H1 block
     int npair, nind, gsize;
     double c0;
     long long rank_off;
@@ -105,10 +106,12 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return f
 
 template <typename T> struct FTab;
 template <> struct FTab<double> {
+    static __device__ const double *img(const KParams &P) { return P.fast.imgd; }
     static __device__ const double *f(const KParams &P) { return P.fast.tabd; }
     static __device__ const double *t(const KParams &P) { return P.tabd; }
 };
 template <> struct FTab<float> {
+    static __device__ const float *img(const KParams &P) { return P.fast.imgf; }
     static __device__ const float *f(const KParams &P) { return P.fast.tabf; }
     static __device__ const float *t(const KParams &P) { return P.tabf; }
 };
@@ -178,6 +181,7 @@ __device__ void derive_layout(const KParams &P, int nvec, int work, FHdr &H)
         else { H.NBrest *= H.nb[j]; H.NGs *= H.nq[j]; stage *= H.nq[j]; }
     }
     if (mat > P.matcap || H.gsize > P.fast.gcap || H.NBO > P.fast.nbocap) { H.bad = 1; return; }
+    H.matsz = mat;
     H.NBIn = NBIn; H.NBo = H.NB / NBIn;
     stage *= NBIn;
     const int64_t per_vec = 2 * (int64_t)H.NB + (H.grid ? 2 * stage : 0);
@@ -187,7 +191,30 @@ __device__ void derive_layout(const KParams &P, int nvec, int work, FHdr &H)
     H.vb = vb;
 }
 
-// out[a][r][c] = sum_k M[r][k] in[a][k][c], matrix in registers, one fibre (a, c) per thread
+// Fibres f = tid, tid + GS, ... of an A x C grid as (a, c) = (f / C, f % C),
+// stepped without a division: one division per call for the start and the
+// step GS = as * C + cs, then one carry per step.
+struct FibreWalk {
+    int a, c, as, cs;
+    __device__ __forceinline__ void step(int C)
+    {
+        a += as;
+        c += cs;
+        if (c >= C) { c -= C; a++; }
+    }
+};
+template <int GS>
+__device__ __forceinline__ FibreWalk fibre_walk(int C, int tid)
+{
+    FibreWalk w;
+    w.a = tid / C;
+    w.c = tid - w.a * C;
+    w.as = GS / C;
+    w.cs = GS - w.as * C;
+    return w;
+}
+
+// out[a][r][c] = sum_k M[r][k] in[a][k][c], matrix in registers, one fibre (a, c) at a time per thread
 template <typename T, int N, int RR, int GS>
 __device__ __forceinline__ void fcontract_t(const T *__restrict__ in, T *__restrict__ out, int A, int C,
                                             const T *__restrict__ M, int tid)
@@ -195,12 +222,9 @@ __device__ __forceinline__ void fcontract_t(const T *__restrict__ in, T *__restr
     T mr[RR * N];
 #pragma unroll
     for (int i = 0; i < RR * N; i++) mr[i] = M[i];
-    const int total = A * C;
-    const unsigned mag = rmag(C);
-    for (int f = tid; f < total; f += GS) {
-        const int a = fdiv(f, C, mag), c = f - a * C;
-        const T *ip = in + a * N * C + c;
-        T *op = out + a * RR * C + c;
+    for (FibreWalk w = fibre_walk<GS>(C, tid); w.a < A; w.step(C)) {
+        const T *ip = in + w.a * N * C + w.c;
+        T *op = out + w.a * RR * C + w.c;
         T xv[N];
 #pragma unroll
         for (int k = 0; k < N; k++) xv[k] = ip[k * C];
@@ -218,14 +242,14 @@ template <typename T, int GS>
 __device__ void fcontract_rt(const T *__restrict__ in, T *__restrict__ out, int A, int n, int r, int C,
                              const T *__restrict__ M, int tid)
 {
-    const int total = A * r * C;
-    for (int e = tid; e < total; e += GS) {
-        const int c = e % C, tq = e / C, rr = tq % r, a = tq / r;
-        const T *ip = in + (a * n) * C + c;
-        const T *mp = M + rr * n;
-        T acc = T(0);
-        for (int k = 0; k < n; k++) acc += mp[k] * ip[k * C];
-        out[e] = acc;
+    for (FibreWalk w = fibre_walk<GS>(C, tid); w.a < A; w.step(C)) {
+        const T *ip = in + (w.a * n) * C + w.c;
+        for (int rr = 0; rr < r; rr++) {
+            const T *mp = M + rr * n;
+            T acc = T(0);
+            for (int k = 0; k < n; k++) acc += mp[k] * ip[k * C];
+            out[(w.a * r + rr) * C + w.c] = acc;
+        }
     }
 }
 
@@ -415,29 +439,15 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
         if (tid == 0 && P.err) atomicCAS(P.err, 0, 110 + H.bad);
         return;
     }
-    const T *tab = FTab<T>::t(P);
-    const T *ftab = FTab<T>::f(P);
     const int m = H.m, R = H.R, NB = H.NB, NBo = H.NBo;
     const int *rk = P.fast.ranks + H.rank_off;
 
-    // per-position matrices: B, B^T W (grid part) and H1 = base + induced; G tables of the active pairs
-    for (int j = 0; j < m; j++) {
-        const int nb = H.nb[j], nq = H.nq[j];
-        if (H.grid)
-            for (int e = tid; e < nb * nq; e += GS) {
-                mats[H.oB[j] + e] = tab[H.gB[j] + e];
-                mats[H.oBW[j] + e] = tab[H.gBW[j] + e];
-            }
-        for (int e = tid; e < nb * nb; e += GS) {
-            T hv = ftab[H.gH1[j] + e];
-            for (int q = 0; q < H.nind; q++)
-                if (H.ipos[q] == j) hv += ftab[H.ioffs[q] + e];
-            mats[H.oH[j] + e] = hv;
-        }
-    }
-    for (int p = 0; p < H.npair; p++) {
-        const int sz = H.nq[H.pa[p]] * H.nq[H.pb[p]];
-        for (int e = tid; e < sz; e += GS) gtab[H.pg[p] + e] = ftab[H.pgg[p] + e];
+    // the term's matrices (B, B^T W, H1 per position) and G tables: one contiguous image
+    {
+        const T *img = FTab<T>::img(P) + P.fast.img_off[p];
+        const int matsz = H.matsz;
+        for (int e = tid; e < matsz; e += GS) mats[e] = img[e];
+        for (int e = tid; e < H.gsize; e += GS) gtab[e] = img[matsz + e];
     }
     gsync<GS>();
 

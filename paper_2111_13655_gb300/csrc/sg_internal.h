@@ -111,6 +111,11 @@ struct FastParams {
     int nbocap;            // largest sliced outer block (slice weights)
     int n_big;             // terms [0, n_big) run one per block, the rest one per warp
     int work_cta, work_warp;   // work-area capacities (elements) of the two kernels
+    // per-term shared-memory images (processing order): the term's B, B^T W and
+    // H1 (base + induced, summed on the host) per position, then its G tables
+    const double *imgd;        // FP64 contexts
+    const float *imgf;         // FP32 contexts
+    const long long *img_off;  // [n_terms + 1] image starts, in elements
 };
 
 // Everything a kernel needs, passed by value.
@@ -176,6 +181,8 @@ struct HostTables {
     std::vector<double> ftab, fsc;
     double c0const = 0.0;
     int fast_cap = 0, fast_maxnb = 0, fast_matcap = 0;
+    std::vector<double> fimg;         // per-term shared-memory images (see FastParams)
+    std::vector<long long> fimg_off;  // [n_terms + 1]
     std::vector<int4> fdesc;          // term records
     std::vector<unsigned> fdesc_off;  // [n_terms+1]
     int64_t franks = 0;               // total compact indices (N_s)

@@ -642,6 +642,7 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
 
     // pass 1: capacities
     int gcap = 1, mcap = 1;
+    size_t img_total = 0;
     TermPlan tp;
     for (int64_t q = 0; q < T.n_terms; q++) {
         plan_term(T.order[q], tp);
@@ -653,6 +654,7 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
             mat += 2 * li.nb * li.nq + li.nb * li.nb;
         }
         mcap = std::max(mcap, mat);
+        img_total += (size_t)mat + tp.gsize;
     }
     const int nbocap = 64;  // sliced blocks larger than this are not used
     const size_t head = ((size_t)rb * (mcap + gcap + 2 * nbocap) + 15) & ~(size_t)15;
@@ -684,6 +686,9 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
     T.fdesc.clear();
     T.fdesc_off.assign(T.n_terms + 1, 0);
     T.fdesccap = 0;
+    T.fimg.clear();
+    T.fimg.reserve(img_total);
+    T.fimg_off.assign(T.n_terms + 1, 0);
     int64_t rank_off = 0;
     for (int64_t q = 0; q < T.n_terms; q++) {
         const int t = T.order[q];
@@ -696,6 +701,27 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
         for (int j = tp.R; j < tp.R + sv; j++) nbo *= LI(tp.posmode[j], lt[tp.posmode[j]]).nb;
         if (nbo > nbocap) { T.fast = false; T.fdesc.clear(); return ""; }
         const int na = tp.na;
+        // the term's shared-memory image: per position B, B^T W, H1 (+ induced), then G tables
+        for (int j = 0; j < na; j++) {
+            const int i = tp.posmode[j];
+            const LevelInfo &li = LI(i, lt[i]);
+            const size_t nbq = (size_t)li.nb * li.nq, nbb = (size_t)li.nb * li.nb;
+            T.fimg.insert(T.fimg.end(), T.tabd.begin() + li.offB, T.tabd.begin() + li.offB + nbq);
+            T.fimg.insert(T.fimg.end(), T.tabd.begin() + li.offBW, T.tabd.begin() + li.offBW + nbq);
+            const size_t h0 = T.fimg.size();
+            const int hb = T.h1off[(size_t)i * Lp + lt[i]];
+            T.fimg.insert(T.fimg.end(), T.ftab.begin() + hb, T.ftab.begin() + hb + nbb);
+            for (const FDescInd &d : tp.inds)
+                if (d.pos == j)
+                    for (size_t e = 0; e < nbb; e++) T.fimg[h0 + e] += T.ftab[d.ioff + e];
+        }
+        for (const FDescPair &pr : tp.prs) {
+            const size_t sz = (size_t)LI(tp.posmode[pr.pa], lt[tp.posmode[pr.pa]]).nq *
+                              LI(tp.posmode[pr.pb], lt[tp.posmode[pr.pb]]).nq;
+            T.fimg.insert(T.fimg.end(), T.ftab.begin() + pr.goff, T.ftab.begin() + pr.goff + sz);
+        }
+        T.fimg_off[q + 1] = (long long)T.fimg.size();
+        tp.inds.clear();  // summed into the image's H1 matrices
         const int units = 3 + na + (int)tp.prs.size() + ((int)tp.inds.size() + 1) / 2;
         const size_t u0 = T.fdesc.size();
         T.fdesc.resize(u0 + units, int4{0, 0, 0, 0});
