@@ -66,7 +66,7 @@ sg_status ensure_workspace(sg_ctx *ctx, int nvec, cudaStream_t s)
     ctx->acc = nullptr;
     ctx->maxbits = nullptr;
     ctx->acc_nvec = 0;
-    const size_t words = (size_t)ctx->host.n_cs * nvec * sg::kAccDigits;
+    const size_t words = (size_t)ctx->host.n_cs * nvec * sg::acc_words(ctx->fp32);
     if ((e = cudaMalloc(&ctx->acc, words * sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMalloc(&ctx->maxbits, sizeof(long long) * nvec)) != cudaSuccess)
         return fail(ctx, SG_ENOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));

@@ -266,8 +266,8 @@ __global__ void __launch_bounds__(kThreads) k_apply(const KParams P, const doubl
 
     for (int v = 0; v < nvec; v++) {
         const double *xv = x + (size_t)v * P.n_cs;
-        unsigned long long *accv = P.acc + (size_t)v * P.n_cs * kAccDigits;
-        const int E = lsb_exponent(maxbits[v]);
+        unsigned long long *accv = P.acc + (size_t)v * P.n_cs * fx::Acc<T>::words;
+        const long long mbv = maxbits[v];
         for (int e = tid; e < H.NB; e += kThreads) { X[e] = (T)__ldg(xv + rk[e]); Y[e] = T(0); }
         __syncthreads();
         if (H.grid) {
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(const KParams P, const doubl
                 const T *Kr = mats + H.oK[j] + kj * nbj;
                 for (int kp = 0; kp < nbj; kp++) acc += Kr[kp] * X[base + kp * H.stride[j]];
             }
-            fx_add_real(accv + (size_t)rk[e] * kAccDigits, Y[e] + acc, H.coef, E, P.err);
+            fx::Acc<T>::add(accv + (size_t)rk[e] * fx::Acc<T>::words, Y[e] + acc, H.coef, mbv, P.err);
         }
         __syncthreads();
     }
@@ -398,8 +398,15 @@ __global__ void k_maxabs(const double *__restrict__ x, int n, long long *__restr
 
 // The accumulated integer of one entry times 2^E (E from the vector's max|x|
 // bits; NaN when x held a non-finite value); clears the accumulator words.
-__device__ __forceinline__ double finalize_value(unsigned long long *a, long long mb)
+// FP32 contexts: one signed word; FP64: four signed 32-bit digits.
+__device__ __forceinline__ double finalize_value(unsigned long long *a, long long mb, int fp32)
 {
+    if (fp32) {
+        const double v1 = (double)(long long)a[0];
+        a[0] = 0ull;
+        return ((mb >> 52) & 0x7FF) == 0x7FF ? __longlong_as_double(0x7FF8000000000000ll)
+                                              : scalbn(v1, lsb_exponent(mb, kAcc32LsbBelowMax));
+    }
     unsigned __int128 tot = 0;
 #pragma unroll
     for (int d = 0; d < kAccDigits; d++) {
@@ -416,13 +423,13 @@ __device__ __forceinline__ double finalize_value(unsigned long long *a, long lon
 
 // y = (accumulated integer) * 2^E + esplit * x; clears the accumulators
 __global__ void k_finalize(const KParams P, const double *__restrict__ x, double *__restrict__ y,
-                           const long long *__restrict__ maxbits, int nvec)
+                           const long long *__restrict__ maxbits, int nvec, int fp32)
 {
     const size_t total = (size_t)nvec * P.n_cs;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int v = (int)(i / P.n_cs);
         const size_t r = i - (size_t)v * P.n_cs;
-        y[i] = finalize_value(P.acc + i * kAccDigits, maxbits[v]) + P.esplit[r] * x[i];
+        y[i] = finalize_value(P.acc + i * acc_words(fp32), maxbits[v], fp32) + P.esplit[r] * x[i];
     }
 }
 
@@ -451,7 +458,8 @@ __global__ void k_maxabs_batch(const double *__restrict__ x, const long long *__
 // over all problems' vectors; clears the accumulators.
 __global__ void k_finalize_batch(const KParams *__restrict__ kps, const long long *__restrict__ cs_prefix,
                                  int nprob, const double *__restrict__ x, double *__restrict__ y,
-                                 unsigned long long *acc, const long long *__restrict__ maxbits, int nvec)
+                                 unsigned long long *acc, const long long *__restrict__ maxbits, int nvec,
+                                 int fp32)
 {
     const size_t total = (size_t)nvec * (size_t)cs_prefix[nprob];
     for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
@@ -464,7 +472,8 @@ __global__ void k_finalize_batch(const KParams *__restrict__ kps, const long lon
         const size_t i = g - (size_t)nvec * (size_t)cs_prefix[lo];
         const int v = (int)(i / n);
         const size_t r = i - (size_t)v * n;
-        y[g] = finalize_value(acc + g * kAccDigits, maxbits[(size_t)lo * nvec + v]) + kps[lo].esplit[r] * x[g];
+        y[g] = finalize_value(acc + g * acc_words(fp32), maxbits[(size_t)lo * nvec + v], fp32) +
+               kps[lo].esplit[r] * x[g];
     }
 }
 
@@ -547,7 +556,7 @@ cudaError_t launch_apply(const KParams &kp, bool fp32, const double *x, double *
     }
     const size_t total = (size_t)nvec * kp.n_cs;
     const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 16);
-    k_finalize<<<blocks, 256, 0, stream>>>(kp, x, y, maxbits, nvec);
+    k_finalize<<<blocks, 256, 0, stream>>>(kp, x, y, maxbits, nvec, fp32 ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -577,11 +586,11 @@ cudaError_t launch_maxabs_batch(const double *x, const long long *cs_prefix, int
 
 cudaError_t launch_finalize_batch(const KParams *kps, const long long *cs_prefix, int nprob, int64_t total_cs,
                                   const double *x, double *y, unsigned long long *acc, const long long *maxbits,
-                                  int nvec, cudaStream_t stream)
+                                  int nvec, bool fp32, cudaStream_t stream)
 {
     const size_t total = (size_t)nvec * (size_t)total_cs;
     const unsigned blocks = (unsigned)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, 152 * 16));
-    k_finalize_batch<<<blocks, 256, 0, stream>>>(kps, cs_prefix, nprob, x, y, acc, maxbits, nvec);
+    k_finalize_batch<<<blocks, 256, 0, stream>>>(kps, cs_prefix, nprob, x, y, acc, maxbits, nvec, fp32 ? 1 : 0);
     return cudaGetLastError();
 }
 

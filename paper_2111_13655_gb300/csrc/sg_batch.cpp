@@ -177,7 +177,7 @@ extern "C" sg_status sg_apply_H_batch(sg_batch *b, const double *x, double *y, i
         b->acc = nullptr;
         b->maxbits = nullptr;
         b->acc_nvec = 0;
-        const size_t words = total * sg::kAccDigits;
+        const size_t words = total * sg::acc_words(b->fp32);
         if ((e = cudaMalloc(&b->acc, words * sizeof(unsigned long long))) != cudaSuccess ||
             (e = cudaMalloc(&b->maxbits, sizeof(long long) * (size_t)nprob * nvec)) != cudaSuccess)
             return bfail(b, SG_ENOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
@@ -194,13 +194,13 @@ extern "C" sg_status sg_apply_H_batch(sg_batch *b, const double *x, double *y, i
     for (int j : b->generic) {
         sg::KParams kp = b->ctxs[j]->kp;
         const size_t off = (size_t)nvec * (size_t)b->cs_prefix[j];
-        kp.acc = b->acc + off * sg::kAccDigits;
+        kp.acc = b->acc + off * sg::acc_words(b->fp32);
         if ((e = sg::launch_apply_terms(kp, b->fp32, x + off, b->maxbits + (size_t)j * nvec, nvec, s)) !=
             cudaSuccess)
             return bfail(b, SG_ECUDA, std::string("term launch: ") + cudaGetErrorString(e));
     }
     if ((e = sg::launch_finalize_batch(b->d_kps, b->d_cs_prefix, nprob, b->cs_prefix.back(), x, y, b->acc,
-                                       b->maxbits, nvec, s)) != cudaSuccess)
+                                       b->maxbits, nvec, b->fp32, s)) != cudaSuccess)
         return bfail(b, SG_ECUDA, std::string("finalise launch: ") + cudaGetErrorString(e));
     return SG_OK;
 }

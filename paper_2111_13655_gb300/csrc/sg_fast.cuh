@@ -571,9 +571,8 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
             const int i = e / NBo, o = e - i * NBo;
             const int r = __ldg(rk + e);
             for (int v = 0; v < vb; v++) {
-                unsigned long long *acc = accp + ((size_t)(v0 + v) * P.n_cs + r) * kAccDigits;
-                fx::fx_add_real(acc, Y[(i * vb + v) * NBo + o], H.coef, fx::lsb_exponent(maxbits[v0 + v]),
-                                P.err);
+                unsigned long long *acc = accp + ((size_t)(v0 + v) * P.n_cs + r) * fx::Acc<T>::words;
+                fx::Acc<T>::add(acc, Y[(i * vb + v) * NBo + o], H.coef, maxbits[v0 + v], P.err);
             }
         }
         gsync<GS>();
@@ -619,7 +618,7 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? SG_F32_MINBLOCKS : SG_F6
     const int2 it = items[pidx];
     const KParams &P = kps[it.x];
     const size_t off = (size_t)nvec * (size_t)cs_prefix[it.x];
-    fast_term<T, NB1, NQ1, RMAX, UNI, GS>(P, x + off, acc + off * kAccDigits, maxbits + (size_t)it.x * nvec, nvec,
+    fast_term<T, NB1, NQ1, RMAX, UNI, GS>(P, x + off, acc + off * fx::Acc<T>::words, maxbits + (size_t)it.x * nvec, nvec,
                                           it.y, GS == kFT ? P.fast.work_cta : P.fast.work_warp,
                                           smraw + (size_t)grp * part, Hs[grp], tid);
 }

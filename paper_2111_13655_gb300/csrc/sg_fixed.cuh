@@ -71,12 +71,60 @@ static __device__ __forceinline__ void fx_add_real(unsigned long long *acc, floa
 }
 
 // E (the exponent of the accumulators' unit) of vector v from max|x_v|
-static __device__ __forceinline__ int lsb_exponent(long long maxbits)
+static __device__ __forceinline__ int lsb_exponent(long long maxbits, int below = kAccLsbBelowMax)
 {
     const int ex = (int)((maxbits >> 52) & 0x7FF);
     if (maxbits == 0) return -1000;
-    return (ex - 1022) - kAccLsbBelowMax;  // max|x| < 2^(ex-1022)
+    return (ex - 1022) - below;  // max|x| < 2^(ex-1022)
 }
+
+// FP32 contributions into one signed 64-bit word in units of 2^E: coef * r is
+// rounded to the nearest unit (half up) and added with one integer atomic.
+// With E = exponent(max|x|) - 40 a single contribution stays below 2^62 units
+// (|coef * r| < 2^22 max|x|; larger ones set error 202), the rounding of each
+// is at most 2^(E-1), and sums wrap modulo 2^64 harmlessly: the final value
+// (|y| far below 2^23 max|x|) is exact up to those roundings, in any order.
+static __device__ __forceinline__ void fx_add_w1(unsigned long long *acc, float r, int coef, int E, int *err)
+{
+    const unsigned bits = (unsigned)__float_as_uint(r);
+    int ex = (int)((bits >> 23) & 0xFF);
+    unsigned long long mant = bits & 0x7FFFFFu;
+    if (ex == 0xFF) { if (err) atomicCAS(err, 0, 201); return; }
+    if (ex == 0) ex = 1; else mant |= 1ull << 23;
+    if (mant == 0 || coef == 0) return;
+    bool neg = (bits >> 31) != 0;
+    if (coef < 0) { neg = !neg; coef = -coef; }
+    const unsigned long long pm = mant * (unsigned)coef;  // < 2^33, exact
+    const int sh = (ex - 150) - E;
+    unsigned long long v;
+    if (sh >= 0) {
+        if (sh > 29) { if (err) atomicCAS(err, 0, 202); return; }
+        v = pm << sh;
+    } else {
+        const int rs = -sh;
+        if (rs > 33) return;  // below half a unit: rounds to zero
+        v = (pm + (1ull << (rs - 1))) >> rs;
+    }
+    if (v) atomicAdd(acc, neg ? (unsigned long long)(-(long long)v) : v);
+}
+
+// The accumulator format of a contraction type: FP64 four 32-bit digits
+// (exact), FP32 one word (above).
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+    static constexpr int words = kAccDigits;
+    static __device__ __forceinline__ void add(unsigned long long *a, double r, int coef, long long mb, int *err)
+    {
+        fx_add_real(a, r, coef, lsb_exponent(mb), err);
+    }
+};
+template <> struct Acc<float> {
+    static constexpr int words = 1;
+    static __device__ __forceinline__ void add(unsigned long long *a, float r, int coef, long long mb, int *err)
+    {
+        fx_add_w1(a, r, coef, lsb_exponent(mb, kAcc32LsbBelowMax), err);
+    }
+};
 
 
 }  // namespace fx

@@ -34,6 +34,10 @@ struct LevelInfo {
 // max|x|), split into four signed 32-bit digits held in int64 words.
 constexpr int kAccDigits = 4;
 constexpr int kAccLsbBelowMax = 80;  // E = exponent(max|x|) - 80
+// FP32 contexts: one signed 64-bit word per entry, unit 2^(exponent(max|x|) - 40)
+constexpr int kAcc32LsbBelowMax = 40;
+// 64-bit words per accumulated entry of a context's precision
+__host__ __device__ inline int acc_words(bool fp32) { return fp32 ? 1 : kAccDigits; }
 
 constexpr int kMaxPairs = 64;  // coupled mode pairs handled by the fast path
 
@@ -139,7 +143,7 @@ struct KParams {
     const int *mfpow;        // [sum nfac]
     const int *harm_mono;    // [D] monomial holding the harmonic part of mode i (-1: not split)
     const double *esplit;    // [n_cs] sum over split modes of omega_i s_i^2 (k_i + 1/2)
-    unsigned long long *acc; // [nvec][n_cs][kAccDigits] fixed-point accumulators
+    unsigned long long *acc; // [nvec][n_cs][acc_words] fixed-point accumulators
     FastParams fast;
     // capacities of the per-CTA shared-memory areas (elements)
     int cap;       // each of the two grid ping-pong buffers
@@ -222,7 +226,7 @@ cudaError_t launch_maxabs_batch(const double *x, const long long *cs_prefix, int
                                 long long *maxbits, cudaStream_t stream);
 cudaError_t launch_finalize_batch(const KParams *kps, const long long *cs_prefix, int nprob, int64_t total_cs,
                                   const double *x, double *y, unsigned long long *acc, const long long *maxbits,
-                                  int nvec, cudaStream_t stream);
+                                  int nvec, bool fp32, cudaStream_t stream);
 // Propagation server (sg_server_api.cpp, sg_server.cu): device state of one
 // active request's Chebyshev recurrence.  One iteration after Y = H X logs
 // norm and energy for requests at k = 0, forms T_{k+1} (T_1 from T_0 when
