@@ -70,6 +70,7 @@ struct FHdr {
     int m, R, NB, NBo, grid, bad, coef;
     int s, vb, NBO, NBrest, NBIn, nslice, NGs;
     int matsz;                                           // elements of the B, B^T W, H1 block
+    unsigned nbomag, nbOmag;                             // reciprocals of NBo and NBO
     int npair, nind, gsize;
     double c0;
     long long rank_off;
@@ -183,6 +184,8 @@ __device__ void derive_layout(const KParams &P, int nvec, int work, FHdr &H)
     if (mat > P.matcap || H.gsize > P.fast.gcap || H.NBO > P.fast.nbocap) { H.bad = 1; return; }
     H.matsz = mat;
     H.NBIn = NBIn; H.NBo = H.NB / NBIn;
+    H.nbomag = rmag((unsigned)H.NBo);
+    H.nbOmag = rmag((unsigned)H.NBO);
     stage *= NBIn;
     const int64_t per_vec = 2 * (int64_t)H.NB + (H.grid ? 2 * stage : 0);
     if (per_vec > work) { H.bad = 2; return; }
@@ -454,16 +457,26 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
     for (int v0 = 0; v0 < nvec; v0 += H.vb) {
         const int vb = min(H.vb, nvec - v0);
         T *X = work, *Y = work + NB * vb, *bufA = Y + NB * vb;
-        // gather: X[i][v][o]
-        for (int e = tid; e < NB; e += GS) {
-            const int i = e / NBo, o = e - i * NBo;
-            const int r = __ldg(rk + e);
-            for (int v = 0; v < vb; v++) X[(i * vb + v) * NBo + o] = (T)__ldg(x + (size_t)(v0 + v) * P.n_cs + r);
+        // gather: X[i][v][o]; all loads of an element issue together, the next rank is prefetched
+        {
+            int rn = tid < NB ? __ldg(rk + tid) : 0;
+            for (int e = tid; e < NB; e += GS) {
+                const int r = rn;
+                if (e + GS < NB) rn = __ldg(rk + e + GS);
+                const int i = fdiv(e, NBo, H.nbomag), o = e - i * NBo;
+                const double *xr = x + (size_t)v0 * P.n_cs + r;
+                T xv[kMaxVB];
+#pragma unroll
+                for (int v = 0; v < kMaxVB; v++) xv[v] = v < vb ? (T)__ldg(xr + (size_t)v * P.n_cs) : T(0);
+#pragma unroll
+                for (int v = 0; v < kMaxVB; v++)
+                    if (v < vb) X[(i * vb + v) * NBo + o] = xv[v];
+            }
         }
         gsync<GS>();
         // basis part: Y = c0 X + sum_j H1_j x_j X, all vectors of the chunk per element
         for (int e = tid; e < NB; e += GS) {
-            const int i = e / NBo, o = e - i * NBo;
+            const int i = fdiv(e, NBo, H.nbomag), o = e - i * NBo;
             const int base0 = i * vb * NBo + o;
             T acc[kMaxVB];
 #pragma unroll
@@ -512,12 +525,11 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
                     }
                     gsync<GS>();
                     // Xs[iv][rest] = sum_ko WoF[ko] X[iv][ko][rest]
-                    for (int e = tid; e < NBIv * H.NBrest; e += GS) {
-                        const int iv = e / H.NBrest, rr = e - iv * H.NBrest;
-                        const T *xp = X + (size_t)iv * NBo + rr;
+                    for (FibreWalk w = fibre_walk<GS>(H.NBrest, tid); w.a < NBIv; w.step(H.NBrest)) {
+                        const T *xp = X + (size_t)w.a * NBo + w.c;
                         T acc = T(0);
                         for (int ko = 0; ko < H.NBO; ko++) acc += WoF[ko] * xp[ko * H.NBrest];
-                        bufA[e] = acc;
+                        bufA[w.a * H.NBrest + w.c] = acc;
                     }
                     gsync<GS>();
                     cur = bufA; oth = bufB; spare = bufA;
@@ -556,9 +568,9 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
                 }
                 // Y[iv][ko][rest] += WoB[ko] cur[iv][rest]
                 if (H.s > 0) {
-                    for (int e = tid; e < NB * vb; e += GS) {
-                        const int rr = e % H.NBrest, t2 = e / H.NBrest, ko = t2 % H.NBO, iv = t2 / H.NBO;
-                        Y[e] += WoB[ko] * cur[iv * H.NBrest + rr];
+                    for (FibreWalk w = fibre_walk<GS>(H.NBrest, tid); w.a < NBIv * H.NBO; w.step(H.NBrest)) {
+                        const int iv = fdiv(w.a, H.NBO, H.nbOmag), ko = w.a - iv * H.NBO;
+                        Y[w.a * H.NBrest + w.c] += WoB[ko] * cur[iv * H.NBrest + w.c];
                     }
                 } else {
                     for (int e = tid; e < NB * vb; e += GS) Y[e] += cur[e];
@@ -566,13 +578,20 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
                 gsync<GS>();
             }
         }
-        // exact compress-add of D_l * y_l
-        for (int e = tid; e < NB; e += GS) {
-            const int i = e / NBo, o = e - i * NBo;
-            const int r = __ldg(rk + e);
-            for (int v = 0; v < vb; v++) {
-                unsigned long long *acc = accp + ((size_t)(v0 + v) * P.n_cs + r) * fx::Acc<T>::words;
-                fx::Acc<T>::add(acc, Y[(i * vb + v) * NBo + o], H.coef, maxbits[v0 + v], P.err);
+        // exact compress-add of D_l * y_l (accumulator units per vector hoisted)
+        {
+            int Ev[kMaxVB];
+#pragma unroll
+            for (int v = 0; v < kMaxVB; v++) Ev[v] = v < vb ? fx::Acc<T>::unit(maxbits[v0 + v]) : 0;
+            for (int e = tid; e < NB; e += GS) {
+                const int i = fdiv(e, NBo, H.nbomag), o = e - i * NBo;
+                const int r = __ldg(rk + e);
+                unsigned long long *acc = accp + ((size_t)v0 * P.n_cs + r) * fx::Acc<T>::words;
+#pragma unroll
+                for (int v = 0; v < kMaxVB; v++)
+                    if (v < vb)
+                        fx::Acc<T>::add_unit(acc + (size_t)v * P.n_cs * fx::Acc<T>::words,
+                                             Y[(i * vb + v) * NBo + o], H.coef, Ev[v], P.err);
             }
         }
         gsync<GS>();

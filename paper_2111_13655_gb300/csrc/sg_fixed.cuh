@@ -113,16 +113,26 @@ static __device__ __forceinline__ void fx_add_w1(unsigned long long *acc, float 
 template <typename T> struct Acc;
 template <> struct Acc<double> {
     static constexpr int words = kAccDigits;
+    static __device__ __forceinline__ int unit(long long mb) { return lsb_exponent(mb); }
+    static __device__ __forceinline__ void add_unit(unsigned long long *a, double r, int coef, int E, int *err)
+    {
+        fx_add_real(a, r, coef, E, err);
+    }
     static __device__ __forceinline__ void add(unsigned long long *a, double r, int coef, long long mb, int *err)
     {
-        fx_add_real(a, r, coef, lsb_exponent(mb), err);
+        add_unit(a, r, coef, unit(mb), err);
     }
 };
 template <> struct Acc<float> {
     static constexpr int words = 1;
+    static __device__ __forceinline__ int unit(long long mb) { return lsb_exponent(mb, kAcc32LsbBelowMax); }
+    static __device__ __forceinline__ void add_unit(unsigned long long *a, float r, int coef, int E, int *err)
+    {
+        fx_add_w1(a, r, coef, E, err);
+    }
     static __device__ __forceinline__ void add(unsigned long long *a, float r, int coef, long long mb, int *err)
     {
-        fx_add_w1(a, r, coef, lsb_exponent(mb, kAcc32LsbBelowMax), err);
+        add_unit(a, r, coef, unit(mb), err);
     }
 };
 

@@ -59,6 +59,9 @@ constexpr int kMaxPairs = 64;  // coupled mode pairs handled by the fast path
 #ifndef SG_F32_MINBLOCKS
 #define SG_F32_MINBLOCKS 4
 #endif
+#ifndef SG_SLICE_VT
+#define SG_SLICE_VT 2
+#endif
 #ifndef SG_F64_SMEM_KB
 #define SG_F64_SMEM_KB 106
 #endif
