@@ -45,8 +45,8 @@ constexpr int kMaxPairs = 64;  // coupled mode pairs handled by the fast path
 // the host descriptor builder and the kernel dispatch both use this.
 // Tuning of the fast kernels (FP32 / FP64): register-slot counts for level-1
 // slots of 2 functions and of 3 functions, the shared-memory budget per block
-// that the host plans terms with, and the resident blocks per SM the kernels
-// are compiled for.
+// that the host plans terms with, the resident blocks per SM the kernels are
+// compiled for, and the vectors per chunk below which a term is sliced.
 #ifndef SG_F32_RMAX2
 #define SG_F32_RMAX2 2
 #endif
@@ -59,8 +59,11 @@ constexpr int kMaxPairs = 64;  // coupled mode pairs handled by the fast path
 #ifndef SG_F32_MINBLOCKS
 #define SG_F32_MINBLOCKS 4
 #endif
-#ifndef SG_SLICE_VT
-#define SG_SLICE_VT 2
+#ifndef SG_F32_SLICE_VT
+#define SG_F32_SLICE_VT 2
+#endif
+#ifndef SG_F64_SLICE_VT
+#define SG_F64_SLICE_VT 4
 #endif
 #ifndef SG_F64_SMEM_KB
 #define SG_F64_SMEM_KB 106

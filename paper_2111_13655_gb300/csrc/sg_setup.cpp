@@ -630,12 +630,13 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
         for (int j = tp.R + s; j < tp.na; j++) sz *= LI(tp.posmode[j], lt[tp.posmode[j]]).nq;
         return sz;
     };
-    // slicing depth for a work area: the smallest leaving room for SG_SLICE_VT
-    // vectors per chunk (else half as many, ...)
+    // slicing depth for a work area: the smallest leaving room for the slicing
+    // target's vectors per chunk (else half as many, ...)
+    const int vt0 = fp32 ? SG_F32_SLICE_VT : SG_F64_SLICE_VT;
     auto depth_for = [&](int t, const TermPlan &tp, int64_t work, int smax) {
         if (2 * tp.NB > work) return -1;
         if (!tp.grid) return 0;
-        for (int vt = SG_SLICE_VT; vt >= 1; vt /= 2)
+        for (int vt = vt0; vt >= 1; vt /= 2)
             for (int s = 0; s <= std::min(smax, tp.na - tp.R); s++)
                 if ((2 * tp.NB + 2 * stage_of(t, tp, s)) * vt <= work) return s;
         return -1;
