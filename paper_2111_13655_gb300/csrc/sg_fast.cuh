@@ -428,11 +428,19 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
 {
     const size_t rb = sizeof(T);
     T *mats = reinterpret_cast<T *>(base);
-    T *gtab = mats + P.matcap;
-    T *WoF = gtab + P.fast.gcap;
+    T *WoF = mats + P.matcap + P.fast.gcap;
     T *WoB = WoF + P.fast.nbocap;
     T *work = reinterpret_cast<T *>(base + part_head_bytes(P, rb));
 
+    // the term's image (B, B^T W, H1 per position, then its G tables) is copied
+    // as it lies while warp 0 decodes the record
+    {
+        const long long i0 = P.fast.img_off[p];
+        const int isz = (int)(P.fast.img_off[p + 1] - i0);
+        const T *img = FTab<T>::img(P) + i0;
+        if (isz <= P.matcap + P.fast.gcap)
+            for (int e = tid; e < isz; e += GS) mats[e] = img[e];
+    }
     if (tid < 32) {
         load_record(P, p, reinterpret_cast<int4 *>(work), H);
         derive_layout(P, nvec, work_cap, H);
@@ -444,15 +452,7 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
     }
     const int m = H.m, R = H.R, NB = H.NB, NBo = H.NBo;
     const int *rk = P.fast.ranks + H.rank_off;
-
-    // the term's matrices (B, B^T W, H1 per position) and G tables: one contiguous image
-    {
-        const T *img = FTab<T>::img(P) + P.fast.img_off[p];
-        const int matsz = H.matsz;
-        for (int e = tid; e < matsz; e += GS) mats[e] = img[e];
-        for (int e = tid; e < H.gsize; e += GS) gtab[e] = img[matsz + e];
-    }
-    gsync<GS>();
+    const T *gtab = mats + H.matsz;  // the term's G tables follow its matrices
 
     for (int v0 = 0; v0 < nvec; v0 += H.vb) {
         const int vb = min(H.vb, nvec - v0);
