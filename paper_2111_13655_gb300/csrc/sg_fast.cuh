@@ -415,6 +415,76 @@ __host__ __device__ inline size_t part_bytes(const KParams &P, size_t rb, int wo
 }
 
 
+// Per-chunk element loops, compiled for VB vectors (no predicated lanes for
+// small chunks).  Tensor layout [i][v][o] (i: inner slots, v: vector, o: outer).
+//   chunk_in:  gather X through M^B (x: the chunk's first vector), a barrier,
+//              then the basis part Y = c0 X + sum_j H1_j x_j X, a barrier.
+//   chunk_out: the exact compress-add of D_l * Y into the accumulators of the
+//              chunk's vectors (acc: the first vector's), a barrier.
+template <typename T, int VB, int GS>
+__device__ __forceinline__ void chunk_in(FHdr &H, const KParams &P, const double *__restrict__ x,
+                                         const int *__restrict__ rk, const T *mats, T *X, T *Y, int tid)
+{
+    const int NB = H.NB, NBo = H.NBo, m = H.m, R = H.R;
+    {
+        int rn = tid < NB ? __ldg(rk + tid) : 0;
+        for (int e = tid; e < NB; e += GS) {
+            const int r = rn;
+            if (e + GS < NB) rn = __ldg(rk + e + GS);
+            const int i = fdiv(e, NBo, H.nbomag), o = e - i * NBo;
+            T xv[VB];
+#pragma unroll
+            for (int v = 0; v < VB; v++) xv[v] = (T)__ldg(x + (size_t)v * P.n_cs + r);
+#pragma unroll
+            for (int v = 0; v < VB; v++) X[(i * VB + v) * NBo + o] = xv[v];
+        }
+    }
+    gsync<GS>();
+    for (int e = tid; e < NB; e += GS) {
+        const int i = fdiv(e, NBo, H.nbomag), o = e - i * NBo;
+        const int base0 = i * VB * NBo + o;
+        T acc[VB];
+#pragma unroll
+        for (int v = 0; v < VB; v++) acc[v] = (T)H.c0 * X[base0 + v * NBo];
+        for (int j = 0; j < m; j++) {
+            const int src = j < R ? i : o;
+            const int q = fdiv(src, H.ostride[j], H.smag[j]);
+            const int nbj = H.nb[j], kj = q - fdiv(q, nbj, H.bmag[j]) * nbj;
+            const int st = j < R ? H.ostride[j] * VB * NBo : H.ostride[j];
+            const T *xp = X + base0 - kj * st;
+            const T *Hr = mats + H.oH[j] + kj * nbj;
+            for (int kp = 0; kp < nbj; kp++) {
+                const T hv = Hr[kp];
+#pragma unroll
+                for (int v = 0; v < VB; v++) acc[v] = fma_t(hv, xp[kp * st + v * NBo], acc[v]);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < VB; v++) Y[base0 + v * NBo] = acc[v];
+    }
+    gsync<GS>();
+}
+
+template <typename T, int VB, int GS>
+__device__ __forceinline__ void chunk_out(FHdr &H, const KParams &P, const int *__restrict__ rk,
+                                          const long long *__restrict__ maxbits, unsigned long long *acc,
+                                          const T *Y, int tid)
+{
+    const int NB = H.NB, NBo = H.NBo;
+    int Ev[VB];
+#pragma unroll
+    for (int v = 0; v < VB; v++) Ev[v] = fx::Acc<T>::unit(maxbits[v]);
+    for (int e = tid; e < NB; e += GS) {
+        const int i = fdiv(e, NBo, H.nbomag), o = e - i * NBo;
+        unsigned long long *a = acc + (size_t)__ldg(rk + e) * fx::Acc<T>::words;
+#pragma unroll
+        for (int v = 0; v < VB; v++)
+            fx::Acc<T>::add_unit(a + (size_t)v * P.n_cs * fx::Acc<T>::words, Y[(i * VB + v) * NBo + o], H.coef,
+                                 Ev[v], P.err);
+    }
+    gsync<GS>();
+}
+
 // One Smolyak term (processing position p of problem P) by a group of GS
 // threads: GS = 128 (a whole block) or GS = 32 (one warp; no block-wide
 // barriers).  `base` is the group's shared-memory partition (part_bytes of P
@@ -457,49 +527,13 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
     for (int v0 = 0; v0 < nvec; v0 += H.vb) {
         const int vb = min(H.vb, nvec - v0);
         T *X = work, *Y = work + NB * vb, *bufA = Y + NB * vb;
-        // gather: X[i][v][o]; all loads of an element issue together, the next rank is prefetched
-        {
-            int rn = tid < NB ? __ldg(rk + tid) : 0;
-            for (int e = tid; e < NB; e += GS) {
-                const int r = rn;
-                if (e + GS < NB) rn = __ldg(rk + e + GS);
-                const int i = fdiv(e, NBo, H.nbomag), o = e - i * NBo;
-                const double *xr = x + (size_t)v0 * P.n_cs + r;
-                T xv[kMaxVB];
-#pragma unroll
-                for (int v = 0; v < kMaxVB; v++) xv[v] = v < vb ? (T)__ldg(xr + (size_t)v * P.n_cs) : T(0);
-#pragma unroll
-                for (int v = 0; v < kMaxVB; v++)
-                    if (v < vb) X[(i * vb + v) * NBo + o] = xv[v];
-            }
+        // gather X[i][v][o] through M^B, then the basis part Y = c0 X + sum_j H1_j x_j X
+        // (element loops compiled for the chunk's vector count)
+        switch (vb) {
+#define SG_VB(VB) case VB: chunk_in<T, VB, GS>(H, P, x + (size_t)v0 * P.n_cs, rk, mats, X, Y, tid); break;
+            SG_VB(1) SG_VB(2) SG_VB(3) SG_VB(4) SG_VB(5) SG_VB(6) SG_VB(7) SG_VB(8)
+#undef SG_VB
         }
-        gsync<GS>();
-        // basis part: Y = c0 X + sum_j H1_j x_j X, all vectors of the chunk per element
-        for (int e = tid; e < NB; e += GS) {
-            const int i = fdiv(e, NBo, H.nbomag), o = e - i * NBo;
-            const int base0 = i * vb * NBo + o;
-            T acc[kMaxVB];
-#pragma unroll
-            for (int v = 0; v < kMaxVB; v++) acc[v] = v < vb ? (T)H.c0 * X[base0 + v * NBo] : T(0);
-            for (int j = 0; j < m; j++) {
-                const int src = j < R ? i : o;
-                const int q = fdiv(src, H.ostride[j], H.smag[j]);
-                const int nbj = H.nb[j], kj = q - fdiv(q, nbj, H.bmag[j]) * nbj;
-                const int st = j < R ? H.ostride[j] * vb * NBo : H.ostride[j];
-                const T *xp = X + base0 - kj * st;
-                const T *Hr = mats + H.oH[j] + kj * nbj;
-                for (int kp = 0; kp < nbj; kp++) {
-                    const T hv = Hr[kp];
-#pragma unroll
-                    for (int v = 0; v < kMaxVB; v++)
-                        if (v < vb) acc[v] = fma_t(hv, xp[kp * st + v * NBo], acc[v]);
-                }
-            }
-#pragma unroll
-            for (int v = 0; v < kMaxVB; v++)
-                if (v < vb) Y[base0 + v * NBo] = acc[v];
-        }
-        gsync<GS>();
         if (H.grid) {
             const int ps = R + H.s;
             const int NBIv = H.NBIn * vb;
@@ -578,23 +612,12 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
                 gsync<GS>();
             }
         }
-        // exact compress-add of D_l * y_l (accumulator units per vector hoisted)
-        {
-            int Ev[kMaxVB];
-#pragma unroll
-            for (int v = 0; v < kMaxVB; v++) Ev[v] = v < vb ? fx::Acc<T>::unit(maxbits[v0 + v]) : 0;
-            for (int e = tid; e < NB; e += GS) {
-                const int i = fdiv(e, NBo, H.nbomag), o = e - i * NBo;
-                const int r = __ldg(rk + e);
-                unsigned long long *acc = accp + ((size_t)v0 * P.n_cs + r) * fx::Acc<T>::words;
-#pragma unroll
-                for (int v = 0; v < kMaxVB; v++)
-                    if (v < vb)
-                        fx::Acc<T>::add_unit(acc + (size_t)v * P.n_cs * fx::Acc<T>::words,
-                                             Y[(i * vb + v) * NBo + o], H.coef, Ev[v], P.err);
-            }
+        // exact compress-add of D_l * y_l
+        switch (vb) {
+#define SG_VB(VB) case VB: chunk_out<T, VB, GS>(H, P, rk, maxbits + v0, accp + (size_t)v0 * P.n_cs * fx::Acc<T>::words, Y, tid); break;
+            SG_VB(1) SG_VB(2) SG_VB(3) SG_VB(4) SG_VB(5) SG_VB(6) SG_VB(7) SG_VB(8)
+#undef SG_VB
         }
-        gsync<GS>();
     }
 }
 
