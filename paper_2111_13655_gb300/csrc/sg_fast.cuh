@@ -421,6 +421,20 @@ __host__ __device__ inline size_t part_bytes(const KParams &P, size_t rb, int wo
 //              then the basis part Y = c0 X + sum_j H1_j x_j X, a barrier.
 //   chunk_out: the exact compress-add of D_l * Y into the accumulators of the
 //              chunk's vectors (acc: the first vector's), a barrier.
+// One row of a single-mode matrix applied along a position: acc[v] +=
+// sum_kp H[kp] x[kp * st + v * NBo], NK and VB at compile time.
+template <typename T, int VB, int NK>
+__device__ __forceinline__ void basis_row(T (&acc)[VB], const T *xp, const T *Hr, int st, int NBo)
+{
+    T hv[NK];
+#pragma unroll
+    for (int kp = 0; kp < NK; kp++) hv[kp] = Hr[kp];
+#pragma unroll
+    for (int kp = 0; kp < NK; kp++)
+#pragma unroll
+        for (int v = 0; v < VB; v++) acc[v] = fma_t(hv[kp], xp[kp * st + v * NBo], acc[v]);
+}
+
 template <typename T, int VB, int GS>
 __device__ __forceinline__ void chunk_in(FHdr &H, const KParams &P, const double *__restrict__ x,
                                          const int *__restrict__ rk, const T *mats, T *X, T *Y, int tid)
@@ -453,10 +467,17 @@ __device__ __forceinline__ void chunk_in(FHdr &H, const KParams &P, const double
             const int st = j < R ? H.ostride[j] * VB * NBo : H.ostride[j];
             const T *xp = X + base0 - kj * st;
             const T *Hr = mats + H.oH[j] + kj * nbj;
-            for (int kp = 0; kp < nbj; kp++) {
-                const T hv = Hr[kp];
+            switch (nbj) {
+                case 2: basis_row<T, VB, 2>(acc, xp, Hr, st, NBo); break;
+                case 3: basis_row<T, VB, 3>(acc, xp, Hr, st, NBo); break;
+                case 4: basis_row<T, VB, 4>(acc, xp, Hr, st, NBo); break;
+                case 5: basis_row<T, VB, 5>(acc, xp, Hr, st, NBo); break;
+                default:
+                    for (int kp = 0; kp < nbj; kp++) {
+                        const T hv = Hr[kp];
 #pragma unroll
-                for (int v = 0; v < VB; v++) acc[v] = fma_t(hv, xp[kp * st + v * NBo], acc[v]);
+                        for (int v = 0; v < VB; v++) acc[v] = fma_t(hv, xp[kp * st + v * NBo], acc[v]);
+                    }
             }
         }
 #pragma unroll
