@@ -333,17 +333,29 @@ __device__ void reg_phase(const FHdr &H, const T *mats, const T *G, T *Z, const 
 #pragma unroll
             for (int u = 0; u < NQ1; u++) hsum[b][u] = T(0);
         unsigned hb = 0;  // inner slots coupled to an outer one
+        // grid digit of outer position j at g; the chain's pairs share positions, so
+        // the digit of one pair's second position is kept for the next pair's first
+        int cj = -1, cu = 0;
+        auto uo = [&](int j) {
+            if (j == cj) return cu;
+            int u;
+            if (j < s0) {
+                u = H.uS[j];
+            } else {
+                const int q = fdiv(g, H.gstride[j], H.gmag[j]);
+                u = q - fdiv(q, H.nq[j], H.qmag[j]) * H.nq[j];
+            }
+            cj = j;
+            cu = u;
+            return u;
+        };
         if (outer_pairs)
             for (int p = 0; p < H.npair; p++) {
                 const int A = H.pa[p], B = H.pb[p];
                 if (A < R && B < R) continue;
-                auto uo = [&](int j) {
-                    if (j < s0) return H.uS[j];
-                    const int q = fdiv(g, H.gstride[j], H.gmag[j]);
-                    return q - fdiv(q, H.nq[j], H.qmag[j]) * H.nq[j];
-                };
                 if (A >= R && B >= R) {
-                    vO += G[H.pg[p] + uo(A) * H.nq[B] + uo(B)];
+                    const int ua = uo(A);
+                    vO += G[H.pg[p] + ua * H.nq[B] + uo(B)];
                 } else if (A >= R) {  // B inner: row u_A of G[u_A][u_B]
                     const T *row = G + H.pg[p] + uo(A) * NQ1;
                     hb |= 1u << B;
