@@ -8,6 +8,23 @@ current torch stream).
 
 If the library has not been built, every call raises: there is no CPU path.
 Build it with `python -m paper_2111_13655_gb300.build`.
+
+Typical use (problems come from paper_2111_13655_gb300.synth or any Problem
+with the same fields):
+
+    import torch, paper_2111_13655_gb300 as sg
+    from paper_2111_13655_gb300 import synth
+    p = synth.workload_C3()                      # D=12 L=10 chained Henon-Heiles
+    with sg.sg_create(p, "mixed") as ctx:        # or "fp64"
+        x = torch.randn(8 * ctx.n_cs, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        sg.sg_apply_H(ctx, x, y, 8)              # y = H_S x for 8 vectors
+        ev, res, vec, ok = sg.sg_eigs(ctx, 20, "davidson", block=8, tol=1e-3, vectors=True)
+    with sg.sg_create(p, "fp64") as c64:         # FP64 refinement of the mixed eigenpairs
+        ev, res, ok = sg.sg_eigs_refine(c64, vec.view(-1), tol=1e-9)
+
+Many problems per apply: sg_batch_create / sg_apply_H_batch.  Propagation:
+sg_propagate on one context, or Server (continuous batching of requests).
 """
 from __future__ import annotations
 
