@@ -215,32 +215,39 @@ def replica_throughput(world: int, units_per_rank: int, slowest_seconds: float) 
 
 
 def run_serving(args, sg, synth, torch):
-    """Poisson stream of propagation requests through the server (mixed
-    precision, continuous batching) against the same requests run one at a
-    time with sg_propagate in FP64."""
+    """Poisson streams of propagation requests through the server (mixed
+    precision, continuous batching), one per arrival rate, against the same
+    requests run one at a time with sg_propagate in FP64."""
     items = synth.workload_C5(args.serve_requests, seed=5, Ds=tuple(range(6, args.serve_dmax + 1)),
                               Ls=tuple(range(4, args.serve_lmax + 1)), steps=(20, args.serve_steps_max))
-    arrivals = np.cumsum(np.random.Generator(np.random.PCG64(55)).exponential(1.0 / args.serve_rate, len(items)))
     factors = [synth.coherent_factors(q0, p.L + 1) for p, q0, _ in items]
-    srv = sg.Server("mixed", hbm_budget_bytes=150 * 10**9)
-    ids = []
-    t0 = time.perf_counter()
-    i = 0
-    while True:
-        now = time.perf_counter() - t0
-        while i < len(items) and arrivals[i] <= now:
-            p, q0, ns = items[i]
-            ids.append(srv.submit(p, 0.1, ns, order=64, factors=factors[i]))
-            i += 1
-        a, q = srv.progress(16)
-        if a == 0 and q == 0:
-            if i == len(items):
-                break
-            time.sleep(max(0.0, arrivals[i] - (time.perf_counter() - t0)))
-    makespan = time.perf_counter() - t0
-    lat = np.array([srv.result(r)[3][1] for r in ids])
-    apps = srv.stats()["applications"]
-    srv.close()
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    sweep = []
+    apps = 0
+    for rate in rates:
+        arrivals = np.cumsum(np.random.Generator(np.random.PCG64(55)).exponential(1.0 / rate, len(items)))
+        srv = sg.Server("mixed", hbm_budget_bytes=150 * 10**9)
+        ids = []
+        t0 = time.perf_counter()
+        i = 0
+        while True:
+            now = time.perf_counter() - t0
+            while i < len(items) and arrivals[i] <= now:
+                p, q0, ns = items[i]
+                ids.append(srv.submit(p, 0.1, ns, order=64, factors=factors[i]))
+                i += 1
+            a, q = srv.progress(16)
+            if a == 0 and q == 0:
+                if i == len(items):
+                    break
+                time.sleep(max(0.0, arrivals[i] - (time.perf_counter() - t0)))
+        makespan = time.perf_counter() - t0
+        lat = np.array([srv.result(r)[3][1] for r in ids])
+        apps = srv.stats()["applications"]
+        srv.close()
+        sweep.append({"rate_req_s": rate, "applications_per_s": apps / makespan,
+                      "requests_per_s": len(items) / makespan, "makespan_s": makespan,
+                      "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}})
     # the same requests, one at a time, FP64 sg_propagate
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -253,15 +260,15 @@ def run_serving(args, sg, synth, torch):
     t_seq = time.perf_counter() - t1
     desc = (f"{len(items)} chained Henon-Heiles propagation requests, D uniform in 6..{args.serve_dmax}, "
             f"L uniform in 4..{args.serve_lmax}, nb=nq=l+1, steps uniform in 20..{args.serve_steps_max}, "
-            f"order 64, dt 0.1, Poisson arrivals at {args.serve_rate:g} req/s, budget 150 GB")
+            f"order 64, dt 0.1, Poisson arrivals, budget 150 GB")
+    head = max(sweep, key=lambda r: r["applications_per_s"])
     return {"workload": desc, "precision": "mixed (server, continuous batching)",
-            "applications_per_s": apps / makespan, "requests_per_s": len(items) / makespan,
-            "makespan_s": makespan, "latency_s": {"p50": float(np.percentile(lat, 50)),
-                                                  "p99": float(np.percentile(lat, 99))},
+            "applications_per_s": head["applications_per_s"], "rate_req_s": head["rate_req_s"],
+            "latency_s": head["latency_s"], "sweep": sweep,
             "per_request_fp64": {"applications_per_s": apps / t_seq, "requests_per_s": len(items) / t_seq,
                                  "seconds": t_seq,
                                  "note": "same requests in arrival order, sg_propagate FP64, one at a time; "
-                                         "applications counted as in the server run"}}
+                                         "applications counted as in the server runs"}}
 
 
 def run_batched(args, sg, synth, torch):
@@ -353,7 +360,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32)
-    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-rates", default="10,100,1000")
     ap.add_argument("--serve-dmax", type=int, default=20)
     ap.add_argument("--serve-lmax", type=int, default=6)
     ap.add_argument("--serve-steps-max", type=int, default=100)
