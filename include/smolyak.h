@@ -194,6 +194,24 @@ const char *sg_batch_last_error(const sg_batch *b);
 void sg_batch_destroy(sg_batch *b);
 
 /*
+ * sg_tune -- measured choice of the term schedule of a context's fast path
+ * (no counterpart in the paper, whose scheme balances MPI ranks by timing).
+ * A term whose grid leaves room for fewer than `slice_vt` vectors per chunk
+ * is sliced over its leading outer positions, else it runs unsliced in more,
+ * smaller chunks; the best target depends on the problem's term shapes and on
+ * the vectors per apply.  sg_tune re-plans the context for slice_vt = 1, 2, 4,
+ * times nvec-vector applies of each (median of three after one warm-up) on
+ * `stream` and keeps the fastest.  Only the slicing depths of the term
+ * records change; results change by rounding only.  Synchronous; allocates
+ * and frees 2 * nvec * N_cs doubles of scratch.  No other work may use the
+ * context meanwhile; batches made from it before or after see the tuned plan.
+ *   nvec 1..64; slice_vt (out, may be NULL): the target kept (0 when the
+ *   context uses the generic kernel, which has no schedule to choose);
+ *   ms (out, may be NULL): its time per apply.
+ */
+sg_status sg_tune(sg_ctx *ctx, int nvec, int *slice_vt, double *ms, void *stream);
+
+/*
  * Propagation server: continuous batching of Chebyshev propagation requests
  * (the propagator of sg_propagate: Sec. 3, Sec. 5) of different D, L and
  * basis sizes on one device.  Single-threaded: the caller submits requests

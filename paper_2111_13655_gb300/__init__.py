@@ -103,6 +103,7 @@ SIGNATURES = {
     "sg_apply_H_batch": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "sg_batch_last_error": (ctypes.c_char_p, [_vp]),
     "sg_batch_destroy": (None, [_vp]),
+    "sg_tune": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_dbl), _vp]),
     "sg_server_create": (_i32, [_i32, _i64, ctypes.POINTER(_vp)]),
     "sg_server_submit": (_i32, [_vp, _vp, _P64]),
     "sg_server_progress": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
@@ -352,6 +353,14 @@ def sg_propagate(ctx: Ctx, psi, dt: float, nsteps: int, order: int = 64, stream=
     _check(lib().sg_propagate(ctx.ptr, psi.data_ptr(), dt, nsteps, order, nl.ctypes.data, el.ctypes.data,
                               _stream_ptr(stream)), ctx)
     return nl[:nsteps], el[:nsteps]
+
+
+def sg_tune(ctx: Ctx, nvec: int = 8, stream=None):
+    """Measured choice of the fast path's slicing target (1, 2 or 4 vectors per
+    chunk) for nvec-vector applies; returns (slice_vt kept, ms per apply)."""
+    vt, ms = ctypes.c_int(), ctypes.c_double()
+    _check(lib().sg_tune(ctx.ptr, int(nvec), ctypes.byref(vt), ctypes.byref(ms), _stream_ptr(stream)), ctx)
+    return vt.value, ms.value
 
 
 def sg_product_state(ctx: Ctx, factors) -> np.ndarray:

@@ -21,7 +21,8 @@ LIB = os.path.join(OUT, "libsmolyak.so")
 # the four fast-path instantiation units take the longest and go first
 SOURCES = ["sg_fast_f32.cu", "sg_fast_f64.cu", "sg_fast_batch_f32.cu", "sg_fast_batch_f64.cu",
            "sg_setup.cpp", "sg_api.cpp", "sg_apply.cu", "sg_apply_fast.cu", "sg_solvers.cu", "sg_solvers_api.cpp",
-           "sg_apply_noalloc.cu", "sg_batch.cpp", "sg_server.cu", "sg_server_api.cpp"]
+           "sg_apply_noalloc.cu", "sg_batch.cpp", "sg_server.cu", "sg_server_api.cpp",
+           "sg_tune.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

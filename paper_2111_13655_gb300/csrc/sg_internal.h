@@ -197,6 +197,8 @@ struct HostTables {
     std::vector<unsigned> fdesc_off;  // [n_terms+1]
     int64_t franks = 0;               // total compact indices (N_s)
     int fdesccap = 0, fgcap = 0, fnbocap = 1, fn_big = 0, fwork_cta = 0, fwork_warp = 0;
+    int slice_vt = 0;                 // slicing target the records were planned with (0: default)
+    int fbudget = 0;                  // shared-memory budget the records were planned with
     int cap = 0, maxnb = 0, matcap = 0, vtabcap = 0;
     int64_t flops_per_vec = 0;       // FMA-counted work of one real apply (2 flops per FMA)
 };

@@ -373,6 +373,7 @@ std::string build_tables(const Problem &p, int smem_budget, int rb, HostTables *
         // fast kernel: matrices, G tables, slice weights and ranks, then a work
         // area for X, Y and two grid buffers (sized per term and vector chunk)
         const int fbudget = std::min(smem_budget, rb == 4 ? SG_F32_SMEM_KB * 1024 : SG_F64_SMEM_KB * 1024);
+        T.fbudget = fbudget;
         std::string de = build_fast_descs(p, rb == 4, &T, fbudget, rb);
         if (!de.empty()) return de;
     }
@@ -632,7 +633,7 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
     };
     // slicing depth for a work area: the smallest leaving room for the slicing
     // target's vectors per chunk (else half as many, ...)
-    const int vt0 = fp32 ? SG_F32_SLICE_VT : SG_F64_SLICE_VT;
+    const int vt0 = T.slice_vt > 0 ? T.slice_vt : fp32 ? SG_F32_SLICE_VT : SG_F64_SLICE_VT;
     auto depth_for = [&](int t, const TermPlan &tp, int64_t work, int smax) {
         if (2 * tp.NB > work) return -1;
         if (!tp.grid) return 0;
