@@ -771,8 +771,8 @@ cudaError_t for_variant_u(const KParams &kp, F &&f)
 {
     constexpr bool F32 = sizeof(T) == 4;
     const int nb1 = kp.fast.nb1, nq1 = kp.fast.nq1;
-    if (nb1 == 2 && nq1 == 3) return f(Variant<T, 2, 3, F32 ? SG_F32_RMAX2 : 1, UNI>{});
-    if (nb1 == 2 && nq1 == 2) return f(Variant<T, 2, 2, F32 ? SG_F32_RMAX2 : 1, UNI>{});
+    if (nb1 == 2 && nq1 == 3) return f(Variant<T, 2, 3, F32 ? SG_F32_RMAX2 : SG_F64_RMAX2, UNI>{});
+    if (nb1 == 2 && nq1 == 2) return f(Variant<T, 2, 2, F32 ? SG_F32_RMAX2 : SG_F64_RMAX2, UNI>{});
     if (nb1 == 3 && nq1 == 3) return f(Variant<T, 3, 3, F32 ? SG_F32_RMAX3 : 1, UNI>{});
     return f(Variant<T, 1, 1, 0, UNI>{});
 }

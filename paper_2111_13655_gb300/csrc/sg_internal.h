@@ -65,6 +65,9 @@ constexpr int kMaxPairs = 64;  // coupled mode pairs handled by the fast path
 #ifndef SG_F64_SLICE_VT
 #define SG_F64_SLICE_VT 4
 #endif
+#ifndef SG_F64_RMAX2
+#define SG_F64_RMAX2 2
+#endif
 #ifndef SG_F64_SMEM_KB
 #define SG_F64_SMEM_KB 106
 #endif
@@ -74,7 +77,7 @@ constexpr int kMaxPairs = 64;  // coupled mode pairs handled by the fast path
 
 inline int fast_rmax(bool fp32, int nb1, int nq1)
 {
-    if (nb1 == 2 && (nq1 == 3 || nq1 == 2)) return fp32 ? SG_F32_RMAX2 : 1;
+    if (nb1 == 2 && (nq1 == 3 || nq1 == 2)) return fp32 ? SG_F32_RMAX2 : SG_F64_RMAX2;
     if (nb1 == 3 && nq1 == 3) return fp32 ? SG_F32_RMAX3 : 1;
     return 0;
 }
