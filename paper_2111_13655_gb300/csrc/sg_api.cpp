@@ -162,7 +162,8 @@ int64_t planned_device_bytes(const sg_ctx *ctx)
     if (T.fast)
         bytes += b(T.pair_modes) + b(T.h1off) + b(T.goff) + b(T.ioff) + b(T.soff) + b(T.spoff) + b(T.fsc) +
                  b(T.ftab) * 3 / 2 + b(T.fdesc) + b(T.fdesc_off) + T.franks * (int64_t)sizeof(int) +
-                 b(T.fimg) / (ctx->fp32 ? 2 : 1) + b(T.fimg_off);
+                 b(T.fimg) / (ctx->fp32 ? 2 : 1) + b(T.fimg_off) + b(T.fvt_off) +
+                 (T.fvt_off.empty() ? 0 : T.fvt_off.back()) * (ctx->fp32 ? 4 : 8);
     return bytes;
 }
 
@@ -227,6 +228,7 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
                     (st = upload(ctx, T.fdesc, &kp.fast.desc)) != SG_OK ||
                     (st = upload(ctx, T.fdesc_off, &kp.fast.desc_off)) != SG_OK ||
                     (st = upload(ctx, T.fimg_off, &kp.fast.img_off)) != SG_OK ||
+                    (st = upload(ctx, T.fvt_off, &kp.fast.vt_off)) != SG_OK ||
                     (ctx->fp32 ? (st = upload(ctx, std::vector<float>(T.fimg.begin(), T.fimg.end()),
                                               &kp.fast.imgf)) != SG_OK
                                : (st = upload(ctx, T.fimg, &kp.fast.imgd)) != SG_OK)))) {
@@ -264,7 +266,22 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
         ctx->allocations.push_back(rp);
         ctx->bytes_device += (int64_t)T.franks * (int64_t)sizeof(int);
         kp.fast.ranks = static_cast<const int *>(rp);
+        // the coupling potential on every term's grid, in the context's precision
+        void *vp = nullptr;
+        const size_t nvt = std::max<size_t>(1, (size_t)T.fvt_off.back());
+        e = cudaMalloc(&vp, nvt * (ctx->fp32 ? sizeof(float) : sizeof(double)));
+        if (e != cudaSuccess) {
+            st = fail(nullptr, SG_ENOMEM, std::string("cudaMalloc (potential tables): ") + cudaGetErrorString(e));
+            free_all(ctx);
+            delete ctx;
+            return st;
+        }
+        ctx->allocations.push_back(vp);
+        ctx->bytes_device += (int64_t)nvt * (ctx->fp32 ? 4 : 8);
+        if (ctx->fp32) kp.fast.vtabf = static_cast<const float *>(vp);
+        else kp.fast.vtabd = static_cast<const double *>(vp);
         e = launch_build_ranks(kp, static_cast<int *>(rp), 0);
+        if (e == cudaSuccess) e = launch_build_vtab(kp, ctx->fp32, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e == cudaSuccess) {
             ctx->smem_bytes = fast_smem_bytes(kp, ctx->fp32);

@@ -37,7 +37,60 @@ __global__ void __launch_bounds__(kFT) k_build_ranks(const KParams P, int *__res
 }
 
 
+// The coupling potential V = sum_p G_p(u_a, u_b) on each term's collapsed grid,
+// once per context, in the order the term kernel's register phase reads it:
+// [slice][inner grid point gi][outer grid point g] (g fastest).  Digits: inner
+// positions from gi (first position slowest), sliced positions from the slice
+// (last fastest), the other outer positions from g.  G tables from the image.
+template <typename T>
+__global__ void __launch_bounds__(kFT) k_build_vtab(const KParams P, T *__restrict__ vt)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ FHdr H;
+    const int p = blockIdx.x;
+    const long long v0 = P.fast.vt_off[p], nv = P.fast.vt_off[p + 1] - v0;
+    if (nv == 0) return;
+    if (threadIdx.x < 32) {
+        load_record(P, p, reinterpret_cast<int4 *>(smraw), H);
+        derive_layout(P, 1, 1 << 30, H);
+    }
+    __syncthreads();
+    const int m = H.m, R = H.R, s0 = R + H.s, NGs = H.NGs;
+    long long NGI = 1;
+    for (int j = 0; j < R; j++) NGI *= H.nq[j];
+    const T *G = FTab<T>::img(P) + P.fast.img_off[p] + H.matsz;
+    for (long long e = threadIdx.x; e < nv; e += kFT) {
+        const long long per_slice = NGI * NGs;
+        const int sl = (int)(e / per_slice);
+        const long long r1 = e - (long long)sl * per_slice;
+        const int gi = (int)(r1 / NGs), g = (int)(r1 - (long long)gi * NGs);
+        int u[kMaxD];
+        int rem = gi;
+        for (int j = R - 1; j >= 0; j--) { u[j] = rem % H.nq[j]; rem /= H.nq[j]; }
+        rem = sl;
+        for (int j = s0 - 1; j >= R; j--) { u[j] = rem % H.nq[j]; rem /= H.nq[j]; }
+        for (int j = s0; j < m; j++) u[j] = (g / H.gstride[j]) % H.nq[j];
+        T v = T(0);
+        for (int q = 0; q < H.npair; q++) {
+            const int a = H.pa[q], b = H.pb[q];
+            v += G[H.pg[q] + u[a] * H.nq[b] + u[b]];
+        }
+        vt[v0 + e] = v;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_build_vtab(const KParams &kp, bool fp32, cudaStream_t stream)
+{
+    if (kp.n_terms == 0) return cudaSuccess;
+    const size_t smem = 16 * (size_t)kp.fast.desccap;
+    if (fp32)
+        k_build_vtab<float><<<(unsigned)kp.n_terms, kFT, smem, stream>>>(kp, const_cast<float *>(kp.fast.vtabf));
+    else
+        k_build_vtab<double><<<(unsigned)kp.n_terms, kFT, smem, stream>>>(kp, const_cast<double *>(kp.fast.vtabd));
+    return cudaGetLastError();
+}
 
 size_t fast_smem_bytes(const KParams &kp, bool fp32)
 {

@@ -107,11 +107,13 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return f
 
 template <typename T> struct FTab;
 template <> struct FTab<double> {
+    static __device__ const double *vt(const KParams &P) { return P.fast.vtabd; }
     static __device__ const double *img(const KParams &P) { return P.fast.imgd; }
     static __device__ const double *f(const KParams &P) { return P.fast.tabd; }
     static __device__ const double *t(const KParams &P) { return P.tabd; }
 };
 template <> struct FTab<float> {
+    static __device__ const float *vt(const KParams &P) { return P.fast.vtabf; }
     static __device__ const float *img(const KParams &P) { return P.fast.imgf; }
     static __device__ const float *f(const KParams &P) { return P.fast.tabf; }
     static __device__ const float *t(const KParams &P) { return P.tabf; }
@@ -291,7 +293,7 @@ __device__ __forceinline__ void rstage(const T (&in)[SZ], T (&out)[SZ], const T 
 // of the chunk, the inner slots basis -> grid, times the potential, grid ->
 // basis, in place in Z[i][v][g].
 template <typename T, int R, int NB1, int NQ1, bool UNI, int GS>
-__device__ void reg_phase(const FHdr &H, const T *mats, const T *G, T *Z, const int vb, const int tid)
+__device__ void reg_phase(const FHdr &H, const T *mats, const T *__restrict__ vt, T *Z, const int vb, const int tid)
 {
     constexpr int NBI = cpow(NB1, R), NGI = cpow(NQ1, R), SZ = NGI;
     constexpr int RA = R > 0 ? R : 1;
@@ -304,83 +306,13 @@ __device__ void reg_phase(const FHdr &H, const T *mats, const T *G, T *Z, const 
             Bm[b][e] = R > 0 ? mats[H.oB[b] + e] : T(0);
             BWm[b][e] = R > 0 ? mats[H.oBW[b] + e] : T(0);
         }
-    const int s0 = R + H.s, NGs = H.NGs;
-    // the part of the potential that depends on inner slots only (same for every g)
-    T Vin[SZ];
-#pragma unroll
-    for (int gi = 0; gi < NGI; gi++) Vin[gi] = T(0);
-    bool outer_pairs = false;
-    for (int p = 0; p < H.npair; p++) {
-        const int A = H.pa[p], B = H.pb[p];
-        if (A >= R || B >= R) { outer_pairs = true; continue; }
-#pragma unroll
-        for (int q0 = 0; q0 < R; q0++)
-#pragma unroll
-            for (int q1 = q0 + 1; q1 < R; q1++)
-                if (q0 == A && q1 == B)
-#pragma unroll
-                    for (int gi = 0; gi < NGI; gi++)
-                        Vin[gi] += G[H.pg[p] + ((gi / cpow(NQ1, R - 1 - q0)) % NQ1) * NQ1 +
-                                     (gi / cpow(NQ1, R - 1 - q1)) % NQ1];
-    }
+    const int NGs = H.NGs;
     for (int g = tid; g < NGs; g += GS) {
-        // add the parts that depend on the outer grid point g
+        // the coupling potential at the NGI inner points of outer grid point g
+        // (evaluated once per context; vt: this slice's table, [gi][g])
         T V[SZ];
-        T vO = T(0);
-        T hsum[RA][NQ1];
 #pragma unroll
-        for (int b = 0; b < RA; b++)
-#pragma unroll
-            for (int u = 0; u < NQ1; u++) hsum[b][u] = T(0);
-        unsigned hb = 0;  // inner slots coupled to an outer one
-        // grid digit of outer position j at g; the chain's pairs share positions, so
-        // the digit of one pair's second position is kept for the next pair's first
-        int cj = -1, cu = 0;
-        auto uo = [&](int j) {
-            if (j == cj) return cu;
-            int u;
-            if (j < s0) {
-                u = H.uS[j];
-            } else {
-                const int q = fdiv(g, H.gstride[j], H.gmag[j]);
-                u = q - fdiv(q, H.nq[j], H.qmag[j]) * H.nq[j];
-            }
-            cj = j;
-            cu = u;
-            return u;
-        };
-        if (outer_pairs)
-            for (int p = 0; p < H.npair; p++) {
-                const int A = H.pa[p], B = H.pb[p];
-                if (A < R && B < R) continue;
-                if (A >= R && B >= R) {
-                    const int ua = uo(A);
-                    vO += G[H.pg[p] + ua * H.nq[B] + uo(B)];
-                } else if (A >= R) {  // B inner: row u_A of G[u_A][u_B]
-                    const T *row = G + H.pg[p] + uo(A) * NQ1;
-                    hb |= 1u << B;
-#pragma unroll
-                    for (int b = 0; b < R; b++)
-                        if (b == B)
-#pragma unroll
-                            for (int u = 0; u < NQ1; u++) hsum[b][u] += row[u];
-                } else {              // A inner: column u_B of G[u_A][u_B]
-                    const int ub = uo(B), nqb = H.nq[B];
-                    hb |= 1u << A;
-#pragma unroll
-                    for (int b = 0; b < R; b++)
-                        if (b == A)
-#pragma unroll
-                            for (int u = 0; u < NQ1; u++) hsum[b][u] += G[H.pg[p] + u * nqb + ub];
-                }
-            }
-#pragma unroll
-        for (int gi = 0; gi < NGI; gi++) V[gi] = Vin[gi] + vO;
-#pragma unroll
-        for (int b = 0; b < R; b++)
-            if (hb & (1u << b))
-#pragma unroll
-                for (int gi = 0; gi < NGI; gi++) V[gi] += hsum[b][(gi / cpow(NQ1, R - 1 - b)) % NQ1];
+        for (int gi = 0; gi < NGI; gi++) V[gi] = __ldg(vt + (size_t)gi * NGs + g);
         for (int v = 0; v < vb; v++) {
             T va[SZ], vw[SZ];
 #pragma unroll
@@ -569,6 +501,8 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
         }
         if (H.grid) {
             const int ps = R + H.s;
+            int vt_ngi = 1;
+            for (int j = 0; j < R; j++) vt_ngi *= H.nq[j];
             const int NBIv = H.NBIn * vb;
             T *bufB = bufA + (size_t)H.NBIn * H.NGs * vb;
             for (int sl = 0; sl < H.nslice; sl++) {
@@ -616,12 +550,15 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
                 }
                 if (cur == X) oth = bufA;
                 // inner slots and potential, in registers
-                switch (R) {
-                    case 0: reg_phase<T, 0, NB1, NQ1, UNI, GS>(H, mats, gtab, cur, vb, tid); break;
-                    case 1: if constexpr (RMAX >= 1) reg_phase<T, 1, NB1, NQ1, UNI, GS>(H, mats, gtab, cur, vb, tid); break;
-                    case 2: if constexpr (RMAX >= 2) reg_phase<T, 2, NB1, NQ1, UNI, GS>(H, mats, gtab, cur, vb, tid); break;
-                    case 3: if constexpr (RMAX >= 3) reg_phase<T, 3, NB1, NQ1, UNI, GS>(H, mats, gtab, cur, vb, tid); break;
-                    default: break;
+                {
+                    const T *vts = FTab<T>::vt(P) + P.fast.vt_off[p] + (size_t)sl * H.NGs * (size_t)vt_ngi;
+                    switch (R) {
+                        case 0: reg_phase<T, 0, NB1, NQ1, UNI, GS>(H, mats, vts, cur, vb, tid); break;
+                        case 1: if constexpr (RMAX >= 1) reg_phase<T, 1, NB1, NQ1, UNI, GS>(H, mats, vts, cur, vb, tid); break;
+                        case 2: if constexpr (RMAX >= 2) reg_phase<T, 2, NB1, NQ1, UNI, GS>(H, mats, vts, cur, vb, tid); break;
+                        case 3: if constexpr (RMAX >= 3) reg_phase<T, 3, NB1, NQ1, UNI, GS>(H, mats, vts, cur, vb, tid); break;
+                        default: break;
+                    }
                 }
                 gsync<GS>();
                 // outer grid -> basis, reverse order

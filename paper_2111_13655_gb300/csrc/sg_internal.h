@@ -129,6 +129,11 @@ struct FastParams {
     const double *imgd;        // FP64 contexts
     const float *imgf;         // FP32 contexts
     const long long *img_off;  // [n_terms + 1] image starts, in elements
+    // the coupling potential on each term's collapsed grid, evaluated once per
+    // context in the term kernel's layout [slice][inner grid point][outer grid point]
+    const double *vtabd;       // FP64 contexts
+    const float *vtabf;        // FP32 contexts
+    const long long *vt_off;   // [n_terms + 1] starts, in elements (0-size for terms without a grid)
 };
 
 // Everything a kernel needs, passed by value.
@@ -196,6 +201,7 @@ struct HostTables {
     int fast_cap = 0, fast_maxnb = 0, fast_matcap = 0;
     std::vector<double> fimg;         // per-term shared-memory images (see FastParams)
     std::vector<long long> fimg_off;  // [n_terms + 1]
+    std::vector<long long> fvt_off;   // [n_terms + 1] potential-table starts (see FastParams)
     std::vector<int4> fdesc;          // term records
     std::vector<unsigned> fdesc_off;  // [n_terms+1]
     int64_t franks = 0;               // total compact indices (N_s)
@@ -224,6 +230,8 @@ cudaError_t configure_kernels(size_t smem_bytes, bool fp32);
 std::string build_fast_tables(const Problem &p, HostTables *T);
 std::string build_fast_descs(const Problem &p, bool fp32, HostTables *T, int fbudget, int rb);
 cudaError_t launch_build_ranks(const KParams &kp, int *ranks, cudaStream_t stream);
+// Fills the per-term potential tables (FastParams::vtab*) from the term images and records.
+cudaError_t launch_build_vtab(const KParams &kp, bool fp32, cudaStream_t stream);
 size_t fast_smem_bytes(const KParams &kp, bool fp32);
 cudaError_t configure_fast_kernels(const KParams &kp, bool fp32);
 cudaError_t launch_apply_fast(const KParams &kp, bool fp32, const double *x, int nvec,

@@ -692,6 +692,7 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
     T.fimg.clear();
     T.fimg.reserve(img_total);
     T.fimg_off.assign(T.n_terms + 1, 0);
+    T.fvt_off.assign(T.n_terms + 1, 0);
     int64_t rank_off = 0;
     for (int64_t q = 0; q < T.n_terms; q++) {
         const int t = T.order[q];
@@ -724,6 +725,14 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
             T.fimg.insert(T.fimg.end(), T.ftab.begin() + pr.goff, T.ftab.begin() + pr.goff + sz);
         }
         T.fimg_off[q + 1] = (long long)T.fimg.size();
+        {
+            long long ng = 0;  // the term's collapsed grid, when it has coupled pairs
+            if (tp.grid) {
+                ng = 1;
+                for (int j = 0; j < na; j++) ng *= LI(tp.posmode[j], lt[tp.posmode[j]]).nq;
+            }
+            T.fvt_off[q + 1] = T.fvt_off[q] + ng;
+        }
         tp.inds.clear();  // summed into the image's H1 matrices
         const int units = 3 + na + (int)tp.prs.size() + ((int)tp.inds.size() + 1) / 2;
         const size_t u0 = T.fdesc.size();

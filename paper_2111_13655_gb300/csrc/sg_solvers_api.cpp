@@ -122,6 +122,26 @@ struct Solver {
         }
         return rank;
     }
+    // Davidson start: unit vectors of the r lowest harmonic energies (the
+    // preconditioner's diagonal; ties by index), so the subspace overlaps the
+    // low-lying states from the first step.  False when no mode is split.
+    bool lowest_diagonal_block(double *X, int r)
+    {
+        const std::vector<double> &d = ctx->host.esplit;
+        if ((int64_t)d.size() != n) return false;
+        bool any = false;
+        for (double v : d) any |= v != 0.0;
+        if (!any) return false;
+        std::vector<int64_t> idx(n);
+        for (int64_t i = 0; i < n; i++) idx[i] = i;
+        std::partial_sort(idx.begin(), idx.begin() + r, idx.end(),
+                          [&](int64_t a, int64_t b) { return d[a] < d[b] || (d[a] == d[b] && a < b); });
+        std::vector<double> h((size_t)r * n, 0.0);
+        for (int j = 0; j < r; j++) h[(size_t)j * n + idx[j]] = 1.0;
+        ck(cudaMemcpyAsync(X, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, s), "start copy");
+        ck(cudaStreamSynchronize(s), "start sync");
+        return true;
+    }
     void random_block(double *X, int r, uint64_t seed)
     {
         std::vector<double> h((size_t)r * n);
@@ -162,7 +182,7 @@ int block_eigs(Solver &S, int nev, int b, bool davidson, double tol, int max_it,
     if (X0 && nx0 > 0) {
         r0 = std::min(nx0, kmax);
         ck(cudaMemcpyAsync(V.p, X0, sizeof(double) * n * r0, cudaMemcpyDeviceToDevice, S.s), "x0 copy");
-    } else {
+    } else if (!davidson || !S.lowest_diagonal_block(V.p, r0)) {
         S.random_block(V.p, r0, 0x5eed1234ull);
     }
     r0 = S.orthonormalise(V.p, r0);

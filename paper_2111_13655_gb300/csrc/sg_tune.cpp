@@ -7,7 +7,8 @@
 // smaller chunks.  Which is faster depends on the problem's term shapes and on
 // the block size in vectors the caller applies, so the context is re-planned
 // for every candidate and timed on real applies.  Only the slicing depths in the
-// term records change: images, M^B and capacities stay as they are.
+// term records change (and with them the layout of the per-term potential
+// tables, rebuilt for each): images, M^B and capacities stay as they are.
 #include <algorithm>
 #include <cmath>
 #include <limits>
@@ -62,7 +63,9 @@ extern "C" sg_status sg_tune(sg_ctx *ctx, int nvec, int *slice_vt, double *ms_ou
             continue;
         }
         if ((e = cudaMemcpy(const_cast<int4 *>(ctx->kp.fast.desc), T.fdesc.data(), rec_bytes,
-                            cudaMemcpyHostToDevice)) != cudaSuccess) { st = SG_ECUDA; break; }
+                            cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = sg::launch_build_vtab(ctx->kp, ctx->fp32, s)) != cudaSuccess ||  // layout follows the slicing
+            (e = cudaStreamSynchronize(s)) != cudaSuccess) { st = SG_ECUDA; break; }
         // one untimed apply, then the median of three
         std::vector<float> t;
         for (int k = 0; k < 4 && st == SG_OK; k++) {
@@ -84,6 +87,8 @@ extern "C" sg_status sg_tune(sg_ctx *ctx, int nvec, int *slice_vt, double *ms_ou
     T.fast = true;
     cudaError_t e2 = cudaMemcpy(const_cast<int4 *>(ctx->kp.fast.desc), T.fdesc.data(), rec_bytes,
                                 cudaMemcpyHostToDevice);
+    if (e2 == cudaSuccess) e2 = sg::launch_build_vtab(ctx->kp, ctx->fp32, s);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
     if (st == SG_OK && e2 != cudaSuccess) { st = SG_ECUDA; e = e2; }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
