@@ -42,7 +42,7 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes per launch of the mixed block-form term kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), from the ncu capture summarised in
 # profiles/k_apply_fast_block_mixed_D12_L10.md; reset to None when that kernel changes
-TRAFFIC_BYTES_MIXED = 1.489591e9 + 0.134730e9
+TRAFFIC_BYTES_MIXED = 7.574451e9 + 0.468579e9
 # kernels of one sg_apply_H at this workload: k_maxabs, k_apply_fast (block form
 # over the large terms), k_apply_fast (warp form over the small terms), k_finalize
 LAUNCHES_PER_APPLY = 4

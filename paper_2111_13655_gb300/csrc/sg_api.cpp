@@ -269,7 +269,8 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
         // the coupling potential on every term's grid, in the context's precision
         void *vp = nullptr;
         const size_t nvt = std::max<size_t>(1, (size_t)T.fvt_off.back());
-        e = cudaMalloc(&vp, nvt * (ctx->fp32 ? sizeof(float) : sizeof(double)));
+        // 16 bytes of padding: the term kernel prefetches 16-byte rounded ranges
+        e = cudaMalloc(&vp, nvt * (ctx->fp32 ? sizeof(float) : sizeof(double)) + 16);
         if (e != cudaSuccess) {
             st = fail(nullptr, SG_ENOMEM, std::string("cudaMalloc (potential tables): ") + cudaGetErrorString(e));
             free_all(ctx);

@@ -105,6 +105,15 @@ __device__ __forceinline__ int fdiv(int x, int d, unsigned mag)
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 
+// Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a multiple of 16)
+static __device__ __forceinline__ void l2_prefetch_bulk(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+// at most this much of a term's stored potential is prefetched at entry (the
+// largest tables are 236 KB in FP32; ~600 resident blocks share the L2)
+constexpr int kVtPrefetchBytes = 32768;
+
 template <typename T> struct FTab;
 template <> struct FTab<double> {
     static __device__ const double *vt(const KParams &P) { return P.fast.vtabd; }
@@ -467,6 +476,18 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
     T *WoB = WoF + P.fast.nbocap;
     T *work = reinterpret_cast<T *>(base + part_head_bytes(P, rb));
 
+    // the start of the term's stored potential is fetched into L2 now: it is
+    // first read after the gather, the basis part and the outer contractions
+    if (tid == 0) {
+        const long long v0 = P.fast.vt_off[p], v1 = P.fast.vt_off[p + 1];
+        if (v1 > v0) {
+            // 16-byte aligned and rounded; the table buffer is padded by 16 bytes
+            const size_t b0 = ((size_t)v0 * rb) & ~(size_t)15;
+            const size_t e1 = ((size_t)v1 * rb + 15) & ~(size_t)15;
+            const size_t b1 = e1 - b0 > (size_t)kVtPrefetchBytes ? b0 + (size_t)kVtPrefetchBytes : e1;
+            l2_prefetch_bulk(reinterpret_cast<const unsigned char *>(FTab<T>::vt(P)) + b0, (unsigned)(b1 - b0));
+        }
+    }
     // the term's image (B, B^T W, H1 per position, then its G tables) is copied
     // as it lies while warp 0 decodes the record
     {

@@ -44,6 +44,18 @@ def test_lanczos_uncoupled_2d_spectrum_with_degeneracies():
     assert np.max(np.abs(ev - np.array([1, 2, 2, 3, 3, 3, 4, 4, 4, 4.0]))) < 1e-10
 
 
+def test_davidson_uncoupled_2d_spectrum_with_degeneracies():
+    """D=2 L=6, lambda = 0, H diagonal: the unit-vector start block holds exact
+    eigenvectors (zero residuals) and the exact diagonal preconditioner maps every
+    correction back into the basis, so the other states come from the random
+    directions added then.  Spectrum 1,2,2,3,3,3,4,4,4,4 as in the Lanczos case."""
+    p = synth.workload_C1(lam=0.0)
+    with sg.sg_create(p, "fp64") as ctx:
+        ev, rs, _, ok = sg.sg_eigs(ctx, 10, "davidson", block=4, tol=1e-10, max_it=100)
+    assert ok
+    assert np.max(np.abs(ev - np.array([1, 2, 2, 3, 3, 3, 4, 4, 4, 4.0]))) < 1e-10
+
+
 def test_lanczos_henon_heiles_2d_matches_oracle_matrix():
     p = synth.workload_C1()
     ref = np.linalg.eigvalsh(0.5 * (dense_oracle(p) + dense_oracle(p).T))[:10]
