@@ -351,12 +351,13 @@ def time_device(ctx, xd, yd, nvec, steps, warmup, flush, torch, sg):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nvec", type=int, default=8)
-    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu1-seconds", type=float, default=5.0)
     ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32)
@@ -390,6 +391,9 @@ def main():
         orc.build()
         r, desc, cores = oracle_sample_rate(synth.workload_C3(), 646646, args.cpu_seconds, 7)
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        if args.cpu1_seconds > 0:  # the same oracle on one host thread
+            r1, desc1, _ = oracle_sample_rate(synth.workload_C3(), 646646, args.cpu1_seconds, 8, threads=1)
+            cpu["single_thread"] = {"value": r1, "unit": UNIT, "cores": 1, "sample": desc1}
 
     p = synth.workload_C3()
     nvec = args.nvec
