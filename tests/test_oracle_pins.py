@@ -231,3 +231,82 @@ def test_masked_galerkin_matrix_is_its_apply_and_symmetric():
     y = galerkin.apply_H(p, x)
     assert np.abs((M @ x.T).T - y).max() <= 1e-13 * np.abs(y).max()
     assert abs(M - M.T).max() <= 1e-14
+
+
+# ---------------------------------------------------------------- Smolyak quadrature exactness
+
+def _hermite_function(k, q):
+    """Orthonormal Hermite function b_k(q), through numpy's physicists' Hermite series."""
+    c = np.zeros(k + 1)
+    c[k] = 1.0
+    norm = math.sqrt(2.0 ** k * math.factorial(k) * math.sqrt(math.pi))
+    return np.polynomial.hermite.hermval(q, c) * np.exp(-q * q / 2) / norm
+
+
+def _gaussian_moment(p):
+    """int b_0(q)^2 q^p dq = (p-1)!!/2^(p/2) for even p, 0 for odd p."""
+    if p % 2:
+        return 0.0
+    return math.prod(range(p - 1, 0, -2)) / 2.0 ** (p // 2)
+
+
+def _surplus_column(D, L, nb_rule, nq_rule, monos):
+    """Column H_S e_0 of a kinetic-free problem with V = sum of product monomials,
+    from the hierarchical (surplus) form of the Smolyak formula instead of the
+    combination coefficients: sum_{|l| <= L} prod_i (g_i(l_i) - g_i(l_i - 1)),
+    where g_i(l) = [k_i < nb(l)] sum_u w_u b_{k_i}(Q_u) b_0(Q_u) Q_u^{p_i} on
+    numpy's level-l Gauss-Hermite rule (weights times e^{Q^2}, so that the rule
+    integrates b_k b_k' exactly).  Both forms are the same sum (Sec. 2, Eqs. (6)-(8))."""
+    import itertools
+
+    nb = lambda l: nb_rule[0] + nb_rule[1] * l
+    nq = lambda l: nq_rule[0] + nq_rule[1] * l
+    lmin = lambda k: next(l for l in range(L + 1) if nb(l) > k)
+    compact = [k for k in itertools.product(range(nb(L)), repeat=D) if sum(lmin(ki) for ki in k) <= L]
+
+    def g(l, k, p):
+        if l < 0 or k >= nb(l):
+            return 0.0
+        x, w = np.polynomial.hermite.hermgauss(nq(l))
+        return float(np.sum(w * np.exp(x * x) * _hermite_function(k, x) * _hermite_function(0, x) * x ** p))
+
+    levels = [l for l in itertools.product(range(L + 1), repeat=D) if sum(l) <= L]
+    y = np.zeros(len(compact))
+    for c, factors in monos:
+        pw = [0] * D
+        for mode, power in factors:
+            pw[mode] = power
+        for j, k in enumerate(compact):
+            y[j] += c * sum(math.prod(g(l[i], k[i], pw[i]) - g(l[i] - 1, k[i], pw[i]) for i in range(D))
+                            for l in levels)
+    return y
+
+
+@pytest.mark.parametrize("D, L, nq_rule, monos", [
+    (2, 3, (1, 1), [(1.0, [(0, 4), (1, 2)])]),
+    (2, 2, (1, 1), [(1.0, [(0, 4), (1, 2)])]),                        # not exact at this level
+    (3, 4, (1, 1), [(0.7, [(0, 3), (2, 2)]), (1.3, [(1, 2)])]),
+    (2, 5, (1, 2), [(1.0, [(0, 5), (1, 1)]), (-0.4, [(0, 2), (1, 6)])]),
+])
+def test_smolyak_quadrature_of_monomials(D, L, nq_rule, monos):
+    """Kinetic-free V = sum of monomials, ground state in: the oracle's column equals
+    the hierarchical Smolyak sum; <0|H_S|0> is the exact Gaussian moment product
+    exactly when levels e(p_i) with 2 nq(e) - 1 >= p_i fit within L (Smolyak
+    quadrature exactness), and differs from it otherwise."""
+    p = synth.polynomial_problem(D, L, np.zeros(D), monos, nb_rule=(1, 1), nq_rule=nq_rule)
+    n = orc.n_compact(p)
+    x = np.zeros((1, n))
+    x[0, 0] = 1.0
+    y = orc.apply_H(p, x)[0]
+    ref = _surplus_column(D, L, (1, 1), nq_rule, monos)
+    assert y.shape == ref.shape
+    assert np.abs(y - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max())
+    exact, within = 0.0, True
+    for c, factors in monos:
+        exact += c * math.prod(_gaussian_moment(pw) for _, pw in factors)
+        e = [next(l for l in range(100) if 2 * (nq_rule[0] + nq_rule[1] * l) - 1 >= pw) for _, pw in factors]
+        within &= sum(e) <= L
+    if within:
+        assert abs(y[0] - exact) <= 1e-13 * max(1.0, abs(exact))
+    else:
+        assert abs(y[0] - exact) > 1e-6
