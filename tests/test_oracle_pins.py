@@ -256,7 +256,9 @@ def _surplus_column(D, L, nb_rule, nq_rule, monos):
     combination coefficients: sum_{|l| <= L} prod_i (g_i(l_i) - g_i(l_i - 1)),
     where g_i(l) = [k_i < nb(l)] sum_u w_u b_{k_i}(Q_u) b_0(Q_u) Q_u^{p_i} on
     numpy's level-l Gauss-Hermite rule (weights times e^{Q^2}, so that the rule
-    integrates b_k b_k' exactly).  Both forms are the same sum (Sec. 2, Eqs. (6)-(8))."""
+    integrates b_k b_k' exactly).  The combination formula of Eq. (8) and this
+    hierarchical form are the same sum for any per-mode sequences g_i (an identity
+    of the combination technique); the 1D rules enter through Eqs. (6)-(7)."""
     import itertools
 
     nb = lambda l: nb_rule[0] + nb_rule[1] * l
