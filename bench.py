@@ -41,7 +41,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes per launch of the mixed block-form term kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), from the ncu capture summarised in
-# profiles/k_apply_fast_block_mixed_D12_L10.md; reset to None when that kernel changes
+# profiles/k_apply_fast_block_mixed_D12_L10.md; reset to None when that kernel changes.
+# The capture predates the fewest-multiply-add order of the outer slots, which
+# changed the term records only: the same kernel streams the same bytes.
 TRAFFIC_BYTES_MIXED = 7.574451e9 + 0.468579e9
 # kernels of one sg_apply_H at this workload: k_maxabs, k_apply_fast (block form
 # over the large terms), k_apply_fast (warp form over the small terms), k_finalize
@@ -52,8 +54,15 @@ def algorithmic_flops_per_vector(levels: np.ndarray, nbA=1, nbB=1, nqA=2, nqB=1)
     """FLOPs of one real-vector apply by the route the kernel takes: per term,
     forward and backward one-mode contractions over the modes with nb > 1
     (2 flops per multiply-add), the kinetic matrices in the basis, one multiply
-    per grid point for the potential, and the weighted compress-add."""
+    per grid point for the potential, and the weighted compress-add.  The
+    forward chain takes the modes in the kernel's order: ascending
+    1/nb - 1/nq (for nb = l+1, nq = l+2: higher levels first), ties in mode
+    order; the backward chain mirrors it."""
     l = levels.astype(np.int64)
+    nb0 = nbA + nbB * l
+    nq0 = nqA + nqB * l
+    key = np.where(nb0 > 1, 1.0 / nb0 - 1.0 / nq0, np.inf)
+    l = np.take_along_axis(l, np.argsort(key, axis=1, kind="stable"), axis=1)
     nb = nbA + nbB * l
     nq = nqA + nqB * l
     act = nb > 1

@@ -84,7 +84,8 @@ inline int fast_rmax(bool fp32, int nb1, int nq1)
 
 // Per-term record of the fast kernel, in processing order, 16-byte units:
 // header | positions[m] | active pairs[npair] | induced matrices[nind] (padded).
-// Positions: the inner slots (mode order) first, then the outer slots (mode order).
+// Positions: the inner slots (mode order) first, then the outer slots in the
+// order of fewest multiply-adds (ascending 1/nb - 1/nq, ties in mode order).
 struct alignas(16) FDescHdr {
     int m, R, NB, coef;          // positions, inner positions, basis size, D_l
     int s, npair, nind, gsize;   // slicing depth, active pairs, induced matrices, G-table words

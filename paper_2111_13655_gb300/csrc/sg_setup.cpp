@@ -598,7 +598,19 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
             if (l1[a]) { inner[a] = true; R++; }
         int pos = 0;
         for (int a = 0; a < na; a++) if (inner[a]) { pos_of_mode[act[a]] = pos; tp.posmode[pos++] = act[a]; }
-        for (int a = 0; a < na; a++) if (!inner[a]) { pos_of_mode[act[a]] = pos; tp.posmode[pos++] = act[a]; }
+        // Outer slots in the order of the forward (basis -> grid) chain that needs
+        // the fewest multiply-adds.  A contraction costs (current size) x nq and
+        // multiplies the size by nq/nb, so swapping neighbours j, k shows that j
+        // goes first iff 1/nb_j - 1/nq_j < 1/nb_k - 1/nq_k (for nb = l+1,
+        // nq = l+2: higher levels first).  Compared exactly in integers; ties
+        // keep mode order.  The backward chain runs in reverse.
+        int outer[kMaxD], no = 0;
+        for (int a = 0; a < na; a++) if (!inner[a]) outer[no++] = a;
+        std::stable_sort(outer, outer + no, [&](int x, int y) {
+            const LevelInfo &u = LI(act[x], lt[act[x]]), &w = LI(act[y], lt[act[y]]);
+            return (int64_t)(u.nq - u.nb) * w.nb * w.nq < (int64_t)(w.nq - w.nb) * u.nb * u.nq;
+        });
+        for (int k = 0; k < no; k++) { pos_of_mode[act[outer[k]]] = pos; tp.posmode[pos++] = act[outer[k]]; }
         tp.na = na; tp.R = R; tp.NB = 1; tp.NBIn = 1;
         for (int j = 0; j < na; j++) {
             tp.NB *= LI(tp.posmode[j], lt[tp.posmode[j]]).nb;
