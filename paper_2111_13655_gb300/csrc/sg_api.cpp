@@ -411,9 +411,10 @@ sg_status sg_device_error(sg_ctx *ctx, int *code)
     cudaError_t e = cudaMemcpy(&v, ctx->kp.err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "read error word");
     *code = v;
-    if (v) {
+    if (v) {  // reported once: clear it for the next apply
         int z = 0;
-        cudaMemcpy(ctx->kp.err, &z, sizeof(int), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(ctx->kp.err, &z, sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "clear error word");
     }
     return SG_OK;
 }

@@ -69,9 +69,9 @@ extern "C" sg_status sg_tune(sg_ctx *ctx, int nvec, int *slice_vt, double *ms_ou
         // one untimed apply, then the median of three
         std::vector<float> t;
         for (int k = 0; k < 4 && st == SG_OK; k++) {
-            cudaEventRecord(e0, s);
+            if ((e = cudaEventRecord(e0, s)) != cudaSuccess) { st = SG_ECUDA; break; }
             st = sg_apply_H(ctx, x, y, nvec, stream);
-            cudaEventRecord(e1, s);
+            if (st == SG_OK && (e = cudaEventRecord(e1, s)) != cudaSuccess) st = SG_ECUDA;
             if (st == SG_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) st = SG_ECUDA;
             float ms = 0.f;
             if (st == SG_OK) cudaEventElapsedTime(&ms, e0, e1);
@@ -95,7 +95,8 @@ extern "C" sg_status sg_tune(sg_ctx *ctx, int nvec, int *slice_vt, double *ms_ou
     cudaFree(x);
     cudaFree(y);
     if (st != SG_OK) {
-        if (st == SG_ECUDA) ctx->last_error = std::string("sg_tune: ") + cudaGetErrorString(e);
+        // a failed apply has set its own message; CUDA errors of the tuner set this one
+        if (st == SG_ECUDA && e != cudaSuccess) ctx->last_error = std::string("sg_tune: ") + cudaGetErrorString(e);
         return st;
     }
     if (slice_vt) *slice_vt = best_vt;
