@@ -460,10 +460,11 @@ def main():
         torch.cuda.empty_cache()
 
     serving = None
-    if rank == 0 and not args.no_serving:
+    # single-GPU legs: at N > 1 they would hold the other GPUs idle
+    if world == 1 and not args.no_serving:
         serving = run_serving(args, sg, synth, torch)
     batched = None
-    if rank == 0 and not args.no_batched:
+    if world == 1 and not args.no_batched:
         batched = run_batched(args, sg, synth, torch)
 
     if rank == 0:
