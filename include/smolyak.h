@@ -97,6 +97,11 @@ typedef struct {
  *          the grid multiply in FP32, accumulation of the compact result in FP64.
  *   out    receives the context (owned by the caller, release with sg_destroy).
  * Setup runs on the host plus synchronous uploads on the current device.
+ * The context keeps on the device M^B (4 bytes per term basis function), the
+ * per-term records and 1D tables, and, when every monomial of V touches at most
+ * two modes, the coupling potential at every grid point of every term (4 bytes
+ * per point for SG_MIXED, 8 for SG_FP64; about 5.1 / 10.2 GB at D=12 L=10,
+ * nq = l+2).  sg_size reports the total.
  * Limits of this build (SG_EUNSUPPORTED): nb(L), nq(L) <= 32, N_cs < 2^31,
  * at most 256 monomials with at most 8 factors each, powers <= 16.
  */
