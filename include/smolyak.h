@@ -24,6 +24,8 @@
  *     sum_u w_u b_k(Q_u) b_k'(Q_u) = delta_kk' whenever nq >= nb.
  *   - Hamiltonian: H = sum_i omega_i/2 (-d^2/dQ_i^2) + V(Q), V a sparse
  *     polynomial (the Henon-Heiles form of Eq. (18) is one instance).
+ *   - A context lives on the CUDA device that was current at sg_create; its
+ *     calls with device work return SG_EINVAL when another device is current.
  *   - Every call that takes a `stream` is enqueued on that CUDA stream
  *     (cudaStream_t passed as void*, NULL = legacy default stream) and
  *     returns before the GPU work ends, unless stated otherwise.

@@ -318,6 +318,7 @@ sg_status sg_apply_H(sg_ctx *ctx, const double *x, double *y, int nvec, void *st
 {
     if (!ctx) return SG_EINVAL;
     if (!ctx->has_device) return fail(ctx, SG_EINVAL, "context was made by sg_plan (no device state)");
+    if (!sg_on_ctx_device(ctx)) return fail(ctx, SG_EINVAL, "the current CUDA device is not the one the context was made on");
     if (!x || !y) return fail(ctx, SG_EINVAL, "x or y is NULL");
     if (nvec < 1) return fail(ctx, SG_EINVAL, "nvec must be >= 1");
     const size_t n = (size_t)ctx->host.n_cs * nvec;
@@ -334,6 +335,7 @@ sg_status sg_apply_H_host(sg_ctx *ctx, const double *x_host, double *y_host, int
 {
     if (!ctx) return SG_EINVAL;
     if (!ctx->has_device) return fail(ctx, SG_EINVAL, "context was made by sg_plan (no device state)");
+    if (!sg_on_ctx_device(ctx)) return fail(ctx, SG_EINVAL, "the current CUDA device is not the one the context was made on");
     if (!x_host || !y_host) return fail(ctx, SG_EINVAL, "x_host or y_host is NULL");
     if (nvec < 1) return fail(ctx, SG_EINVAL, "nvec must be >= 1");
     const int64_t n = ctx->host.n_cs * (int64_t)nvec;
@@ -391,6 +393,7 @@ sg_status sg_index_map(sg_ctx *ctx, int64_t t0, int64_t nt, int64_t *offsets_hos
     }
     if (!cs_index_dev || nt == 0) return SG_OK;
     if (!ctx->has_device) return fail(ctx, SG_EINVAL, "context was made by sg_plan (no device state)");
+    if (!sg_on_ctx_device(ctx)) return fail(ctx, SG_EINVAL, "the current CUDA device is not the one the context was made on");
     int64_t *offs_dev = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMalloc(&offs_dev, sizeof(int64_t) * (nt + 1));
@@ -407,6 +410,7 @@ sg_status sg_device_error(sg_ctx *ctx, int *code)
 {
     if (!ctx || !code) return SG_EINVAL;
     if (!ctx->has_device) return fail(ctx, SG_EINVAL, "context was made by sg_plan (no device state)");
+    if (!sg_on_ctx_device(ctx)) return fail(ctx, SG_EINVAL, "the current CUDA device is not the one the context was made on");
     int v = 0;
     cudaError_t e = cudaMemcpy(&v, ctx->kp.err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "read error word");

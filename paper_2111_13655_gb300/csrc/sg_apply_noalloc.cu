@@ -54,6 +54,7 @@ extern "C" sg_status sg_apply_H_noalloc(sg_ctx *ctx, const double *x, double *y,
 {
     if (!ctx) return SG_EINVAL;
     if (!ctx->has_device) return noalloc_fail(ctx, SG_EINVAL, "context was made by sg_plan (no device state)");
+    if (!sg_on_ctx_device(ctx)) return noalloc_fail(ctx, SG_EINVAL, "the current CUDA device is not the one the context was made on");
     if (!x || !y) return noalloc_fail(ctx, SG_EINVAL, "x or y is NULL");
     if (nvec < 1) return noalloc_fail(ctx, SG_EINVAL, "nvec must be >= 1");
     const size_t n = (size_t)ctx->host.n_cs * (size_t)nvec;

@@ -303,3 +303,11 @@ struct sg_ctx {
     int acc_nvec = 0;
     std::string last_error;
 };
+
+// Calls with device work run on the device the context was made on: from any
+// other current device its kernels would be handed another GPU's pointers.
+inline bool sg_on_ctx_device(const sg_ctx *ctx)
+{
+    int cur = -1;
+    return cudaGetDevice(&cur) == cudaSuccess && cur == ctx->device;
+}

@@ -323,6 +323,7 @@ sg_status sg_eigs(sg_ctx *ctx, int nev, int method, int block, double tol, int m
 {
     if (!ctx) return SG_EINVAL;
     if (!ctx->has_device) { ctx->last_error = "context was made by sg_plan"; return SG_EINVAL; }
+    if (!sg_on_ctx_device(ctx)) { ctx->last_error = "the current CUDA device is not the one the context was made on"; return SG_EINVAL; }
     if (nev < 1 || nev > ctx->host.n_cs || !evals || !(tol > 0) || max_it < 1 ||
         (method != SG_LANCZOS && method != SG_DAVIDSON)) {
         ctx->last_error = "sg_eigs: need 1 <= nev <= N_cs, tol > 0, max_it >= 1, a known method, evals";
@@ -351,6 +352,7 @@ sg_status sg_eigs_refine(sg_ctx *ctx, int nev, double *evecs, double *evals, dou
         ctx->last_error = "sg_eigs_refine: invalid arguments";
         return SG_EINVAL;
     }
+    if (!sg_on_ctx_device(ctx)) { ctx->last_error = "the current CUDA device is not the one the context was made on"; return SG_EINVAL; }
     const int b = std::min(nev, kBlk);
     try {
         Solver S(ctx, (cudaStream_t)stream, std::max(3 * nev, nev + 6 * b) + 8);
@@ -398,6 +400,7 @@ sg_status sg_propagate(sg_ctx *ctx, double *psi, double dt, int nsteps, int orde
         ctx->last_error = "sg_propagate: invalid arguments";
         return SG_EINVAL;
     }
+    if (!sg_on_ctx_device(ctx)) { ctx->last_error = "the current CUDA device is not the one the context was made on"; return SG_EINVAL; }
     try {
         Solver S(ctx, (cudaStream_t)stream, 48);
         const int64_t n = S.n;

@@ -21,6 +21,7 @@ extern "C" sg_status sg_tune(sg_ctx *ctx, int nvec, int *slice_vt, double *ms_ou
 {
     if (!ctx) return SG_EINVAL;
     if (!ctx->has_device) { ctx->last_error = "sg_tune: context was made by sg_plan"; return SG_EINVAL; }
+    if (!sg_on_ctx_device(ctx)) { ctx->last_error = std::string("sg_tune: ") + "the current CUDA device is not the one the context was made on"; return SG_EINVAL; }
     if (nvec < 1 || nvec > 64) { ctx->last_error = "sg_tune: need 1 <= nvec <= 64"; return SG_EINVAL; }
     sg::HostTables &T = ctx->host;
     if (!ctx->kp.fast.enabled) {  // generic kernel: no schedule to choose
