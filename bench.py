@@ -37,7 +37,7 @@ UNIT = "applications/s"
 WORKLOAD = "chained Henon-Heiles D=12 L=10 nb=l+1 nq=l+2 (N_cs=646646, 646646 terms)"
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.070 GHz (max SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# FP64: the nominal GB300 rate (1.25 TFLOP/s); the FMA microbenchmark is reported beside it
+# FP64: the nominal GB300 rate (1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes per launch of the mixed block-form term kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), from the ncu capture summarised in
