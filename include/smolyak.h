@@ -122,7 +122,9 @@ sg_status sg_plan(int D, int L, const sg_basis *basis, const sg_grid *grids,
 
 /* Sizes: n_cs = N_cs (compact basis), n_terms = N_st, n_s = N_s (sum of term
  * basis sizes, Sec. 2, Eq. (11)), n_grid = sum of term grid sizes, bytes_device =
- * device memory held by the context.  Any pointer may be NULL. */
+ * device memory held by the context (for a context made by sg_plan: the tables
+ * sg_create would allocate for the same problem, without the apply workspace,
+ * which grows with the block size).  Any pointer may be NULL. */
 sg_status sg_size(const sg_ctx *ctx, int64_t *n_cs, int64_t *n_terms, int64_t *n_s,
                   int64_t *n_grid, int64_t *bytes_device);
 

@@ -310,7 +310,9 @@ sg_status sg_size(const sg_ctx *ctx, int64_t *n_cs, int64_t *n_terms, int64_t *n
     if (n_terms) *n_terms = ctx->host.n_terms;
     if (n_s) *n_s = ctx->host.n_s;
     if (n_grid) *n_grid = ctx->host.n_grid;
-    if (bytes_device) *bytes_device = ctx->bytes_device;
+    // a context made by sg_plan holds nothing on the device: report what
+    // sg_create would allocate for the same problem
+    if (bytes_device) *bytes_device = ctx->has_device ? ctx->bytes_device : sg::planned_device_bytes(ctx);
     return SG_OK;
 }
 

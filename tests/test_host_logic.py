@@ -96,3 +96,20 @@ def test_c3_plan_sizes():
     assert s["n_terms"] == 646646 and s["n_cs"] == 646646 and s["n_s"] == 131128140
     assert s["n_grid"] == 68292740824
     sg.sg_destroy(ctx)
+
+
+def test_plan_reports_the_device_bytes_of_sg_create():
+    """A planned context holds no device memory but reports what sg_create would
+    allocate. At D=12 L=10 that includes M^B (N_s int32) and the coupling
+    potential at every grid point of the coupled terms: 1,248,275,065 points.
+    Both are in the context's precision for the potential, so FP64 needs more."""
+    p = synth.workload_C3()
+    sizes = {}
+    for prec, rb in (("mixed", 4), ("fp64", 8)):
+        ctx = sg.sg_plan(p, prec)
+        b = sg.sg_size(ctx)["bytes_device"]
+        sg.sg_destroy(ctx)
+        lower = 131128140 * 4 + 1248275065 * rb
+        assert lower <= b <= lower + 3 * 10 ** 9, (prec, b)
+        sizes[prec] = b
+    assert sizes["fp64"] > sizes["mixed"]
