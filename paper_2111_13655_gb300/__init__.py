@@ -227,6 +227,11 @@ def _dev_ptr(t, n_expected: int, name: str):
         raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
     if t.numel() != n_expected:
         raise ValueError(f"{name} has {t.numel()} elements, expected {n_expected}")
+    # the library requires the context's device to be current: a tensor on
+    # another GPU would hand its kernels a foreign pointer
+    cur = torch.cuda.current_device()
+    if t.device.index != cur:
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{cur}")
     return t.data_ptr()
 
 
