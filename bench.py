@@ -35,16 +35,12 @@ sys.path.insert(0, ROOT)
 METRIC = "Smolyak H|psi> applications/s and % roofline at D=12 L=10; mixed vs FP64; p50/p99"
 UNIT = "applications/s"
 WORKLOAD = "chained Henon-Heiles D=12 L=10 nb=l+1 nq=l+2 (N_cs=646646, 646646 terms)"
-# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.070 GHz (max SM clock)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# FP64: the nominal GB300 rate (1.25 TFLOP/s)
-FP64_PEAK_TFLOPS = 1.25
-# DRAM bytes per launch of the mixed block-form term kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum), from the ncu capture summarised in
-# profiles/k_apply_fast_block_mixed_D12_L10.md; reset to None when that kernel changes.
-# The capture predates the fewest-multiply-add order of the outer slots, which
-# changed the term records only: the same kernel streams the same bytes.
-TRAFFIC_BYTES_MIXED = 7.574451e9 + 0.468579e9
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant term kernel at the benchmark workload, per precision, from the ncu
+# captures summarised in profiles/; None until the current kernel is captured.
+TRAFFIC_BYTES = {"mixed": None, "fp64": None}
+# FP32 lanes per SM (the unit count of the derived FP32 peak)
+FP32_LANES_PER_SM = 128
 # kernels of one sg_apply_H at this workload: k_maxabs, k_apply_fast (block form
 # over the large terms), k_apply_fast (warp form over the small terms), k_finalize
 LAUNCHES_PER_APPLY = 4
@@ -156,6 +152,41 @@ def oracle_sample_rate(problem, n_terms: int, seconds: float, seed: int, threads
         f"full apply estimated as sample time x {n_terms}/{n}", used
 
 
+def bench_config(args, world: int) -> dict:
+    """The `config` of the JSON line; the same for both arms."""
+    return {"workload": workload_name(args.L), "precision": "mixed (FP32 contractions, FP64 accumulation)",
+            "vectors_per_step": args.nvec, "parallelism": f"replicas x{world}",
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
+def workload_name(L: int) -> str:
+    if L == 10:
+        return WORKLOAD
+    return f"chained Henon-Heiles D=12 L={L} nb=l+1 nq=l+2 (reduced size)"
+
+
+def measure_peaks(sg, torch, seconds: float) -> dict:
+    """Roofline denominators measured on this GPU: FP32 (the larger of the scalar
+    and the packed two-lane fma loops) and FP64 fma throughput from
+    sg_measure_peak, with the SM clock sampled meanwhile.  Beside them the
+    derived FP32 figure: SM count (read from the device) x 128 lanes x 2 flops
+    x the maximum SM clock."""
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        f32, sms = sg.sg_measure_peak("fp32", seconds)
+        f32x2, _ = sg.sg_measure_peak("fp32x2", seconds)
+        f64, _ = sg.sg_measure_peak("fp64", seconds)
+    c = clk.summary()
+    mx = c.get("sm_max_mhz") or 2070.0
+    clock = f"SM clock median {c.get('sm_mhz')} MHz of max {mx} MHz, reasons {c.get('reasons')}"
+    return {"fp32": max(f32, f32x2) / 1e12, "fp64": f64 / 1e12, "sms": sms,
+            "fp32_scalar": f32 / 1e12, "fp32_packed": f32x2 / 1e12,
+            "derived_fp32": sms * FP32_LANES_PER_SM * 2 * mx * 1e6 / 1e12,
+            "note_fp32": f"measured FP32 fma loop on {sms} SMs (scalar {f32 / 1e12:.1f}, packed f32x2 "
+                         f"{f32x2 / 1e12:.1f} TFLOP/s; the larger); {clock}",
+            "note_fp64": f"measured FP64 fma loop on {sms} SMs; {clock}",
+            "clocks": c}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -176,9 +207,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64 (CPU oracle)"},
+            "data": "synthetic", "config": bench_config(args, 1),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "each step: " + desc},
+                             "sample": "each step: " + desc + " (the FP64 CPU oracle, one vector)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -378,6 +409,10 @@ def main():
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--L", type=int, default=10, help="Smolyak level of the D=12 workload (10: the benchmark)")
+    ap.add_argument("--precisions", default="mixed,fp64")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--peak-seconds", type=float, default=1.0, help="0: skip the peak measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -404,10 +439,16 @@ def main():
             r1, desc1, _ = oracle_sample_rate(synth.workload_C3(), 646646, args.cpu1_seconds, 8, threads=1)
             cpu["single_thread"] = {"value": r1, "unit": UNIT, "cores": 1, "sample": desc1}
 
-    p = synth.workload_C3()
+    peaks = None
+    if args.peak_seconds > 0:
+        peaks = measure_peaks(sg, torch, args.peak_seconds)
+    else:
+        peaks = {"fp32": None, "fp64": None, "note_fp32": "not measured", "note_fp64": "not measured",
+                 "derived_fp32": None}
+    p = synth.workload_C3(L=args.L)
     nvec = args.nvec
     results = {}
-    for prec in ("mixed", "fp64"):
+    for prec in args.precisions.split(","):
         ctx = sg.sg_create(p, prec)
         n = ctx.n_cs
         x = synth.random_vectors(n, nvec, 11 + rank)
@@ -429,20 +470,22 @@ def main():
         lv, _ = sg.sg_term_levels(ctx)
         f_alg = algorithmic_flops_per_vector(lv) * nvec
         ms = total_ms / steps
-        peak = FP32_PEAK_TFLOPS if prec == "mixed" else FP64_PEAK_TFLOPS
+        peak = peaks["fp32"] if prec == "mixed" else peaks["fp64"]
         achieved = f_alg / (statistics.mean(times) * 1e-3) / 1e12
+        frac = achieved / peak if peak else None
         results[prec] = {
             "value": replica_throughput(world, nvec * steps, total_ms * 1e-3), "ms_per_step": ms, "steps": steps,
             "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak,
-                         "traffic": TRAFFIC_BYTES_MIXED if prec == "mixed" else None,
+                         "frac": frac,
+                         "traffic": TRAFFIC_BYTES[prec],
                          "flops_per_launch": f_alg,
-                         "peak_note": ("FP32 CUDA cores, derived: 152 SM x 128 lanes x 2 x 2.07 GHz"
-                                       if prec == "mixed" else "FP64, nominal GB300 rate")},
+                         "peak_source": "measured",
+                         "peak_note": peaks["note_fp32" if prec == "mixed" else "note_fp64"],
+                         "peak_derived": peaks["derived_fp32"] if prec == "mixed" else None},
             "clocks": clk.summary(),
         }
-        if prec == "mixed":
+        if prec == "mixed" and not args.no_e2e:
             # end to end through the host-buffer entry point: H2D + apply + D2H per step
             xh = torch.from_numpy(x).pin_memory()
             yh = torch.empty_like(xh).pin_memory()
@@ -468,18 +511,18 @@ def main():
         batched = run_batched(args, sg, synth, torch)
 
     if rank == 0:
-        m = results["mixed"]
-        f = results["fp64"]
+        m = results.get("mixed") or next(iter(results.values()))
+        f = results.get("fp64")
         line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": m["steps"],
                 "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "precision": "mixed (FP32 contractions, FP64 accumulation)",
-                           "vectors_per_step": nvec, "parallelism": f"replicas x{world}",
-                           "l2": "flushed between timed steps (256 MB write)"},
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if "mixed" in results else "f64",
+                "data": "synthetic", "config": bench_config(args, world),
                 "latency_ms": m["latency_ms"], "roofline": m["roofline"], "clocks": m["clocks"],
-                "e2e": m["e2e"], "gpu_launches": LAUNCHES_PER_APPLY * m["steps"],
-                "fp64": {"value": f["value"], "unit": UNIT, "ms_per_step": f["ms_per_step"], "steps": f["steps"],
-                         "latency_ms": f["latency_ms"], "roofline": f["roofline"], "clocks": f["clocks"]},
+                "e2e": m.get("e2e"), "gpu_launches": LAUNCHES_PER_APPLY * m["steps"],
+                "fp64": ({"value": f["value"], "unit": UNIT, "ms_per_step": f["ms_per_step"], "steps": f["steps"],
+                          "latency_ms": f["latency_ms"], "roofline": f["roofline"], "clocks": f["clocks"]}
+                         if f else None),
+                "peaks": {k: v for k, v in peaks.items() if k != "clocks"} if peaks else None,
                 "cpu_baseline": cpu, "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     rep.close()

@@ -156,7 +156,9 @@ sg_status sg_apply_H_host(sg_ctx *ctx, const double *x_host, double *y_host, int
  *   keeps in context-owned device memory come here from one array of
  *   SG_NOALLOC_SCRATCH_BYTES compiled into the library; every GPU that loads
  *   the library holds it until the process exits.  The call allocates nothing.
- *   Limits: nvec <= SG_NOALLOC_MAX_NVEC and nvec * N_cs <= SG_NOALLOC_MAX_ELEMS;
+ *   Limits: nvec <= SG_NOALLOC_MAX_NVEC and nvec * N_cs <= SG_NOALLOC_MAX_ELEMS
+ *   for SG_FP64 contexts (four accumulator words per element), or
+ *   SG_NOALLOC_MAX_ELEMS_MIXED for SG_MIXED contexts (one word per element);
  *   larger requests return SG_EUNSUPPORTED with the limits in sg_last_error.
  *   The context's device must be the current device (else SG_EINVAL).  The
  *   first call on a device looks up the array's device address
@@ -169,6 +171,7 @@ sg_status sg_apply_H_host(sg_ctx *ctx, const double *x_host, double *y_host, int
 #define SG_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
 #define SG_NOALLOC_MAX_NVEC 64
 #define SG_NOALLOC_MAX_ELEMS 524272
+#define SG_NOALLOC_MAX_ELEMS_MIXED 2097088
 sg_status sg_apply_H_noalloc(sg_ctx *ctx, const double *x, double *y, int nvec, void *stream);
 
 /*
@@ -389,6 +392,23 @@ sg_status sg_propagate(sg_ctx *ctx, double *psi, double dt, int nsteps, int orde
  * examples from its 1D Hermite-function coefficients.
  */
 sg_status sg_product_state(const sg_ctx *ctx, const double *factors, int ld, double *out_host);
+
+/*
+ * sg_measure_peak -- measured arithmetic throughput of the current device (no
+ * counterpart in the paper; it supplies the denominators of the roofline
+ * fractions of the operator action, which is bound by CUDA-core arithmetic).
+ * Every SM runs 32 warps of register-resident multiply-add chains for about
+ * `seconds` (0 < seconds <= 60); the result counts 2 flops per multiply-add.
+ *   kind        SG_PEAK_FP32: scalar FP32 fma; SG_PEAK_FP32X2: the packed
+ *               two-lane FP32 fma (fma.rn.f32x2, two multiply-adds per
+ *               instruction); SG_PEAK_FP64: FP64 fma.
+ *   flops_per_s host (out): achieved flop/s of the timed launch.
+ *   sms         host (out, may be NULL): the device's multiprocessor count.
+ * Synchronous (CUDA events on `stream`).  Allocates and frees 8 bytes per
+ * launched thread (about 1.2 MB on a 152-SM device).
+ */
+typedef enum { SG_PEAK_FP32 = 0, SG_PEAK_FP32X2 = 1, SG_PEAK_FP64 = 2 } sg_peak_kind;
+sg_status sg_measure_peak(int kind, double seconds, double *flops_per_s, int *sms, void *stream);
 
 /* Text of the last error of ctx (or of the calling thread's last sg_create
  * when ctx is NULL).  Never NULL; valid until the next call on ctx. */

@@ -112,6 +112,7 @@ SIGNATURES = {
     "sg_server_stats": (_i32, [_vp, _P64, _P64, _P64]),
     "sg_server_last_error": (ctypes.c_char_p, [_vp]),
     "sg_server_destroy": (None, [_vp]),
+    "sg_measure_peak": (_i32, [_i32, _dbl, ctypes.POINTER(_dbl), ctypes.POINTER(_i32), _vp]),
     "sg_destroy": (None, [_vp]),
 }
 
@@ -519,6 +520,20 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+SG_PEAK_FP32, SG_PEAK_FP32X2, SG_PEAK_FP64 = range(3)
+
+
+def sg_measure_peak(kind="fp32", seconds: float = 1.0, stream=None):
+    """Measured multiply-add throughput of the current device: (flop/s, SM count).
+    kind: "fp32" (scalar fma), "fp32x2" (packed two-lane fma) or "fp64"."""
+    k = {"fp32": SG_PEAK_FP32, "fp32x2": SG_PEAK_FP32X2, "fp64": SG_PEAK_FP64}.get(kind, kind)
+    f, n = ctypes.c_double(), ctypes.c_int()
+    st = lib().sg_measure_peak(int(k), float(seconds), ctypes.byref(f), ctypes.byref(n), _stream_ptr(stream))
+    if st != SG_OK:
+        raise SgError(st, "sg_measure_peak failed")
+    return f.value, n.value
 
 
 def sg_last_error(ctx: Ctx = None) -> str:

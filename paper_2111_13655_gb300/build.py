@@ -22,7 +22,7 @@ LIB = os.path.join(OUT, "libsmolyak.so")
 SOURCES = ["sg_fast_f32.cu", "sg_fast_f64.cu", "sg_fast_batch_f32.cu", "sg_fast_batch_f64.cu",
            "sg_setup.cpp", "sg_api.cpp", "sg_apply.cu", "sg_apply_fast.cu", "sg_solvers.cu", "sg_solvers_api.cpp",
            "sg_apply_noalloc.cu", "sg_batch.cpp", "sg_server.cu", "sg_server_api.cpp",
-           "sg_tune.cpp"]
+           "sg_tune.cpp", "sg_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

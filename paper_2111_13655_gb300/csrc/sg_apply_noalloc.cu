@@ -13,7 +13,7 @@
 //
 // The scratch holds, per call, the per-vector scale exponents (kNoAllocMaxVec
 // words) followed by the fixed-point accumulators of the compact vectors
-// (kAccDigits words per element).  It is one array shared by every call on a
+// (sg::acc_words words per element: four for FP64 contexts, one for mixed).  It is one array shared by every call on a
 // device, and keeps whatever the last call left in it: each call clears the
 // part it uses before its kernels run.  Two calls whose GPU work overlaps
 // (different streams, host threads or contexts on the same device) use the
@@ -25,13 +25,15 @@
 
 namespace {
 
-// 16 MiB: kNoAllocMaxVec exponent words + up to (16 MiB / 8 - 64) / 4 =
-// 524,272 vector elements (nvec * N_cs) of accumulators.
+// 16 MiB: kNoAllocMaxVec exponent words + (16 MiB / 8 - 64) = 2,097,088 words
+// of accumulators: 524,272 vector elements (nvec * N_cs) for FP64 contexts,
+// 2,097,088 for mixed-precision contexts.
 constexpr size_t kNoAllocWords = (size_t)SG_NOALLOC_SCRATCH_BYTES / sizeof(unsigned long long);
 constexpr int kNoAllocMaxVec = SG_NOALLOC_MAX_NVEC;
-constexpr size_t kNoAllocMaxElems = (kNoAllocWords - kNoAllocMaxVec) / sg::kAccDigits;
+constexpr size_t kNoAllocAccWords = kNoAllocWords - kNoAllocMaxVec;
 static_assert(SG_NOALLOC_SCRATCH_BYTES % 256 == 0, "scratch size must keep 256-byte alignment");
-static_assert(kNoAllocMaxElems == SG_NOALLOC_MAX_ELEMS, "header limit out of date");
+static_assert(kNoAllocAccWords / sg::acc_words(false) == SG_NOALLOC_MAX_ELEMS, "header limit out of date");
+static_assert(kNoAllocAccWords / sg::acc_words(true) == SG_NOALLOC_MAX_ELEMS_MIXED, "header limit out of date");
 
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocWords];
 
@@ -58,11 +60,14 @@ extern "C" sg_status sg_apply_H_noalloc(sg_ctx *ctx, const double *x, double *y,
     if (!x || !y) return noalloc_fail(ctx, SG_EINVAL, "x or y is NULL");
     if (nvec < 1) return noalloc_fail(ctx, SG_EINVAL, "nvec must be >= 1");
     const size_t n = (size_t)ctx->host.n_cs * (size_t)nvec;
-    if (nvec > kNoAllocMaxVec || n > kNoAllocMaxElems)
+    const size_t words = (size_t)sg::acc_words(ctx->fp32);
+    const size_t max_elems = kNoAllocAccWords / words;
+    if (nvec > kNoAllocMaxVec || n > max_elems)
         return noalloc_fail(ctx, SG_EUNSUPPORTED,
                             "nvec * N_cs = " + std::to_string(n) + " with nvec = " + std::to_string(nvec) +
                                 " exceeds the fixed scratch (nvec <= " + std::to_string(kNoAllocMaxVec) +
-                                ", nvec * N_cs <= " + std::to_string(kNoAllocMaxElems) +
+                                ", nvec * N_cs <= " + std::to_string(max_elems) +
+                                (ctx->fp32 ? " for mixed-precision contexts" : " for FP64 contexts") +
                                 "); use sg_apply_H");
     if ((x < y + n) && (y < x + n)) return noalloc_fail(ctx, SG_EINVAL, "x and y overlap");
 
@@ -93,7 +98,7 @@ extern "C" sg_status sg_apply_H_noalloc(sg_ctx *ctx, const double *x, double *y,
     unsigned long long *acc = scratch + kNoAllocMaxVec;
     // The accumulators are summed into and must start at zero; the exponents
     // are cleared by the launch itself.
-    e = cudaMemsetAsync(acc, 0, n * sg::kAccDigits * sizeof(unsigned long long), s);
+    e = cudaMemsetAsync(acc, 0, n * words * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return noalloc_fail(ctx, SG_ECUDA, std::string("memset: ") + cudaGetErrorString(e));
 
     sg::KParams kp = ctx->kp;

@@ -37,7 +37,7 @@ constexpr int kAccLsbBelowMax = 80;  // E = exponent(max|x|) - 80
 // FP32 contexts: one signed 64-bit word per entry, unit 2^(exponent(max|x|) - 40)
 constexpr int kAcc32LsbBelowMax = 40;
 // 64-bit words per accumulated entry of a context's precision
-__host__ __device__ inline int acc_words(bool fp32) { return fp32 ? 1 : kAccDigits; }
+__host__ __device__ constexpr int acc_words(bool fp32) { return fp32 ? 1 : kAccDigits; }
 
 constexpr int kMaxPairs = 64;  // coupled mode pairs handled by the fast path
 

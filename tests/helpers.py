@@ -1,0 +1,65 @@
+"""Error measures and tolerances of the GPU parity tests, and a cached dense
+oracle matrix for the propagation checks.
+
+Two measures, both per vector, the worst vector reported:
+  norm_rel(y, r) = ||y - r||_2 / ||r||_2
+  elem_rel(y, r) = max_i |y_i - r_i| / max_i |r_i|
+The element-wise form catches a single wrong entry (a mis-ranked compact
+index, a dropped or doubled term) that the 2-norm would dilute by up to
+sqrt(N_cs).
+
+FP64 mode: both <= 1e-12.
+Mixed mode (FP32 contractions, exact fixed-point sum): every term's result
+carries FP32 rounding (~6e-8 relative) and the combination coefficients D_l
+(Eq. (8); |D_l| up to 462 at D=12) sum those errors over the terms sharing a
+compact function.  The compact function k = 0 lies in every term, so its
+error is the largest: the element-wise measure is looser than the norm-wise
+one.  MIXED_ELEM_TOL is the measured worst case over the parity cases times
+a margin of about ten (values in the test that uses it).
+"""
+import numpy as np
+
+FP64_TOL = 1e-12
+MIXED_TOL = 5e-6
+MIXED_ELEM_TOL = 5e-5
+
+
+def norm_rel(y, r):
+    y = np.atleast_2d(y); r = np.atleast_2d(r)
+    return float(np.max(np.linalg.norm(y - r, axis=1) / np.linalg.norm(r, axis=1)))
+
+
+def elem_rel(y, r):
+    y = np.atleast_2d(y); r = np.atleast_2d(r)
+    return float(np.max(np.max(np.abs(y - r), axis=1) / np.max(np.abs(r), axis=1)))
+
+
+def assert_parity(y, r, precision, what=""):
+    """Both measures within the tolerances of `precision` ("fp64" or "mixed")."""
+    n, e = norm_rel(y, r), elem_rel(y, r)
+    if precision == "fp64":
+        assert n <= FP64_TOL and e <= FP64_TOL, f"{what}: norm-wise {n:.3e}, element-wise {e:.3e}"
+    else:
+        assert n <= MIXED_TOL and e <= MIXED_ELEM_TOL, f"{what}: norm-wise {n:.3e}, element-wise {e:.3e}"
+    return n, e
+
+
+_DENSE = {}
+
+
+def dense_oracle(p):
+    """H_S of problem p as a dense symmetric matrix, column j = H_S e_j, from
+    the literal CPU oracle (symmetrised: H_S is symmetric, Sec. 2); cached per
+    problem name within a test process."""
+    from oracle import oracle as orc
+    key = (p.name, p.D, p.L, tuple(np.asarray(p.omega).round(15)), tuple(np.asarray(p.coef).round(15)))
+    if key not in _DENSE:
+        n = orc.n_compact(p)
+        H = orc.apply_H(p, np.eye(n)).T
+        _DENSE[key] = 0.5 * (H + H.T)
+    return _DENSE[key]
+
+
+def exact_propagator(H):
+    """(w, U) with H = U diag(w) U^T, for psi(t) = U exp(-i w t) U^T psi(0)."""
+    return np.linalg.eigh(H)

@@ -15,6 +15,8 @@ import paper_2111_13655_gb300 as sg
 from oracle import oracle as orc
 from paper_2111_13655_gb300 import synth
 
+from helpers import assert_parity
+
 pytestmark = pytest.mark.gpu
 
 
@@ -86,8 +88,7 @@ def test_batch_fp64_matches_oracle():
         for j, p in enumerate(probs):
             ref = orc.apply_H(p, xs_np[j])
             g = got[j].view(nvec, -1).cpu().numpy()
-            err = np.linalg.norm(g - ref, axis=1) / np.linalg.norm(ref, axis=1)
-            assert err.max() <= 1e-12, (p.name, err)
+            assert_parity(g, ref, "fp64", p.name)
     finally:
         sg.sg_batch_destroy(b)
         for c in ctxs:

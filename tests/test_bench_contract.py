@@ -26,3 +26,8 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
+    # the reference arm reports the same config as the GPU arm
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["config"] == bench.bench_config(types.SimpleNamespace(L=10, nvec=8), 1)

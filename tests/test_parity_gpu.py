@@ -1,9 +1,10 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
-FP64 mode: norm-wise relative error <= 1e-12 per vector against the literal
-oracle (Alg. 1) or the masked-Galerkin closed form where it is exact.
-Mixed mode (FP32 contractions, FP64 accumulation): a bound derived from FP32
-rounding, see MIXED_TOL.  Index maps: bit-exact.  The compress-add is an exact
+FP64 mode: relative error <= 1e-12 per vector, both norm-wise and element by
+element (max_i |y_i - y_ref,i| / max_i |y_ref,i|), against the literal oracle
+(Alg. 1) or the masked-Galerkin closed form where it is exact.
+Mixed mode (FP32 contractions, FP64 accumulation): tolerances from FP32
+rounding (tests/helpers.py).  Index maps: bit-exact.  The compress-add is an exact
 fixed-point sum, so results are bitwise reproducible: batched vs single
 vectors, host vs device entry, and power-of-two scalings are compared exactly.
 """
@@ -17,19 +18,13 @@ from oracle import galerkin
 from oracle import oracle as orc
 from paper_2111_13655_gb300 import synth
 
+from helpers import FP64_TOL, assert_parity, elem_rel, norm_rel
+
 pytestmark = pytest.mark.gpu
 
-FP64_TOL = 1e-12
-# FP32 contractions: each term's result carries ~6e-8 relative error; the
-# combination coefficients (|D_l| up to 462 at D=12) amplify it in a random
-# walk over the ~200 terms sharing a compact function.  D=12 L=10 shows 5e-7;
-# 5e-6 keeps a factor 10 of margin.
-MIXED_TOL = 5e-6
-
-
-def rel_per_vector(a, b):
-    a = np.atleast_2d(a); b = np.atleast_2d(b)
-    return float(np.max(np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)))
+# Mixed mode at D=12 L=10, element-wise: the compact functions of small k lie
+# in most of the 646,646 terms and collect their FP32 rounding.
+C3_MIXED_ELEM_TOL = 1e-3
 
 
 def gpu_apply(p, x, precision="fp64", nvec=None):
@@ -71,7 +66,7 @@ def test_fp64_matches_literal_oracle(name):
     x = synth.random_vectors(n, nvec, 1234)
     y_ref = orc.apply_H(p, x)
     y = gpu_apply(p, x, "fp64")
-    assert rel_per_vector(y, y_ref) <= FP64_TOL
+    assert_parity(y, y_ref, "fp64", name)
 
 
 @pytest.mark.parametrize("name", ["C1 D=2 L=6 nq=l+1", "C2 D=6 L=8 nq=l+1", "D=12 L=5 nq=l+2",
@@ -82,7 +77,8 @@ def test_mixed_matches_literal_oracle(name):
     x = synth.random_vectors(n, nvec, 99)
     y_ref = orc.apply_H(p, x)
     y = gpu_apply(p, x, "mixed")
-    assert rel_per_vector(y, y_ref) <= MIXED_TOL
+    n, e = assert_parity(y, y_ref, "mixed", name)
+    print(f"mixed {name}: norm-wise {n:.3e}, element-wise {e:.3e}")
 
 
 def test_fp64_c3_full_size_matches_masked_galerkin():
@@ -93,15 +89,21 @@ def test_fp64_c3_full_size_matches_masked_galerkin():
     x = synth.random_vectors(n, 1, 7)
     y_ref = galerkin.apply_H(p, x)
     y = gpu_apply(p, x, "fp64")
-    assert rel_per_vector(y, y_ref) <= FP64_TOL
+    assert_parity(y, y_ref, "fp64", "D=12 L=10")
 
 
 def test_mixed_c3_full_size_matches_masked_galerkin():
+    """Mixed precision at full size.  The element-wise error is dominated by
+    the compact functions of small k, which lie in most of the 646,646 terms
+    (|D_l| up to 462): it is held to a bound of its own, 10x the measured."""
     p = synth.workload_C3()
     x = synth.random_vectors(646646, 1, 8)
     y_ref = galerkin.apply_H(p, x)
     y = gpu_apply(p, x, "mixed")
-    assert rel_per_vector(y, y_ref) <= MIXED_TOL
+    n, e = norm_rel(y, y_ref), elem_rel(y, y_ref)
+    print(f"mixed D=12 L=10: norm-wise {n:.3e}, element-wise {e:.3e}")
+    assert n <= 5e-6
+    assert e <= C3_MIXED_ELEM_TOL
 
 
 def test_uncoupled_spectrum_c3_shape():
@@ -112,7 +114,7 @@ def test_uncoupled_spectrum_c3_shape():
     x = synth.random_vectors(K.shape[0], 1, 3)
     y = gpu_apply(p, x, "fp64")
     E = (K + 0.5) @ om
-    assert rel_per_vector(y, E[None, :] * x) <= FP64_TOL
+    assert_parity(y, E[None, :] * x, "fp64", "lambda=0 D=12 L=10")
 
 
 def test_host_buffer_entry_matches_device_entry():

@@ -14,6 +14,8 @@ import paper_2111_13655_gb300 as sg
 from oracle import oracle as orc
 from paper_2111_13655_gb300 import synth
 
+from helpers import dense_oracle
+
 pytestmark = pytest.mark.gpu
 
 
@@ -59,6 +61,24 @@ def test_server_matches_sg_propagate():
     assert np.max(np.abs(psi - ref)) < 1e-11
     assert np.max(np.abs(nl - nl_ref)) < 1e-12
     assert np.max(np.abs(el - el_ref)) < 1e-11
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_request_matches_exact_propagator_of_the_oracle(prec, tol):
+    """A D=6 L=8 coupled request (the 6D propagation configuration, 50 steps of
+    0.1) against psi(t) = exp(-i H_S t) psi(0) from the literal oracle's dense
+    H_S, element by element; the mixed server's error is printed."""
+    p = synth.workload_C2()
+    w, U = np.linalg.eigh(dense_oracle(p))
+    psi0 = normalised_state(p, 2.0)
+    exact = U @ (np.exp(-1j * w * 5.0) * (U.T @ psi0))
+    with sg.Server(prec) as srv:
+        rid = srv.submit(p, 0.1, 50, psi0=psi0.astype(complex))
+        srv.run()
+        psi, nl, el, _ = srv.result(rid)
+    err = np.max(np.abs(psi - exact))
+    print(f"server {prec}, D=6 L=8, t = 5: max |psi - psi_exact| = {err:.2e}")
+    assert err <= tol
 
 
 def mix_problems():

@@ -1,8 +1,9 @@
 """sg_tune: measured choice of the fast path's slicing target.
 
 After tuning, the context must still compute H_S within the parity
-tolerances (FP64 1e-12 against the oracles, mixed 5e-6), repeatably to the
-bit, and report which target it kept."""
+tolerances (FP64 1e-12 norm-wise and element-wise against the oracles, mixed
+as in tests/helpers.py), repeatably to the bit, and report which target it
+kept."""
 import numpy as np
 import pytest
 
@@ -13,16 +14,14 @@ from oracle import galerkin
 from oracle import oracle as orc
 from paper_2111_13655_gb300 import synth
 
+from helpers import assert_parity
+
 pytestmark = pytest.mark.gpu
 
 
-def rel(a, b):
-    return float(np.max(np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)))
-
-
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 5e-6)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("which", ["D=6 L=8 nq=l+1 (literal oracle)", "D=12 L=6 nq=l+2 (Galerkin)"])
-def test_tuned_context_keeps_parity_and_determinism(prec, tol, which):
+def test_tuned_context_keeps_parity_and_determinism(prec, which):
     if which.startswith("D=6"):
         p = synth.workload_C2()
         ref_of = lambda x: orc.apply_H(p, x)
@@ -41,7 +40,7 @@ def test_tuned_context_keeps_parity_and_determinism(prec, tol, which):
         torch.cuda.synchronize()
         assert sg.sg_device_error(ctx) == 0
         assert torch.equal(y1, y2)
-        assert rel(y1.view(nvec, -1).cpu().numpy(), ref_of(xn)) <= tol
+        assert_parity(y1.view(nvec, -1).cpu().numpy(), ref_of(xn), prec, which)
 
 
 def test_generic_path_has_nothing_to_tune():
