@@ -46,34 +46,50 @@ FP32_LANES_PER_SM = 128
 LAUNCHES_PER_APPLY = 4
 
 
-def algorithmic_flops_per_vector(levels: np.ndarray, nbA=1, nbB=1, nqA=2, nqB=1) -> int:
-    """FLOPs of one real-vector apply by the route the kernel takes: per term,
-    forward and backward one-mode contractions over the modes with nb > 1
-    (2 flops per multiply-add), the kinetic matrices in the basis, one multiply
-    per grid point for the potential, and the weighted compress-add.  The
-    forward chain takes the modes in the kernel's order: ascending
-    1/nb - 1/nq (for nb = l+1, nq = l+2: higher levels first), ties in mode
-    order; the backward chain mirrors it."""
-    l = levels.astype(np.int64)
-    nb0 = nbA + nbB * l
-    nq0 = nqA + nqB * l
-    key = np.where(nb0 > 1, 1.0 / nb0 - 1.0 / nq0, np.inf)
-    l = np.take_along_axis(l, np.argsort(key, axis=1, kind="stable"), axis=1)
-    nb = nbA + nbB * l
-    nq = nqA + nqB * l
-    act = nb > 1
-    a = np.where(act, nb, 1)
-    g = np.where(act, nq, 1)
-    # prefix product of g over j < i, suffix product of a over j > i
-    pre = np.cumprod(np.concatenate([np.ones((l.shape[0], 1), np.int64), g[:, :-1]], axis=1), axis=1)
-    suf = np.ones_like(a)
-    for i in range(l.shape[1] - 2, -1, -1):
-        suf[:, i] = suf[:, i + 1] * a[:, i + 1]
-    fwd = (np.where(act, a * g, 0) * pre * suf).sum(axis=1)
-    NB = a.prod(axis=1)
-    NG = g.prod(axis=1)
-    kin = NB * np.where(act, a, 0).sum(axis=1)
-    return int((2 * (2 * fwd + kin) + NG + 2 * NB).sum())
+def algorithmic_flops_per_vector(levels: np.ndarray, nbA=1, nbB=1, nqA=2, nqB=1, rmax=None) -> int:
+    """FLOPs of one real-vector apply of the chained Henon-Heiles operator by
+    the route the fast kernel takes, 2 flops per multiply-add.  Per term:
+      - a term has a grid when two neighbouring modes (a coupled pair) both
+        have nb > 1; then its last `rmax` level-1 modes (mode order) are inner
+        positions (rmax = 3 for nb(1) = 2, 2 for nb(1) = 3, else 0);
+      - forward one-mode contractions over the other (outer) modes with
+        nb > 1, in the planned order (ascending 1/nb - 1/nq, ties in mode
+        order), each on NBI = prod(inner nb) values per site, and the mirrored
+        backward chain (the same count);
+      - at every outer grid point the NBI x NBI inner block;
+      - the single-mode matrices of the outer modes (and the constant c0 of a
+        term without a grid), one multiply-add per basis entry and function;
+      - the weighted compress-add, 2 flops per basis entry."""
+    l = np.asarray(levels).astype(np.int64)
+    n_t, D = l.shape
+    nb_all = nbA + nbB * l
+    nq_all = nqA + nqB * l
+    act = nb_all > 1
+    if rmax is None:
+        rmax = 3 if nbA + nbB == 2 else 2 if nbA + nbB == 3 else 0
+    grid = (act[:, :-1] & act[:, 1:]).any(axis=1) if D > 1 else np.zeros(n_t, bool)
+    l1 = (l == 1) & act
+    # rank of each level-1 mode counted from the last mode: inner if <= R
+    from_right = np.cumsum(l1[:, ::-1], axis=1)[:, ::-1]
+    inner = l1 & (from_right <= rmax) & grid[:, None]
+    outer = act & ~inner
+    NBI = np.where(inner, nb_all, 1).prod(axis=1)
+    key = np.where(outer, 1.0 / nb_all - 1.0 / nq_all, np.inf)
+    idx = np.argsort(key, axis=1, kind="stable")
+    ob = np.take_along_axis(np.where(outer, nb_all, 1), idx, axis=1)
+    oq = np.take_along_axis(np.where(outer, nq_all, 1), idx, axis=1)
+    om = np.take_along_axis(outer, idx, axis=1)
+    # prefix product of nq over earlier outer positions, suffix product of nb over later ones
+    pre = np.cumprod(np.concatenate([np.ones((n_t, 1), np.int64), oq[:, :-1]], axis=1), axis=1)
+    suf = np.ones_like(ob)
+    for i in range(D - 2, -1, -1):
+        suf[:, i] = suf[:, i + 1] * ob[:, i + 1]
+    fwd = (np.where(om, ob * oq, 0) * pre * suf).sum(axis=1) * NBI
+    NB = np.where(act, nb_all, 1).prod(axis=1)
+    NGo = oq.prod(axis=1)
+    reg = np.where(grid, NGo * NBI * NBI, 0)
+    basis = NB * (np.where(outer, nb_all, 0).sum(axis=1) + np.where(grid, 0, 1))
+    return int((2 * (2 * fwd + reg + basis) + 2 * NB).sum())
 
 
 class ClockSampler:

@@ -228,7 +228,7 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
                     (st = upload(ctx, T.fdesc, &kp.fast.desc)) != SG_OK ||
                     (st = upload(ctx, T.fdesc_off, &kp.fast.desc_off)) != SG_OK ||
                     (st = upload(ctx, T.fimg_off, &kp.fast.img_off)) != SG_OK ||
-                    (st = upload(ctx, T.fvt_off, &kp.fast.vt_off)) != SG_OK ||
+                    (st = upload(ctx, T.fvt_off, &kp.fast.mt_off)) != SG_OK ||
                     (ctx->fp32 ? (st = upload(ctx, std::vector<float>(T.fimg.begin(), T.fimg.end()),
                                               &kp.fast.imgf)) != SG_OK
                                : (st = upload(ctx, T.fimg, &kp.fast.imgd)) != SG_OK)))) {
@@ -243,7 +243,6 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
         kp.fast.enabled = 1;
         kp.fast.nb1 = T.nb1;
         kp.fast.nq1 = T.nq1;
-        kp.fast.uni1 = T.uni1;
         kp.fast.npairs = (int)T.pair_modes.size() / 2;
         kp.fast.c0const = T.c0const;
         kp.fast.desccap = T.fdesccap;
@@ -266,23 +265,23 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
         ctx->allocations.push_back(rp);
         ctx->bytes_device += (int64_t)T.franks * (int64_t)sizeof(int);
         kp.fast.ranks = static_cast<const int *>(rp);
-        // the coupling potential on every term's grid, in the context's precision
+        // the inner-block tables of every term with a grid, in the context's precision
         void *vp = nullptr;
         const size_t nvt = std::max<size_t>(1, (size_t)T.fvt_off.back());
         // 16 bytes of padding: the term kernel prefetches 16-byte rounded ranges
         e = cudaMalloc(&vp, nvt * (ctx->fp32 ? sizeof(float) : sizeof(double)) + 16);
         if (e != cudaSuccess) {
-            st = fail(nullptr, SG_ENOMEM, std::string("cudaMalloc (potential tables): ") + cudaGetErrorString(e));
+            st = fail(nullptr, SG_ENOMEM, std::string("cudaMalloc (inner-block tables): ") + cudaGetErrorString(e));
             free_all(ctx);
             delete ctx;
             return st;
         }
         ctx->allocations.push_back(vp);
         ctx->bytes_device += (int64_t)nvt * (ctx->fp32 ? 4 : 8);
-        if (ctx->fp32) kp.fast.vtabf = static_cast<const float *>(vp);
-        else kp.fast.vtabd = static_cast<const double *>(vp);
+        if (ctx->fp32) kp.fast.mtabf = static_cast<const float *>(vp);
+        else kp.fast.mtabd = static_cast<const double *>(vp);
         e = launch_build_ranks(kp, static_cast<int *>(rp), 0);
-        if (e == cudaSuccess) e = launch_build_vtab(kp, ctx->fp32, 0);
+        if (e == cudaSuccess) e = launch_build_mtab(kp, ctx->fp32, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e == cudaSuccess) {
             ctx->smem_bytes = fast_smem_bytes(kp, ctx->fp32);

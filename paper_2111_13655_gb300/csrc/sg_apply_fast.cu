@@ -1,13 +1,14 @@
-// Fast path of the Smolyak operator action: per-context set-up kernels and
-// the host entry points; the term kernels are in sg_fast.cuh, instantiated by
-// sg_fast_f32.cu and sg_fast_f64.cu.
+// Fast path of the Smolyak operator action: per-context set-up kernels (M^B,
+// the inner-block tables) and the host entry points; the term kernels are in
+// sg_fast.cuh, instantiated by sg_fast_f32.cu, sg_fast_f64.cu and the batch units.
 #include "sg_fast.cuh"
 
 namespace sg {
 
 namespace {
 
-// M^B in layout order: compact index of every basis function of every term
+// M^B in layout order: compact index of every basis function of every term,
+// element e = o * NBI + i (outer site o, inner index i) of the term's list
 // (built once per context; the same partial-rank arithmetic as the generic kernel).
 __global__ void __launch_bounds__(kFT) k_build_ranks(const KParams P, int *__restrict__ ranks)
 {
@@ -16,12 +17,12 @@ __global__ void __launch_bounds__(kFT) k_build_ranks(const KParams P, int *__res
     int4 *buf = reinterpret_cast<int4 *>(smraw);
     if (threadIdx.x < 32) {
         load_record(P, blockIdx.x, buf, H);
-        derive_layout(P, 1, 1 << 30, H);
+        derive_layout<float>(P, 1, 1 << 30, H);
     }
     __syncthreads();
-    const int m = H.m, R = H.R, NBo = H.NBo, Lp = P.L + 1;
+    const int m = H.m, R = H.R, NBI = H.NBI, Lp = P.L + 1;
     for (int e = threadIdx.x; e < H.NB; e += kFT) {
-        const int i = e / NBo, o = e - i * NBo;
+        const int o = e / NBI, i = e - o * NBI;
         int r = 0, s = 0;
         for (int a = 0; a < m; a++) {
             const int j = H.bymode[a];
@@ -36,59 +37,139 @@ __global__ void __launch_bounds__(kFT) k_build_ranks(const KParams P, int *__res
     }
 }
 
+__host__ __device__ constexpr int ipow(int b, int e) { return e <= 0 ? 1 : b * ipow(b, e - 1); }
 
-// The coupling potential V = sum_p G_p(u_a, u_b) on each term's collapsed grid,
-// once per context, in the order the term kernel's register phase reads it:
-// [slice][inner grid point gi][outer grid point g] (g fastest).  Digits: inner
-// positions from gi (first position slowest), sliced positions from the slice
-// (last fastest), the other outer positions from g.  G tables from the image.
-template <typename T>
-__global__ void __launch_bounds__(kFT) k_build_vtab(const KParams P, T *__restrict__ vt)
+// Inner-block table of one term with coupled pairs (FP64 arithmetic, stored in
+// T): for every slice and outer grid point g of the slice,
+//   M_g[r][c] = sum_{inner grid points u} V(g, u) prod_j w_{u_j} b_{r_j}(u_j) b_{c_j}(u_j)
+//             + sum_{inner j} H1_j[r_j][c_j] prod_{i != j} delta(r_i, c_i) + c0 delta(r, c),
+// V = sum over the term's active pairs of G_p (the two-mode monomials on the
+// pair's grid), H1_j = the single-mode matrix of inner position j with its
+// induced parts, c0 = the term's constant.  Indices r, c run over the inner
+// basis (first inner position slowest); M_g is stored as its upper triangle,
+// row by row, in units of `UE` elements: [slice][unit][g][UE].
+template <typename T, int NB1, int R>
+__device__ void build_mtab_term(const KParams &P, const FHdr &H, T *__restrict__ mt)
+{
+    constexpr int NBI = ipow(NB1, R), NE = NBI * (NBI + 1) / 2;
+    constexpr int U = vunit<T>(), UE = NBI == 1 ? 1 : U, NEU = (NE + UE - 1) / UE;
+    const int m = H.m, ps = R + H.s, NGs = H.NGs, nitems = H.nslice * NGs;
+    int NGI = 1;
+    for (int j = 0; j < R; j++) NGI *= H.nq[j];
+    const double *t1 = P.tabd, *ft = P.fast.tabd;
+    for (int it = threadIdx.x; it < nitems; it += kFT) {
+        const int sl = it / NGs, g = it - sl * NGs;
+        int u[kMaxD];
+        int rem = sl;
+        for (int j = ps - 1; j >= R; j--) { u[j] = rem % H.nq[j]; rem /= H.nq[j]; }
+        for (int j = ps; j < m; j++) u[j] = (g / H.gstride[j]) % H.nq[j];
+        double M[NE];
+#pragma unroll
+        for (int e = 0; e < NE; e++) M[e] = 0.0;
+        for (int gi = 0; gi < NGI; gi++) {
+            int r2 = gi;
+            for (int j = R - 1; j >= 0; j--) { u[j] = r2 % H.nq[j]; r2 /= H.nq[j]; }
+            double V = 0.0;
+            for (int q = 0; q < H.npair; q++) {
+                const int a = H.pa[q], b = H.pb[q];
+                V += ft[H.pgg[q] + u[a] * H.nq[b] + u[b]];
+            }
+            // w[r] = prod_j (B^T W)_j[r_j][u_j], b[c] = prod_j B_j[u_j][c_j]
+            double wv[NBI], bv[NBI];
+#pragma unroll
+            for (int r = 0; r < NBI; r++) {
+                double wp = V, bp = 1.0;
+                int rr = r;
+#pragma unroll
+                for (int j = R - 1; j >= 0; j--) {
+                    const int kj = rr % NB1;
+                    rr /= NB1;
+                    wp *= t1[H.gBW[j] + kj * H.nq[j] + u[j]];
+                    bp *= t1[H.gB[j] + u[j] * NB1 + kj];
+                }
+                wv[r] = wp; bv[r] = bp;
+            }
+#pragma unroll
+            for (int r = 0; r < NBI; r++)
+#pragma unroll
+                for (int c = r; c < NBI; c++) M[tri_index(r, c, NBI)] += wv[r] * bv[c];
+        }
+        // single-mode matrices of the inner positions (base + induced parts), and c0
+#pragma unroll
+        for (int j = 0; j < R; j++) {
+            const int st = ipow(NB1, R - 1 - j);
+#pragma unroll
+            for (int r = 0; r < NBI; r++)
+#pragma unroll
+                for (int c = r; c < NBI; c++) {
+                    const int rj = (r / st) % NB1, cj = (c / st) % NB1;
+                    if (r - rj * st != c - cj * st) continue;  // other inner digits differ
+                    double h = ft[H.gH1[j] + rj * NB1 + cj];
+                    for (int q = 0; q < H.nind; q++)
+                        if (H.ipos[q] == j) h += ft[H.ioffs[q] + rj * NB1 + cj];
+                    M[tri_index(r, c, NBI)] += h;
+                }
+        }
+#pragma unroll
+        for (int r = 0; r < NBI; r++) M[tri_index(r, r, NBI)] += H.c0;
+#pragma unroll
+        for (int q = 0; q < NEU; q++)
+#pragma unroll
+            for (int e = 0; e < UE; e++) {
+                const int idx = q * UE + e;
+                mt[((size_t)(sl * NEU + q) * NGs + g) * UE + e] = idx < NE ? (T)M[idx] : T(0);
+            }
+    }
+}
+
+template <typename T, int NB1>
+__global__ void __launch_bounds__(kFT) k_build_mtab(const KParams P, T *__restrict__ mt)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ FHdr H;
     const int p = blockIdx.x;
-    const long long v0 = P.fast.vt_off[p], nv = P.fast.vt_off[p + 1] - v0;
-    if (nv == 0) return;
+    const long long t0 = P.fast.mt_off[p];
+    if (P.fast.mt_off[p + 1] == t0) return;
     if (threadIdx.x < 32) {
         load_record(P, p, reinterpret_cast<int4 *>(smraw), H);
-        derive_layout(P, 1, 1 << 30, H);
+        derive_layout<T>(P, 1, 1 << 30, H);
     }
     __syncthreads();
-    const int m = H.m, R = H.R, s0 = R + H.s, NGs = H.NGs;
-    long long NGI = 1;
-    for (int j = 0; j < R; j++) NGI *= H.nq[j];
-    const T *G = FTab<T>::img(P) + P.fast.img_off[p] + H.matsz;
-    for (long long e = threadIdx.x; e < nv; e += kFT) {
-        const long long per_slice = NGI * NGs;
-        const int sl = (int)(e / per_slice);
-        const long long r1 = e - (long long)sl * per_slice;
-        const int gi = (int)(r1 / NGs), g = (int)(r1 - (long long)gi * NGs);
-        int u[kMaxD];
-        int rem = gi;
-        for (int j = R - 1; j >= 0; j--) { u[j] = rem % H.nq[j]; rem /= H.nq[j]; }
-        rem = sl;
-        for (int j = s0 - 1; j >= R; j--) { u[j] = rem % H.nq[j]; rem /= H.nq[j]; }
-        for (int j = s0; j < m; j++) u[j] = (g / H.gstride[j]) % H.nq[j];
-        T v = T(0);
-        for (int q = 0; q < H.npair; q++) {
-            const int a = H.pa[q], b = H.pb[q];
-            v += G[H.pg[q] + u[a] * H.nq[b] + u[b]];
-        }
-        vt[v0 + e] = v;
+    if (H.bad) return;
+    T *out = mt + t0;
+    switch (H.R) {
+        case 0: build_mtab_term<T, NB1, 0>(P, H, out); return;
+        case 1: if constexpr (NB1 > 1) build_mtab_term<T, NB1, 1>(P, H, out); return;
+        case 2: if constexpr (NB1 > 1) build_mtab_term<T, NB1, 2>(P, H, out); return;
+        case 3: if constexpr (NB1 == 2) build_mtab_term<T, NB1, 3>(P, H, out); return;
+        default: if (threadIdx.x == 0 && P.err) atomicCAS(P.err, 0, 113); return;
     }
 }
 
 }  // namespace
 
-cudaError_t launch_build_vtab(const KParams &kp, bool fp32, cudaStream_t stream)
+cudaError_t launch_build_mtab(const KParams &kp, bool fp32, cudaStream_t stream)
 {
     if (kp.n_terms == 0) return cudaSuccess;
     const size_t smem = 16 * (size_t)kp.fast.desccap;
-    if (fp32)
-        k_build_vtab<float><<<(unsigned)kp.n_terms, kFT, smem, stream>>>(kp, const_cast<float *>(kp.fast.vtabf));
-    else
-        k_build_vtab<double><<<(unsigned)kp.n_terms, kFT, smem, stream>>>(kp, const_cast<double *>(kp.fast.vtabd));
+    const unsigned nb = (unsigned)kp.n_terms;
+    float *mf = const_cast<float *>(kp.fast.mtabf);
+    double *md = const_cast<double *>(kp.fast.mtabd);
+    // inner positions are level-1 modes of a uniform size nb1 (2 or 3); none otherwise
+    switch (fast_inner_nb(kp.fast.nb1)) {
+        case 2:
+            if (fp32) k_build_mtab<float, 2><<<nb, kFT, smem, stream>>>(kp, mf);
+            else k_build_mtab<double, 2><<<nb, kFT, smem, stream>>>(kp, md);
+            break;
+        case 3:
+            if (fp32) k_build_mtab<float, 3><<<nb, kFT, smem, stream>>>(kp, mf);
+            else k_build_mtab<double, 3><<<nb, kFT, smem, stream>>>(kp, md);
+            break;
+        default:
+            if (fp32) k_build_mtab<float, 1><<<nb, kFT, smem, stream>>>(kp, mf);
+            else k_build_mtab<double, 1><<<nb, kFT, smem, stream>>>(kp, md);
+            break;
+    }
     return cudaGetLastError();
 }
 

@@ -95,11 +95,11 @@ extern "C" sg_status sg_batch_create(sg_ctx *const *ctxs, int n, sg_batch **out)
         kps[j].acc = nullptr;  // the batch kernels take the batch's accumulators explicitly
     }
 
-    // problems of one fast-kernel variant share a launch
-    std::map<std::tuple<int, int, int>, std::vector<int>> by_variant;
+    // every fast-path problem (of the batch's one precision) shares the launches
+    std::map<int, std::vector<int>> by_variant;
     for (int j = 0; j < n; j++) {
         const sg::KParams &kp = ctxs[j]->kp;
-        if (kp.fast.enabled) by_variant[{kp.fast.nb1, kp.fast.nq1, kp.fast.uni1}].push_back(j);
+        if (kp.fast.enabled) by_variant[0].push_back(j);
         else b->generic.push_back(j);
     }
     sg_status st;

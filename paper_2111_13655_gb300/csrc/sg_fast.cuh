@@ -1,27 +1,40 @@
 // Device code of the fast path of the Smolyak operator action (sm_103a):
 // potentials whose monomials touch at most two modes (the Henon-Heiles family
 // of Sec. 4, Eq. (18)).  Included by the units that instantiate it:
-// sg_fast_f32.cu / sg_fast_f64.cu (one problem per launch) and
-// sg_fast_batch_f32.cu / sg_fast_batch_f64.cu (many problems per launch).
+// sg_fast_f32.cu / sg_fast_f64.cu (one problem per launch),
+// sg_fast_batch_f32.cu / sg_fast_batch_f64.cu (many problems per launch) and
+// sg_apply_fast.cu (the per-context set-up kernels).
 //
 // One thread block (or, for small terms, one warp) per Smolyak term, terms
-// ordered most-expensive first.  The term operator (Alg. 1 of arXiv
-// 2111.13655 with the grid operator split as described in build_fast_tables) is
-//     y_l = c0 x_l + sum_j H1_j x_l + (x B^T W) diag(V_l) (x B) x_l,
+// ordered most-expensive first.  With the grid operator split as described in
+// build_fast_tables, the term operator of Alg. 1 is
+//     y_l = c0 x_l + sum_j H1_j x_l + (x_j B_j^T W_j) diag(V_l) (x_j B_j) x_l,
 // V_l(u) = sum over the term's active coupled pairs of G_p(u_a, u_b).
-// The basis->grid (Eq. (15)) and grid->basis (Eq. (14)) transfers run mode by
-// mode.
 //
-// Layout of a term tensor: [i][v][o] -- i runs over the "inner" slots (up to
-// RMAX slots of level 1, the slowest positions), v over a chunk of vectors,
-// o over the "outer" slots in mode order (last fastest).  Outer slots are
-// contracted breadth-first in shared memory with the 1D matrix in registers,
-// one (fibre, vector) per thread; the inner slots, the potential and their
-// back-transfer run in registers, one outer grid point per thread, the
-// potential evaluated once for all vectors of the chunk.  Vectors are batched
-// inside every phase, so block-wide barriers are shared by the whole chunk.
-// The compress-add of D_l * y_l into the compact result is the exact
-// fixed-point sum of sg_fixed.cuh.
+// Positions of a term: the transformed modes (nb > 1).  Up to three level-1
+// modes are "inner" positions, the others "outer".  The basis -> grid
+// (Eq. (15)) and grid -> basis (Eq. (14)) transfers of the outer positions
+// run mode by mode in shared memory.  The inner positions never go to the
+// grid in the term kernel: at every outer grid point g their whole action,
+//     M_g = (x_in B^T W) diag(V_l(g, .)) (x_in B) + c0 I + sum_{j inner} H1_j,
+// an NBI x NBI symmetric matrix (NBI = product of the inner sizes), is the
+// same for every apply.  It is formed once per context in FP64 (k_build_mtab)
+// from the quadrature rule, the pair tables and the single-mode matrices, and
+// stored per term ("inner-block table").  Because B_j^T W_j B_j = I for nq >= nb
+// on the outer positions, applying M_g between the outer transfers gives
+// exactly the term operator above (up to rounding).
+//
+// Shared-memory layout of a term tensor: [outer site][vector][inner index],
+// the outer site in canonical order (first outer position slowest).  A site
+// holds a contiguous payload of vb * NBI values, moved as 16-byte vectors:
+//   forward pass of position j:  [k_j][rest][payload] -> [rest][u_j][payload]
+//     (the slowest axis is contracted and becomes the fastest), positions in
+//     the order of fewest multiply-adds, ending on the canonical grid order;
+//   backward pass of position j: [rest][u_j][payload] -> [k_j][rest][payload]
+//     (the fastest axis is contracted and becomes the slowest), positions in
+//     reverse order, ending on the canonical basis order.
+// The basis part of the outer positions is fused with the exact fixed-point
+// compress-add of D_l * y_l (sg_fixed.cuh).
 #pragma once
 
 #include <algorithm>
@@ -43,7 +56,7 @@ struct FastLaunch {
 cudaError_t fast_launch_f32(const KParams &kp, const FastLaunch &a);
 cudaError_t fast_launch_f64(const KParams &kp, const FastLaunch &a);
 
-// Many problems of one kernel variant per launch (sg_fast_batch_f32.cu,
+// Many problems of one precision per launch (sg_fast_batch_f32.cu,
 // sg_fast_batch_f64.cu).  [0]: block-form items, [1]: warp-form items.
 struct FastBatchLaunch {
     const KParams *kps;           // device, one per problem
@@ -67,23 +80,20 @@ constexpr int kFT = 128;   // threads per term block
 constexpr int kMaxVB = 8;  // vectors per chunk
 
 struct FHdr {
-    int m, R, NB, NBo, grid, bad, coef;
-    int s, vb, NBO, NBrest, NBIn, nslice, NGs;
-    int matsz;                                           // elements of the B, B^T W, H1 block
-    unsigned nbomag, nbOmag;                             // reciprocals of NBo and NBO
-    int npair, nind, gsize;
+    int m, R, NB, NBI, NBo, grid, bad, coef;
+    int s, vb, NBO, NBrest, NGs, nslice;
+    int matsz, npair, nind;
     double c0;
     long long rank_off;
-    int mode[kMaxD], nb[kMaxD], nq[kMaxD];               // by layout position
-    int ostride[kMaxD];                                  // stride of a position inside its block (i or o)
+    int mode[kMaxD], nb[kMaxD], nq[kMaxD];               // by position
+    int ostride[kMaxD];                                  // stride inside the inner index (j < R) or in outer sites
     unsigned smag[kMaxD], bmag[kMaxD];                   // reciprocals of ostride and nb
     int oB[kMaxD], oBW[kMaxD], oH[kMaxD];                // shared-memory offsets of B, B^T W, H1
-    int gstride[kMaxD];                                  // outer grid strides inside a slice
-    unsigned gmag[kMaxD], qmag[kMaxD];                   // reciprocals of gstride and nq
+    int gB[kMaxD], gBW[kMaxD], gH1[kMaxD];               // global offsets of B, B^T W (1D tables), H1 base (fast tables)
+    int gstride[kMaxD];                                  // grid strides of the non-sliced outer positions
     int bymode[kMaxD];                                   // positions sorted by mode
-    int gB[kMaxD], gBW[kMaxD], gH1[kMaxD];               // global offsets of B, B^T W, H1 base
-    int uS[kMaxD];                                       // slice indices of the sliced positions
-    int pg[kMaxPairs], pgg[kMaxPairs], ioffs[kMaxPairs]; // G offsets (shared, global), induced offsets
+    int uS[kMaxD];                                       // slice digits of the sliced positions
+    int pgg[kMaxPairs], ioffs[kMaxPairs];                // G-table and induced-matrix offsets (fast tables)
     unsigned char pa[kMaxPairs], pb[kMaxPairs], ipos[kMaxPairs];
 };
 constexpr int kHdrBytes = 4096;  // per-group header budget the host plans with
@@ -110,32 +120,68 @@ static __device__ __forceinline__ void l2_prefetch_bulk(const void *p, unsigned 
 {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
-// at most this much of a term's stored potential is prefetched at entry (the
-// largest tables are 236 KB in FP32; ~600 resident blocks share the L2)
-constexpr int kVtPrefetchBytes = 32768;
+// at most this much of a term's inner-block table is prefetched at entry
+constexpr int kMtPrefetchBytes = 32768;
 
 template <typename T> struct FTab;
 template <> struct FTab<double> {
-    static __device__ const double *vt(const KParams &P) { return P.fast.vtabd; }
+    static __device__ const double *mt(const KParams &P) { return P.fast.mtabd; }
     static __device__ const double *img(const KParams &P) { return P.fast.imgd; }
-    static __device__ const double *f(const KParams &P) { return P.fast.tabd; }
-    static __device__ const double *t(const KParams &P) { return P.tabd; }
 };
 template <> struct FTab<float> {
-    static __device__ const float *vt(const KParams &P) { return P.fast.vtabf; }
+    static __device__ const float *mt(const KParams &P) { return P.fast.mtabf; }
     static __device__ const float *img(const KParams &P) { return P.fast.imgf; }
-    static __device__ const float *f(const KParams &P) { return P.fast.tabf; }
-    static __device__ const float *t(const KParams &P) { return P.tabf; }
 };
 
-__device__ __forceinline__ double warp_sum(double v)
+// W consecutive elements of T moved as one access (W * sizeof(T) <= 16 bytes)
+template <typename T, int W>
+struct alignas(sizeof(T) * W) VecT {
+    T v[W];
+};
+template <typename T, int W>
+__device__ __forceinline__ VecT<T, W> vld(const T *p)
 {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    return *reinterpret_cast<const VecT<T, W> *>(p);
+}
+template <typename T, int W>
+__device__ __forceinline__ void vst(T *p, const VecT<T, W> &a)
+{
+    *reinterpret_cast<VecT<T, W> *>(p) = a;
+}
+// read-only global loads of one unit
+template <typename T, int W> struct Ldg;
+template <> struct Ldg<float, 1> {
+    static __device__ __forceinline__ VecT<float, 1> f(const float *p) { return {{__ldg(p)}}; }
+};
+template <> struct Ldg<float, 4> {
+    static __device__ __forceinline__ VecT<float, 4> f(const float *p)
+    {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        return {{t.x, t.y, t.z, t.w}};
+    }
+};
+template <> struct Ldg<double, 1> {
+    static __device__ __forceinline__ VecT<double, 1> f(const double *p) { return {{__ldg(p)}}; }
+};
+template <> struct Ldg<double, 2> {
+    static __device__ __forceinline__ VecT<double, 2> f(const double *p)
+    {
+        const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+        return {{t.x, t.y}};
+    }
+};
+
+// elements per 16 bytes
+template <typename T> __host__ __device__ constexpr int vunit() { return 16 / (int)sizeof(T); }
+
+__host__ __device__ constexpr int tri_index(int r, int c, int n)
+{
+    // row r of the upper triangle starts after rows 0..r-1 (n, n-1, ... entries)
+    return r <= c ? r * n - r * (r - 1) / 2 + (c - r) : c * n - c * (c - 1) / 2 + (r - c);
 }
 
 // Per-term set-up from the term's record (built on the host): warp 0 copies
-// the record to shared memory and parses it, lane 0 derives the layout.
+// the record to shared memory and parses it.
 __device__ void load_record(const KParams &P, int p, int4 *buf, FHdr &H)
 {
     const int lane = threadIdx.x & 31;
@@ -151,17 +197,18 @@ __device__ void load_record(const KParams &P, int p, int4 *buf, FHdr &H)
         H.mode[j] = ps[j].mode; H.nb[j] = ps[j].nb; H.nq[j] = ps[j].nq;
         H.gB[j] = ps[j].offB; H.gBW[j] = ps[j].offBW; H.gH1[j] = ps[j].offH1;
     }
-    for (int q = lane; q < np; q += 32) { H.pa[q] = pr[q].pa; H.pb[q] = pr[q].pb; H.pg[q] = pr[q].gsm; H.pgg[q] = pr[q].goff; }
+    for (int q = lane; q < np; q += 32) { H.pa[q] = pr[q].pa; H.pb[q] = pr[q].pb; H.pgg[q] = pr[q].goff; }
     for (int q = lane; q < ni; q += 32) { H.ipos[q] = in[q].pos; H.ioffs[q] = in[q].ioff; }
     if (lane == 0) {
         H.m = m; H.R = hd->R; H.NB = hd->NB; H.coef = hd->coef; H.s = hd->s;
-        H.npair = np; H.nind = ni; H.gsize = hd->gsize; H.c0 = hd->c0; H.rank_off = hd->rank_off;
+        H.npair = np; H.nind = ni; H.c0 = hd->c0; H.rank_off = hd->rank_off;
         H.grid = np > 0;
     }
     __syncwarp();
 }
 
 // Layout quantities of the term, shared memory only: lane j handles position j.
+template <typename T>
 __device__ void derive_layout(const KParams &P, int nvec, int work, FHdr &H)
 {
     const int lane = threadIdx.x & 31;
@@ -175,189 +222,195 @@ __device__ void derive_layout(const KParams &P, int nvec, int work, FHdr &H)
         for (int i = j + 1; i < m; i++) gs *= H.nq[i];
         for (int i = 0; i < m; i++) rank += H.mode[i] < H.mode[j];
         H.oB[j] = off; H.oBW[j] = off + nq * nb; H.oH[j] = off + 2 * nq * nb;
-        H.bmag[j] = rmag(nb); H.qmag[j] = rmag(nq);
+        H.bmag[j] = rmag(nb);
         H.ostride[j] = st; H.smag[j] = rmag(st);
-        H.gstride[j] = gs; H.gmag[j] = rmag(gs);
+        H.gstride[j] = gs;
         H.bymode[rank] = j;
     }
     __syncwarp();
     if (lane != 0) return;
     H.bad = 0;
-    int mat = 0, NBIn = 1;
-    int64_t stage = 1;
+    int mat = 0, NBI = 1;
     H.NBO = 1; H.nslice = 1; H.NBrest = 1; H.NGs = 1;
     for (int j = 0; j < m; j++) {
         mat += 2 * H.nq[j] * H.nb[j] + H.nb[j] * H.nb[j];
-        if (j < R) NBIn *= H.nb[j];
+        if (j < R) NBI *= H.nb[j];
         else if (j < R + sv) { H.NBO *= H.nb[j]; H.nslice *= H.nq[j]; }
-        else { H.NBrest *= H.nb[j]; H.NGs *= H.nq[j]; stage *= H.nq[j]; }
+        else { H.NBrest *= H.nb[j]; H.NGs *= H.nq[j]; }
     }
-    if (mat > P.matcap || H.gsize > P.fast.gcap || H.NBO > P.fast.nbocap) { H.bad = 1; return; }
+    if (mat > P.matcap || H.NBO > P.fast.nbocap) { H.bad = 1; return; }
     H.matsz = mat;
-    H.NBIn = NBIn; H.NBo = H.NB / NBIn;
-    H.nbomag = rmag((unsigned)H.NBo);
-    H.nbOmag = rmag((unsigned)H.NBO);
-    stage *= NBIn;
-    const int64_t per_vec = 2 * (int64_t)H.NB + (H.grid ? 2 * stage : 0);
-    if (per_vec > work) { H.bad = 2; return; }
+    H.NBI = NBI; H.NBo = H.NB / NBI;
+    constexpr int U = vunit<T>();
+    const int64_t stage = (int64_t)NBI * H.NGs;
+    if (chunk_need(H.NB, stage, sv > 0, H.grid, 1, U) > work) { H.bad = 2; return; }
     int vb = nvec < kMaxVB ? nvec : kMaxVB;
-    while (vb > 1 && per_vec * vb > work) vb--;
+    while (vb > 1 && chunk_need(H.NB, stage, sv > 0, H.grid, vb, U) > work) vb--;
     H.vb = vb;
 }
 
-// Fibres f = tid, tid + GS, ... of an A x C grid as (a, c) = (f / C, f % C),
-// stepped without a division: one division per call for the start and the
-// step GS = as * C + cs, then one carry per step.
-struct FibreWalk {
-    int a, c, as, cs;
-    __device__ __forceinline__ void step(int C)
-    {
-        a += as;
-        c += cs;
-        if (c >= C) { c -= C; a++; }
-    }
-};
-template <int GS>
-__device__ __forceinline__ FibreWalk fibre_walk(int C, int tid)
+// ---------------------------------------------------------------------------
+// One-position transfers over a tensor of sites with a payload of PW units of
+// W elements each (unit-aligned).  M is the nout x nin matrix (row-major) of
+// the transfer: B (nq x nb) forward, B^T W (nb x nq) backward.
+//
+// forward:  in[k][c][pw] -> out[c][u][pw],  c < C, out = sum_k M[u][k] in[k]
+// backward: in[c][u][pw] -> out[k][c][pw]
+template <typename T, int W, int NI, int NO, int GS>
+__device__ __forceinline__ void fwd_pass_t(const T *__restrict__ in, T *__restrict__ out, int C, int PW,
+                                           unsigned pwmag, const T *__restrict__ M, int tid)
 {
-    FibreWalk w;
-    w.a = tid / C;
-    w.c = tid - w.a * C;
-    w.as = GS / C;
-    w.cs = GS - w.as * C;
-    return w;
-}
-
-// out[a][r][c] = sum_k M[r][k] in[a][k][c], matrix in registers, one fibre (a, c) at a time per thread
-template <typename T, int N, int RR, int GS>
-__device__ __forceinline__ void fcontract_t(const T *__restrict__ in, T *__restrict__ out, int A, int C,
-                                            const T *__restrict__ M, int tid)
-{
-    T mr[RR * N];
+    T mr[NO * NI];
 #pragma unroll
-    for (int i = 0; i < RR * N; i++) mr[i] = M[i];
-    for (FibreWalk w = fibre_walk<GS>(C, tid); w.a < A; w.step(C)) {
-        const T *ip = in + w.a * N * C + w.c;
-        T *op = out + w.a * RR * C + w.c;
-        T xv[N];
+    for (int i = 0; i < NO * NI; i++) mr[i] = M[i];
+    const int total = C * PW, cpw = C * PW;
+    for (int w = tid; w < total; w += GS) {
+        const int c = fdiv(w, PW, pwmag), pw = w - c * PW;
+        VecT<T, W> xv[NI];
 #pragma unroll
-        for (int k = 0; k < N; k++) xv[k] = ip[k * C];
+        for (int k = 0; k < NI; k++) xv[k] = vld<T, W>(in + (size_t)(k * cpw + w) * W);
+        T *op = out + (size_t)((c * NO) * PW + pw) * W;
 #pragma unroll
-        for (int r = 0; r < RR; r++) {
-            T acc = T(0);
+        for (int u = 0; u < NO; u++) {
+            VecT<T, W> a;
 #pragma unroll
-            for (int k = 0; k < N; k++) acc = fma_t(mr[r * N + k], xv[k], acc);
-            op[r * C] = acc;
-        }
-    }
-}
-
-template <typename T, int GS>
-__device__ void fcontract_rt(const T *__restrict__ in, T *__restrict__ out, int A, int n, int r, int C,
-                             const T *__restrict__ M, int tid)
-{
-    for (FibreWalk w = fibre_walk<GS>(C, tid); w.a < A; w.step(C)) {
-        const T *ip = in + (w.a * n) * C + w.c;
-        for (int rr = 0; rr < r; rr++) {
-            const T *mp = M + rr * n;
-            T acc = T(0);
-            for (int k = 0; k < n; k++) acc += mp[k] * ip[k * C];
-            out[(w.a * r + rr) * C + w.c] = acc;
-        }
-    }
-}
-
-template <typename T, int GS>
-__device__ void fcontract(const T *in, T *out, int A, int n, int r, int C, const T *M, int tid)
-{
-#define SG_FC(NN, RRR) case (NN) * 64 + (RRR): fcontract_t<T, NN, RRR, GS>(in, out, A, C, M, tid); return;
-    switch (n * 64 + r) {
-        SG_FC(2, 2) SG_FC(2, 3) SG_FC(3, 2) SG_FC(3, 3) SG_FC(3, 4) SG_FC(4, 3) SG_FC(4, 4) SG_FC(4, 5)
-        SG_FC(5, 4) SG_FC(5, 5) SG_FC(5, 6) SG_FC(6, 5) SG_FC(6, 6) SG_FC(6, 7) SG_FC(7, 6)
-        default: fcontract_rt<T, GS>(in, out, A, n, r, C, M, tid); return;
-    }
-#undef SG_FC
-}
-
-__host__ __device__ constexpr int cpow(int b, int e) { return e <= 0 ? 1 : b * cpow(b, e - 1); }
-
-// one register stage: out[p][u][q] = sum_k M[u][k] in[p][k][q]
-template <typename T, int SZ, int PP, int N, int RR, int Q, int MS>
-__device__ __forceinline__ void rstage(const T (&in)[SZ], T (&out)[SZ], const T (&M)[MS])
-{
-#pragma unroll
-    for (int p = 0; p < PP; p++)
-#pragma unroll
-        for (int u = 0; u < RR; u++)
-#pragma unroll
-            for (int q = 0; q < Q; q++) {
+            for (int e = 0; e < W; e++) {
                 T acc = T(0);
 #pragma unroll
-                for (int k = 0; k < N; k++) acc = fma_t(M[u * N + k], in[(p * N + k) * Q + q], acc);
-                out[(p * RR + u) * Q + q] = acc;
+                for (int k = 0; k < NI; k++) acc = fma_t(mr[u * NI + k], xv[k].v[e], acc);
+                a.v[e] = acc;
             }
-}
-
-// Register phase: for every outer grid point g of the slice and every vector
-// of the chunk, the inner slots basis -> grid, times the potential, grid ->
-// basis, in place in Z[i][v][g].
-template <typename T, int R, int NB1, int NQ1, bool UNI, int GS>
-__device__ void reg_phase(const FHdr &H, const T *mats, const T *__restrict__ vt, T *Z, const int vb, const int tid)
-{
-    constexpr int NBI = cpow(NB1, R), NGI = cpow(NQ1, R), SZ = NGI;
-    constexpr int RA = R > 0 ? R : 1;
-    constexpr int NM = UNI ? 1 : RA;
-    T Bm[NM][NQ1 * NB1], BWm[NM][NB1 * NQ1];
-#pragma unroll
-    for (int b = 0; b < NM; b++)
-#pragma unroll
-        for (int e = 0; e < NQ1 * NB1; e++) {
-            Bm[b][e] = R > 0 ? mats[H.oB[b] + e] : T(0);
-            BWm[b][e] = R > 0 ? mats[H.oBW[b] + e] : T(0);
-        }
-    const int NGs = H.NGs;
-    for (int g = tid; g < NGs; g += GS) {
-        // the coupling potential at the NGI inner points of outer grid point g
-        // (evaluated once per context; vt: this slice's table, [gi][g])
-        T V[SZ];
-#pragma unroll
-        for (int gi = 0; gi < NGI; gi++) V[gi] = __ldg(vt + (size_t)gi * NGs + g);
-        for (int v = 0; v < vb; v++) {
-            T va[SZ], vw[SZ];
-#pragma unroll
-            for (int i = 0; i < NBI; i++) va[i] = Z[(i * vb + v) * NGs + g];
-            if constexpr (R == 0) {
-                va[0] *= V[0];
-            } else if constexpr (R == 1) {
-                rstage<T, SZ, 1, NB1, NQ1, 1>(va, vw, Bm[0]);
-#pragma unroll
-                for (int gi = 0; gi < NGI; gi++) vw[gi] *= V[gi];
-                rstage<T, SZ, 1, NQ1, NB1, 1>(vw, va, BWm[0]);
-            } else if constexpr (R == 2) {
-                rstage<T, SZ, 1, NB1, NQ1, NB1>(va, vw, Bm[0]);
-                rstage<T, SZ, NQ1, NB1, NQ1, 1>(vw, va, Bm[UNI ? 0 : 1]);
-#pragma unroll
-                for (int gi = 0; gi < NGI; gi++) va[gi] *= V[gi];
-                rstage<T, SZ, NQ1, NQ1, NB1, 1>(va, vw, BWm[UNI ? 0 : 1]);
-                rstage<T, SZ, 1, NQ1, NB1, NB1>(vw, va, BWm[0]);
-            } else if constexpr (R == 3) {
-                rstage<T, SZ, 1, NB1, NQ1, NB1 * NB1>(va, vw, Bm[0]);
-                rstage<T, SZ, NQ1, NB1, NQ1, NB1>(vw, va, Bm[UNI ? 0 : 1]);
-                rstage<T, SZ, NQ1 * NQ1, NB1, NQ1, 1>(va, vw, Bm[UNI ? 0 : 2]);
-#pragma unroll
-                for (int gi = 0; gi < NGI; gi++) vw[gi] *= V[gi];
-                rstage<T, SZ, NQ1 * NQ1, NQ1, NB1, 1>(vw, va, BWm[UNI ? 0 : 2]);
-                rstage<T, SZ, NQ1, NQ1, NB1, NB1>(va, vw, BWm[UNI ? 0 : 1]);
-                rstage<T, SZ, 1, NQ1, NB1, NB1 * NB1>(vw, va, BWm[0]);
-            }
-#pragma unroll
-            for (int i = 0; i < NBI; i++) Z[(i * vb + v) * NGs + g] = va[i];
+            vst<T, W>(op + (size_t)u * PW * W, a);
         }
     }
 }
 
-// Shared-memory partition of one term group: matrices, G tables, slice
-// weights (head), then the work area for X, Y and the two grid buffers.
+template <typename T, int W, int NI, int NO, int GS>
+__device__ __forceinline__ void bwd_pass_t(const T *__restrict__ in, T *__restrict__ out, int C, int PW,
+                                           unsigned pwmag, const T *__restrict__ M, int tid)
+{
+    T mr[NO * NI];
+#pragma unroll
+    for (int i = 0; i < NO * NI; i++) mr[i] = M[i];
+    const int total = C * PW, cpw = C * PW;
+    for (int w = tid; w < total; w += GS) {
+        const int c = fdiv(w, PW, pwmag), pw = w - c * PW;
+        const T *ip = in + (size_t)((c * NI) * PW + pw) * W;
+        VecT<T, W> xv[NI];
+#pragma unroll
+        for (int u = 0; u < NI; u++) xv[u] = vld<T, W>(ip + (size_t)u * PW * W);
+#pragma unroll
+        for (int k = 0; k < NO; k++) {
+            VecT<T, W> a;
+#pragma unroll
+            for (int e = 0; e < W; e++) {
+                T acc = T(0);
+#pragma unroll
+                for (int u = 0; u < NI; u++) acc = fma_t(mr[k * NI + u], xv[u].v[e], acc);
+                a.v[e] = acc;
+            }
+            vst<T, W>(out + (size_t)(k * cpw + w) * W, a);
+        }
+    }
+}
+
+// Any sizes (levels beyond the compiled ones): matrix and inputs read from
+// shared memory per output.
+template <typename T, int W, int GS>
+__device__ void pass_rt(const T *__restrict__ in, T *__restrict__ out, int C, int PW, unsigned pwmag, int ni,
+                        int no, const T *__restrict__ M, bool forward, int tid)
+{
+    const int total = C * PW, cpw = C * PW;
+    for (int w = tid; w < total; w += GS) {
+        const int c = fdiv(w, PW, pwmag), pw = w - c * PW;
+        for (int r = 0; r < no; r++) {
+            VecT<T, W> a;
+#pragma unroll
+            for (int e = 0; e < W; e++) a.v[e] = T(0);
+            for (int k = 0; k < ni; k++) {
+                const T mv = M[r * ni + k];
+                const VecT<T, W> xv = forward ? vld<T, W>(in + (size_t)(k * cpw + w) * W)
+                                              : vld<T, W>(in + (size_t)((c * ni + k) * PW + pw) * W);
+#pragma unroll
+                for (int e = 0; e < W; e++) a.v[e] = fma_t(mv, xv.v[e], a.v[e]);
+            }
+            if (forward) vst<T, W>(out + (size_t)((c * no + r) * PW + pw) * W, a);
+            else vst<T, W>(out + (size_t)(r * cpw + w) * W, a);
+        }
+    }
+}
+
+template <typename T, int W, int GS>
+__device__ void fwd_pass(const T *in, T *out, int C, int PW, int nb, int nq, const T *M, int tid)
+{
+    const unsigned mag = rmag((unsigned)PW);
+#define SG_FP(NI, NO) case (NI) * 64 + (NO): fwd_pass_t<T, W, NI, NO, GS>(in, out, C, PW, mag, M, tid); return;
+    switch (nb * 64 + nq) {
+        SG_FP(2, 3) SG_FP(3, 4) SG_FP(4, 5) SG_FP(5, 6) SG_FP(2, 2) SG_FP(3, 3) SG_FP(4, 4) SG_FP(5, 5)
+        default: pass_rt<T, W, GS>(in, out, C, PW, mag, nb, nq, M, true, tid); return;
+    }
+#undef SG_FP
+}
+
+template <typename T, int W, int GS>
+__device__ void bwd_pass(const T *in, T *out, int C, int PW, int nq, int nb, const T *M, int tid)
+{
+    const unsigned mag = rmag((unsigned)PW);
+#define SG_BP(NI, NO) case (NI) * 64 + (NO): bwd_pass_t<T, W, NI, NO, GS>(in, out, C, PW, mag, M, tid); return;
+    switch (nq * 64 + nb) {
+        SG_BP(3, 2) SG_BP(4, 3) SG_BP(5, 4) SG_BP(6, 5) SG_BP(2, 2) SG_BP(3, 3) SG_BP(4, 4) SG_BP(5, 5)
+        default: pass_rt<T, W, GS>(in, out, C, PW, mag, nq, nb, M, false, tid); return;
+    }
+#undef SG_BP
+}
+
+// Register phase: at every outer grid point g of the slice, every vector's
+// inner block z (NBI values) becomes M_g z, in place in Z[g][v][i].  M_g is
+// read from the inner-block table tab ([unit][g][unit elements], this slice).
+template <typename T, int NBI, int GS>
+__device__ void reg_phase(const T *__restrict__ tab, T *Z, int NGs, int vb, int tid)
+{
+    constexpr int U = vunit<T>();
+    constexpr int UE = NBI == 1 ? 1 : U;
+    constexpr int NEU = (NBI * (NBI + 1) / 2 + UE - 1) / UE;
+    constexpr int ZW = (NBI * (int)sizeof(T)) % 16 == 0 ? U : NBI == 2 && sizeof(T) == 4 ? 2 : 1;
+    for (int g = tid; g < NGs; g += GS) {
+        T mm[NEU * UE];
+#pragma unroll
+        for (int q = 0; q < NEU; q++) {
+            const VecT<T, UE> t = Ldg<T, UE>::f(tab + ((size_t)q * NGs + g) * UE);
+#pragma unroll
+            for (int e = 0; e < UE; e++) mm[q * UE + e] = t.v[e];
+        }
+        T *zp = Z + (size_t)g * vb * NBI;
+        for (int v = 0; v < vb; v++, zp += NBI) {
+            T z[NBI], y[NBI];
+#pragma unroll
+            for (int i = 0; i < NBI; i += ZW) {
+                const VecT<T, ZW> t = vld<T, ZW>(zp + i);
+#pragma unroll
+                for (int e = 0; e < ZW; e++) z[i + e] = t.v[e];
+            }
+#pragma unroll
+            for (int r = 0; r < NBI; r++) {
+                T acc = T(0);
+#pragma unroll
+                for (int c = 0; c < NBI; c++) acc = fma_t(mm[tri_index(r, c, NBI)], z[c], acc);
+                y[r] = acc;
+            }
+#pragma unroll
+            for (int i = 0; i < NBI; i += ZW) {
+                VecT<T, ZW> t;
+#pragma unroll
+                for (int e = 0; e < ZW; e++) t.v[e] = y[i + e];
+                vst<T, ZW>(zp + i, t);
+            }
+        }
+    }
+}
+
+// Shared-memory partition of one term group: matrices, slice weights
+// (head), then the work area.
 __host__ __device__ inline size_t part_head_bytes(const KParams &P, size_t rb)
 {
     return (((size_t)P.matcap + P.fast.gcap + 2 * (size_t)P.fast.nbocap) * rb + 15) & ~(size_t)15;
@@ -367,96 +420,108 @@ __host__ __device__ inline size_t part_bytes(const KParams &P, size_t rb, int wo
     return (part_head_bytes(P, rb) + (size_t)work * rb + 15) & ~(size_t)15;
 }
 
-
-// Per-chunk element loops, compiled for VB vectors (no predicated lanes for
-// small chunks).  Tensor layout [i][v][o] (i: inner slots, v: vector, o: outer).
-//   chunk_in:  gather X through M^B (x: the chunk's first vector), a barrier,
-//              then the basis part Y = c0 X + sum_j H1_j x_j X, a barrier.
-//   chunk_out: the exact compress-add of D_l * Y into the accumulators of the
-//              chunk's vectors (acc: the first vector's), a barrier.
-// One row of a single-mode matrix applied along a position: acc[v] +=
-// sum_kp H[kp] x[kp * st + v * NBo], NK and VB at compile time.
-template <typename T, int VB, int NK>
-__device__ __forceinline__ void basis_row(T (&acc)[VB], const T *xp, const T *Hr, int st, int NBo)
+// Gather of one chunk: X[o][v][i] = x_v[rank(o, i)] (M^B holds the ranks in
+// the order [outer site][inner index]).
+template <typename T, int NBI, int GS>
+__device__ __forceinline__ void gather_t(const FHdr &H, const KParams &P, const double *__restrict__ x,
+                                         const int *__restrict__ rk, T *X, int vb, int tid)
 {
-    T hv[NK];
+    constexpr int ZW = (NBI * (int)sizeof(T)) % 16 == 0 ? vunit<T>() : NBI == 2 && sizeof(T) == 4 ? 2 : 1;
+    const int NBo = H.NBo, total = NBo * vb;
+    const unsigned vmag = rmag((unsigned)vb);
+    for (int w = tid; w < total; w += GS) {
+        const int o = fdiv(w, vb, vmag), v = w - o * vb;
+        const int *rp = rk + (size_t)o * NBI;
+        const double *xv = x + (size_t)v * P.n_cs;
+        T val[NBI];
 #pragma unroll
-    for (int kp = 0; kp < NK; kp++) hv[kp] = Hr[kp];
+        for (int i = 0; i < NBI; i++) val[i] = (T)__ldg(xv + __ldg(rp + i));
+        T *dst = X + (size_t)w * NBI;
 #pragma unroll
-    for (int kp = 0; kp < NK; kp++)
+        for (int i = 0; i < NBI; i += ZW) {
+            VecT<T, ZW> t;
 #pragma unroll
-        for (int v = 0; v < VB; v++) acc[v] = fma_t(hv[kp], xp[kp * st + v * NBo], acc[v]);
-}
-
-template <typename T, int VB, int GS>
-__device__ __forceinline__ void chunk_in(FHdr &H, const KParams &P, const double *__restrict__ x,
-                                         const int *__restrict__ rk, const T *mats, T *X, T *Y, int tid)
-{
-    const int NB = H.NB, NBo = H.NBo, m = H.m, R = H.R;
-    {
-        int rn = tid < NB ? __ldg(rk + tid) : 0;
-        for (int e = tid; e < NB; e += GS) {
-            const int r = rn;
-            if (e + GS < NB) rn = __ldg(rk + e + GS);
-            const int i = fdiv(e, NBo, H.nbomag), o = e - i * NBo;
-            T xv[VB];
-#pragma unroll
-            for (int v = 0; v < VB; v++) xv[v] = (T)__ldg(x + (size_t)v * P.n_cs + r);
-#pragma unroll
-            for (int v = 0; v < VB; v++) X[(i * VB + v) * NBo + o] = xv[v];
+            for (int e = 0; e < ZW; e++) t.v[e] = val[i + e];
+            vst<T, ZW>(dst + i, t);
         }
     }
-    gsync<GS>();
-    for (int e = tid; e < NB; e += GS) {
-        const int i = fdiv(e, NBo, H.nbomag), o = e - i * NBo;
-        const int base0 = i * VB * NBo + o;
-        T acc[VB];
+}
+
+template <typename T, int GS>
+__device__ void gather_rt(const FHdr &H, const KParams &P, const double *__restrict__ x,
+                          const int *__restrict__ rk, T *X, int vb, int tid)
+{
+    const int NBI = H.NBI, total = H.NBo * vb;
+    const unsigned vmag = rmag((unsigned)vb);
+    for (int w = tid; w < total; w += GS) {
+        const int o = fdiv(w, vb, vmag), v = w - o * vb;
+        for (int i = 0; i < NBI; i++)
+            X[(size_t)w * NBI + i] = (T)__ldg(x + (size_t)v * P.n_cs + __ldg(rk + (size_t)o * NBI + i));
+    }
+}
+
+template <typename T, int GS>
+__device__ void gather(const FHdr &H, const KParams &P, const double *x, const int *rk, T *X, int vb, int tid)
+{
+    switch (H.NBI) {
+        case 1: gather_t<T, 1, GS>(H, P, x, rk, X, vb, tid); return;
+        case 2: gather_t<T, 2, GS>(H, P, x, rk, X, vb, tid); return;
+        case 4: gather_t<T, 4, GS>(H, P, x, rk, X, vb, tid); return;
+        case 8: gather_t<T, 8, GS>(H, P, x, rk, X, vb, tid); return;
+        default: gather_rt<T, GS>(H, P, x, rk, X, vb, tid); return;
+    }
+}
+
+// Final step of a chunk, fused: y = F + (c0 X when the term has no grid) +
+// sum over outer positions j of H1_j x_j X, then the exact compress-add of
+// D_l * y into the accumulators.  Work item = (outer site o, unit of W payload
+// elements); F may be NULL (no grid).
+template <typename T, int W, int GS>
+__device__ void combine_add(const FHdr &H, const KParams &P, const int *__restrict__ rk,
+                            const long long *__restrict__ maxbits, unsigned long long *acc, const T *X,
+                            const T *F, const T *mats, int vb, int tid)
+{
+    const int NBI = H.NBI, Pl = NBI * vb, PW = Pl / W, total = H.NBo * PW;
+    const int m = H.m, R = H.R;
+    const unsigned pwmag = rmag((unsigned)PW), nbimag = rmag((unsigned)NBI);
+    const T c0 = H.grid ? T(0) : (T)H.c0;
+    for (int w = tid; w < total; w += GS) {
+        const int o = fdiv(w, PW, pwmag), pw = w - o * PW;
+        const size_t eoff = (size_t)w * W;  // = o * Pl + pw * W
+        T a[W];
+        {
+            const VecT<T, W> xv = vld<T, W>(X + eoff);
+            if (F) {
+                const VecT<T, W> fv = vld<T, W>(F + eoff);
 #pragma unroll
-        for (int v = 0; v < VB; v++) acc[v] = (T)H.c0 * X[base0 + v * NBo];
-        for (int j = 0; j < m; j++) {
-            const int src = j < R ? i : o;
-            const int q = fdiv(src, H.ostride[j], H.smag[j]);
-            const int nbj = H.nb[j], kj = q - fdiv(q, nbj, H.bmag[j]) * nbj;
-            const int st = j < R ? H.ostride[j] * VB * NBo : H.ostride[j];
-            const T *xp = X + base0 - kj * st;
-            const T *Hr = mats + H.oH[j] + kj * nbj;
-            switch (nbj) {
-                case 2: basis_row<T, VB, 2>(acc, xp, Hr, st, NBo); break;
-                case 3: basis_row<T, VB, 3>(acc, xp, Hr, st, NBo); break;
-                case 4: basis_row<T, VB, 4>(acc, xp, Hr, st, NBo); break;
-                case 5: basis_row<T, VB, 5>(acc, xp, Hr, st, NBo); break;
-                default:
-                    for (int kp = 0; kp < nbj; kp++) {
-                        const T hv = Hr[kp];
+                for (int e = 0; e < W; e++) a[e] = fma_t(c0, xv.v[e], fv.v[e]);
+            } else {
 #pragma unroll
-                        for (int v = 0; v < VB; v++) acc[v] = fma_t(hv, xp[kp * st + v * NBo], acc[v]);
-                    }
+                for (int e = 0; e < W; e++) a[e] = c0 * xv.v[e];
             }
         }
+        for (int j = R; j < m; j++) {
+            const int q = fdiv(o, H.ostride[j], H.smag[j]);
+            const int nbj = H.nb[j], kj = q - fdiv(q, nbj, H.bmag[j]) * nbj;
+            const int st = H.ostride[j] * Pl;
+            const T *xp = X + eoff - (size_t)kj * st;
+            const T *hr = mats + H.oH[j] + kj * nbj;
+            for (int kp = 0; kp < nbj; kp++) {
+                const T hv = hr[kp];
+                const VecT<T, W> xv = vld<T, W>(xp + (size_t)kp * st);
 #pragma unroll
-        for (int v = 0; v < VB; v++) Y[base0 + v * NBo] = acc[v];
+                for (int e = 0; e < W; e++) a[e] = fma_t(hv, xv.v[e], a[e]);
+            }
+        }
+        // element e of the unit is payload element pw * W + e = v * NBI + i
+#pragma unroll
+        for (int e = 0; e < W; e++) {
+            const int pe = pw * W + e;
+            const int v = fdiv(pe, NBI, nbimag), i = pe - v * NBI;
+            const int r = __ldg(rk + (size_t)o * NBI + i);
+            fx::Acc<T>::add(acc + ((size_t)v * P.n_cs + r) * fx::Acc<T>::words, a[e], H.coef, maxbits[v], P.err);
+        }
     }
-    gsync<GS>();
-}
-
-template <typename T, int VB, int GS>
-__device__ __forceinline__ void chunk_out(FHdr &H, const KParams &P, const int *__restrict__ rk,
-                                          const long long *__restrict__ maxbits, unsigned long long *acc,
-                                          const T *Y, int tid)
-{
-    const int NB = H.NB, NBo = H.NBo;
-    int Ev[VB];
-#pragma unroll
-    for (int v = 0; v < VB; v++) Ev[v] = fx::Acc<T>::unit(maxbits[v]);
-    for (int e = tid; e < NB; e += GS) {
-        const int i = fdiv(e, NBo, H.nbomag), o = e - i * NBo;
-        unsigned long long *a = acc + (size_t)__ldg(rk + e) * fx::Acc<T>::words;
-#pragma unroll
-        for (int v = 0; v < VB; v++)
-            fx::Acc<T>::add_unit(a + (size_t)v * P.n_cs * fx::Acc<T>::words, Y[(i * VB + v) * NBo + o], H.coef,
-                                 Ev[v], P.err);
-    }
-    gsync<GS>();
 }
 
 // One Smolyak term (processing position p of problem P) by a group of GS
@@ -464,28 +529,29 @@ __device__ __forceinline__ void chunk_out(FHdr &H, const KParams &P, const int *
 // barriers).  `base` is the group's shared-memory partition (part_bytes of P
 // with `work_cap` work elements), `accp` the problem's fixed-point
 // accumulators, `x` and `maxbits` its input vectors and their exponents.
-template <typename T, int NB1, int NQ1, int RMAX, bool UNI, int GS>
+template <typename T, int GS>
 __device__ __forceinline__ void fast_term(const KParams &P, const double *__restrict__ x,
                                           unsigned long long *accp, const long long *__restrict__ maxbits,
                                           int nvec, int p, int work_cap, unsigned char *base, FHdr &H,
                                           const int tid)
 {
+    constexpr int U = vunit<T>();
     const size_t rb = sizeof(T);
     T *mats = reinterpret_cast<T *>(base);
     T *WoF = mats + P.matcap + P.fast.gcap;
     T *WoB = WoF + P.fast.nbocap;
     T *work = reinterpret_cast<T *>(base + part_head_bytes(P, rb));
 
-    // the start of the term's stored potential is fetched into L2 now: it is
-    // first read after the gather, the basis part and the outer contractions
+    // the start of the term's inner-block table is fetched into L2 now: it is
+    // first read after the gather and the forward transfers
     if (tid == 0) {
-        const long long v0 = P.fast.vt_off[p], v1 = P.fast.vt_off[p + 1];
+        const long long v0 = P.fast.mt_off[p], v1 = P.fast.mt_off[p + 1];
         if (v1 > v0) {
             // 16-byte aligned and rounded; the table buffer is padded by 16 bytes
             const size_t b0 = ((size_t)v0 * rb) & ~(size_t)15;
             const size_t e1 = ((size_t)v1 * rb + 15) & ~(size_t)15;
-            const size_t b1 = e1 - b0 > (size_t)kVtPrefetchBytes ? b0 + (size_t)kVtPrefetchBytes : e1;
-            l2_prefetch_bulk(reinterpret_cast<const unsigned char *>(FTab<T>::vt(P)) + b0, (unsigned)(b1 - b0));
+            const size_t b1 = e1 - b0 > (size_t)kMtPrefetchBytes ? b0 + (size_t)kMtPrefetchBytes : e1;
+            l2_prefetch_bulk(reinterpret_cast<const unsigned char *>(FTab<T>::mt(P)) + b0, (unsigned)(b1 - b0));
         }
     }
     // the term's image (B, B^T W, H1 per position, then its G tables) is copied
@@ -499,36 +565,35 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
     }
     if (tid < 32) {
         load_record(P, p, reinterpret_cast<int4 *>(work), H);
-        derive_layout(P, nvec, work_cap, H);
+        derive_layout<T>(P, nvec, work_cap, H);
     }
     gsync<GS>();
     if (H.bad) {
         if (tid == 0 && P.err) atomicCAS(P.err, 0, 110 + H.bad);
         return;
     }
-    const int m = H.m, R = H.R, NB = H.NB, NBo = H.NBo;
+    const int m = H.m, R = H.R, NB = H.NB, NBI = H.NBI;
     const int *rk = P.fast.ranks + H.rank_off;
-    const T *gtab = mats + H.matsz;  // the term's G tables follow its matrices
+    const bool sliced = H.s > 0;
+    const int ps = R + H.s;  // first non-sliced outer position
 
     for (int v0 = 0; v0 < nvec; v0 += H.vb) {
         const int vb = min(H.vb, nvec - v0);
-        T *X = work, *Y = work + NB * vb, *bufA = Y + NB * vb;
-        // gather X[i][v][o] through M^B, then the basis part Y = c0 X + sum_j H1_j x_j X
-        // (element loops compiled for the chunk's vector count)
-        switch (vb) {
-#define SG_VB(VB) case VB: chunk_in<T, VB, GS>(H, P, x + (size_t)v0 * P.n_cs, rk, mats, X, Y, tid); break;
-            SG_VB(1) SG_VB(2) SG_VB(3) SG_VB(4) SG_VB(5) SG_VB(6) SG_VB(7) SG_VB(8)
-#undef SG_VB
-        }
+        const int Pl = NBI * vb;                       // payload elements per site
+        const int WW = Pl % U == 0 ? U : 1;            // unit of the vector accesses
+        const int PW = Pl / WW;
+        T *X = work;
+        T *Y = X + pad_elems((int64_t)NB * vb, U);
+        T *A = sliced ? Y + pad_elems((int64_t)NB * vb, U) : Y;
+        T *Bf = A + pad_elems((int64_t)NBI * H.NGs * vb, U);
+        gather<T, GS>(H, P, x + (size_t)v0 * P.n_cs, rk, X, vb, tid);
+        gsync<GS>();
+        const T *F = nullptr;
         if (H.grid) {
-            const int ps = R + H.s;
-            int vt_ngi = 1;
-            for (int j = 0; j < R; j++) vt_ngi *= H.nq[j];
-            const int NBIv = H.NBIn * vb;
-            T *bufB = bufA + (size_t)H.NBIn * H.NGs * vb;
             for (int sl = 0; sl < H.nslice; sl++) {
-                T *cur, *oth, *spare;
-                if (H.s > 0) {
+                const T *cur;
+                int nxt;
+                if (sliced) {
                     if (tid == 0) {
                         int rem = sl;
                         for (int j = ps - 1; j >= R; j--) { H.uS[j] = rem % H.nq[j]; rem /= H.nq[j]; }
@@ -546,75 +611,83 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
                         WoF[ko] = wf; WoB[ko] = wb;
                     }
                     gsync<GS>();
-                    // Xs[iv][rest] = sum_ko WoF[ko] X[iv][ko][rest]
-                    for (FibreWalk w = fibre_walk<GS>(H.NBrest, tid); w.a < NBIv; w.step(H.NBrest)) {
-                        const T *xp = X + (size_t)w.a * NBo + w.c;
+                    // A[rest][payload] = sum_ko WoF[ko] X[ko][rest][payload]
+                    const int nrest = H.NBrest * Pl;
+                    for (int e = tid; e < nrest; e += GS) {
                         T acc = T(0);
-                        for (int ko = 0; ko < H.NBO; ko++) acc += WoF[ko] * xp[ko * H.NBrest];
-                        bufA[w.a * H.NBrest + w.c] = acc;
+                        for (int ko = 0; ko < H.NBO; ko++) acc = fma_t(WoF[ko], X[(size_t)ko * nrest + e], acc);
+                        A[e] = acc;
                     }
                     gsync<GS>();
-                    cur = bufA; oth = bufB; spare = bufA;
+                    cur = A; nxt = 1;
                 } else {
-                    cur = X; oth = bufA; spare = bufB;  // X is not needed after the basis part
+                    cur = X; nxt = 0;
                 }
-                // outer basis -> grid (ping-pong between the two grid buffers)
-                int A = NBIv;
+                // outer basis -> grid, positions ps..m-1 (slowest axis each time)
+                int sites = H.NBrest;
                 for (int j = ps; j < m; j++) {
-                    int C = 1;
-                    for (int i2 = j + 1; i2 < m; i2++) C *= H.nb[i2];
-                    fcontract<T, GS>(cur, oth, A, H.nb[j], H.nq[j], C, mats + H.oB[j], tid);
-                    A *= H.nq[j];
-                    T *freed = (cur == X) ? spare : cur;
-                    cur = oth; oth = freed;
+                    const int C = sites / H.nb[j];
+                    T *out = nxt ? Bf : A;
+                    if (WW == U) fwd_pass<T, U, GS>(cur, out, C, PW, H.nb[j], H.nq[j], mats + H.oB[j], tid);
+                    else fwd_pass<T, 1, GS>(cur, out, C, PW, H.nb[j], H.nq[j], mats + H.oB[j], tid);
+                    sites = C * H.nq[j];
+                    cur = out; nxt ^= 1;
                     gsync<GS>();
                 }
-                if (cur == X) oth = bufA;
-                // inner slots and potential, in registers
+                // inner blocks at every outer grid point
                 {
-                    const T *vts = FTab<T>::vt(P) + P.fast.vt_off[p] + (size_t)sl * H.NGs * (size_t)vt_ngi;
-                    switch (R) {
-                        case 0: reg_phase<T, 0, NB1, NQ1, UNI, GS>(H, mats, vts, cur, vb, tid); break;
-                        case 1: if constexpr (RMAX >= 1) reg_phase<T, 1, NB1, NQ1, UNI, GS>(H, mats, vts, cur, vb, tid); break;
-                        case 2: if constexpr (RMAX >= 2) reg_phase<T, 2, NB1, NQ1, UNI, GS>(H, mats, vts, cur, vb, tid); break;
-                        case 3: if constexpr (RMAX >= 3) reg_phase<T, 3, NB1, NQ1, UNI, GS>(H, mats, vts, cur, vb, tid); break;
+                    T *Z = const_cast<T *>(cur);
+                    const int ue = mt_unit(NBI, U), neu = mt_units(NBI, U);
+                    const T *tab = FTab<T>::mt(P) + P.fast.mt_off[p] + (size_t)sl * neu * ue * H.NGs;
+                    switch (NBI) {
+                        case 1: reg_phase<T, 1, GS>(tab, Z, H.NGs, vb, tid); break;
+                        case 2: reg_phase<T, 2, GS>(tab, Z, H.NGs, vb, tid); break;
+                        case 3: reg_phase<T, 3, GS>(tab, Z, H.NGs, vb, tid); break;
+                        case 4: reg_phase<T, 4, GS>(tab, Z, H.NGs, vb, tid); break;
+                        case 8: reg_phase<T, 8, GS>(tab, Z, H.NGs, vb, tid); break;
+                        case 9: reg_phase<T, 9, GS>(tab, Z, H.NGs, vb, tid); break;
                         default: break;
                     }
                 }
                 gsync<GS>();
-                // outer grid -> basis, reverse order
+                // outer grid -> basis, positions m-1..ps (fastest axis each time)
                 for (int j = m - 1; j >= ps; j--) {
-                    int Aj = NBIv, C = 1;
-                    for (int i2 = ps; i2 < j; i2++) Aj *= H.nq[i2];
-                    for (int i2 = j + 1; i2 < m; i2++) C *= H.nb[i2];
-                    fcontract<T, GS>(cur, oth, Aj, H.nq[j], H.nb[j], C, mats + H.oBW[j], tid);
-                    T *tp = cur; cur = oth; oth = tp;
+                    const int C = sites / H.nq[j];
+                    T *out = nxt ? Bf : A;
+                    if (WW == U) bwd_pass<T, U, GS>(cur, out, C, PW, H.nq[j], H.nb[j], mats + H.oBW[j], tid);
+                    else bwd_pass<T, 1, GS>(cur, out, C, PW, H.nq[j], H.nb[j], mats + H.oBW[j], tid);
+                    sites = C * H.nb[j];
+                    cur = out; nxt ^= 1;
                     gsync<GS>();
                 }
-                // Y[iv][ko][rest] += WoB[ko] cur[iv][rest]
-                if (H.s > 0) {
-                    for (FibreWalk w = fibre_walk<GS>(H.NBrest, tid); w.a < NBIv * H.NBO; w.step(H.NBrest)) {
-                        const int iv = fdiv(w.a, H.NBO, H.nbOmag), ko = w.a - iv * H.NBO;
-                        Y[w.a * H.NBrest + w.c] += WoB[ko] * cur[iv * H.NBrest + w.c];
+                if (sliced) {
+                    // Y[ko][rest][payload] (+)= WoB[ko] cur[rest][payload]
+                    const int nrest = H.NBrest * Pl;
+                    for (int e = tid; e < nrest; e += GS) {
+                        const T c = cur[e];
+                        for (int ko = 0; ko < H.NBO; ko++) {
+                            T *yp = Y + (size_t)ko * nrest + e;
+                            *yp = sl == 0 ? WoB[ko] * c : fma_t(WoB[ko], c, *yp);
+                        }
                     }
+                    gsync<GS>();
                 } else {
-                    for (int e = tid; e < NB * vb; e += GS) Y[e] += cur[e];
+                    F = cur;
                 }
-                gsync<GS>();
             }
+            if (sliced) F = Y;
         }
-        // exact compress-add of D_l * y_l
-        switch (vb) {
-#define SG_VB(VB) case VB: chunk_out<T, VB, GS>(H, P, rk, maxbits + v0, accp + (size_t)v0 * P.n_cs * fx::Acc<T>::words, Y, tid); break;
-            SG_VB(1) SG_VB(2) SG_VB(3) SG_VB(4) SG_VB(5) SG_VB(6) SG_VB(7) SG_VB(8)
-#undef SG_VB
-        }
+        // basis part of the outer positions and exact compress-add of D_l * y_l
+        unsigned long long *acc = accp + (size_t)v0 * P.n_cs * fx::Acc<T>::words;
+        if (WW == U) combine_add<T, U, GS>(H, P, rk, maxbits + v0, acc, X, F, mats, vb, tid);
+        else combine_add<T, 1, GS>(H, P, rk, maxbits + v0, acc, X, F, mats, vb, tid);
+        gsync<GS>();
     }
 }
 
 // Terms [p0, p0 + pcount) of one problem's processing order; NG = 128 / GS
 // term groups per block.
-template <typename T, int NB1, int NQ1, int RMAX, bool UNI, int GS>
+template <typename T, int GS>
 __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? SG_F32_MINBLOCKS : SG_F64_MINBLOCKS)
     k_apply_fast(const KParams P, const double *__restrict__ x, const long long *__restrict__ maxbits, int nvec,
                  int p0, int pcount, int work_cap)
@@ -625,17 +698,16 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? SG_F32_MINBLOCKS : SG_F6
     const int grp = threadIdx.x / GS, tid = threadIdx.x % GS;
     const int pidx = blockIdx.x * NG + grp;
     if (pidx >= pcount) return;
-    fast_term<T, NB1, NQ1, RMAX, UNI, GS>(P, x, P.acc, maxbits, nvec, p0 + pidx, work_cap,
-                                          smraw + (size_t)grp * part_bytes(P, sizeof(T), work_cap), Hs[grp],
-                                          tid);
+    fast_term<T, GS>(P, x, P.acc, maxbits, nvec, p0 + pidx, work_cap,
+                     smraw + (size_t)grp * part_bytes(P, sizeof(T), work_cap), Hs[grp], tid);
 }
 
 // Many problems in one launch: work item i = (problem, processing position);
 // items come ordered by estimated cost over all problems.  Problem j's
 // vectors, accumulators and exponents start at nvec * cs_prefix[j] (times
-// kAccDigits for the accumulators) and j * nvec.  Every group's shared-memory
-// partition is `part` bytes, the largest over the problems.
-template <typename T, int NB1, int NQ1, int RMAX, bool UNI, int GS>
+// the accumulator words for the accumulators) and j * nvec.  Every group's
+// shared-memory partition is `part` bytes, the largest over the problems.
+template <typename T, int GS>
 __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? SG_F32_MINBLOCKS : SG_F64_MINBLOCKS)
     k_apply_fast_batch(const KParams *__restrict__ kps, const int2 *__restrict__ items, int count,
                        const double *__restrict__ x, unsigned long long *acc,
@@ -651,9 +723,8 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? SG_F32_MINBLOCKS : SG_F6
     const int2 it = items[pidx];
     const KParams &P = kps[it.x];
     const size_t off = (size_t)nvec * (size_t)cs_prefix[it.x];
-    fast_term<T, NB1, NQ1, RMAX, UNI, GS>(P, x + off, acc + off * fx::Acc<T>::words, maxbits + (size_t)it.x * nvec, nvec,
-                                          it.y, GS == kFT ? P.fast.work_cta : P.fast.work_warp,
-                                          smraw + (size_t)grp * part, Hs[grp], tid);
+    fast_term<T, GS>(P, x + off, acc + off * fx::Acc<T>::words, maxbits + (size_t)it.x * nvec, nvec, it.y,
+                     GS == kFT ? P.fast.work_cta : P.fast.work_warp, smraw + (size_t)grp * part, Hs[grp], tid);
 }
 
 // Sets a kernel's dynamic shared-memory limit to the most the device allows
@@ -673,72 +744,45 @@ cudaError_t set_smem_limit(K kernel, size_t need)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
 }
 
-template <typename T, int NB1, int NQ1, int RMAX, bool UNI>
+template <typename T>
 cudaError_t launch_t(const KParams &kp, const FastLaunch &a)
 {
     const size_t rb = sizeof(T);
     const size_t smem_cta = part_bytes(kp, rb, kp.fast.work_cta);
     const size_t smem_warp = (size_t)(kFT / 32) * part_bytes(kp, rb, kp.fast.work_warp);
     if (a.configure) {
-        cudaError_t e = set_smem_limit(k_apply_fast<T, NB1, NQ1, RMAX, UNI, kFT>, smem_cta);
+        cudaError_t e = set_smem_limit(k_apply_fast<T, kFT>, smem_cta);
         if (e != cudaSuccess) return e;
-        return set_smem_limit(k_apply_fast<T, NB1, NQ1, RMAX, UNI, 32>, smem_warp);
+        return set_smem_limit(k_apply_fast<T, 32>, smem_warp);
     }
     const int nbig = kp.fast.n_big, nrest = (int)kp.n_terms - nbig;
     if (nbig > 0)
-        k_apply_fast<T, NB1, NQ1, RMAX, UNI, kFT><<<(unsigned)nbig, kFT, smem_cta, a.stream>>>(
-            kp, a.x, a.maxbits, a.nvec, 0, nbig, kp.fast.work_cta);
+        k_apply_fast<T, kFT><<<(unsigned)nbig, kFT, smem_cta, a.stream>>>(kp, a.x, a.maxbits, a.nvec, 0, nbig,
+                                                                        kp.fast.work_cta);
     if (nrest > 0) {
         const unsigned blocks = (unsigned)((nrest + kFT / 32 - 1) / (kFT / 32));
-        k_apply_fast<T, NB1, NQ1, RMAX, UNI, 32><<<blocks, kFT, smem_warp, a.stream>>>(
-            kp, a.x, a.maxbits, a.nvec, nbig, nrest, kp.fast.work_warp);
+        k_apply_fast<T, 32><<<blocks, kFT, smem_warp, a.stream>>>(kp, a.x, a.maxbits, a.nvec, nbig, nrest,
+                                                                kp.fast.work_warp);
     }
     return cudaGetLastError();
 }
 
-template <typename T, int NB1, int NQ1, int RMAX, bool UNI>
+template <typename T>
 cudaError_t batch_t(const FastBatchLaunch &a)
 {
     constexpr int NG = kFT / 32;
     if (a.configure) {
-        cudaError_t e = set_smem_limit(k_apply_fast_batch<T, NB1, NQ1, RMAX, UNI, kFT>, (size_t)a.part[0]);
+        cudaError_t e = set_smem_limit(k_apply_fast_batch<T, kFT>, (size_t)a.part[0]);
         if (e != cudaSuccess) return e;
-        return set_smem_limit(k_apply_fast_batch<T, NB1, NQ1, RMAX, UNI, 32>, (size_t)NG * a.part[1]);
+        return set_smem_limit(k_apply_fast_batch<T, 32>, (size_t)NG * a.part[1]);
     }
     if (a.count[0] > 0)
-        k_apply_fast_batch<T, NB1, NQ1, RMAX, UNI, kFT><<<(unsigned)a.count[0], kFT, (size_t)a.part[0], a.stream>>>(
+        k_apply_fast_batch<T, kFT><<<(unsigned)a.count[0], kFT, (size_t)a.part[0], a.stream>>>(
             a.kps, a.items[0], a.count[0], a.x, a.acc, a.maxbits, a.cs_prefix, a.nvec, a.part[0]);
     if (a.count[1] > 0)
-        k_apply_fast_batch<T, NB1, NQ1, RMAX, UNI, 32>
-            <<<(unsigned)((a.count[1] + NG - 1) / NG), kFT, (size_t)NG * a.part[1], a.stream>>>(
-                a.kps, a.items[1], a.count[1], a.x, a.acc, a.maxbits, a.cs_prefix, a.nvec, a.part[1]);
+        k_apply_fast_batch<T, 32><<<(unsigned)((a.count[1] + NG - 1) / NG), kFT, (size_t)NG * a.part[1], a.stream>>>(
+            a.kps, a.items[1], a.count[1], a.x, a.acc, a.maxbits, a.cs_prefix, a.nvec, a.part[1]);
     return cudaGetLastError();
-}
-
-template <typename T_, int NB1_, int NQ1_, int RMAX_, bool UNI_>
-struct Variant {
-    using T = T_;
-    static constexpr int NB1 = NB1_, NQ1 = NQ1_, RMAX = RMAX_;
-    static constexpr bool UNI = UNI_;
-};
-
-// Calls f(Variant<...>{}) for the kernel variant of kp's fast tables.  The
-// register-slot count must be fast_rmax(...): the host built the records with it.
-template <typename T, bool UNI, typename F>
-cudaError_t for_variant_u(const KParams &kp, F &&f)
-{
-    constexpr bool F32 = sizeof(T) == 4;
-    const int nb1 = kp.fast.nb1, nq1 = kp.fast.nq1;
-    if (nb1 == 2 && nq1 == 3) return f(Variant<T, 2, 3, F32 ? SG_F32_RMAX2 : SG_F64_RMAX2, UNI>{});
-    if (nb1 == 2 && nq1 == 2) return f(Variant<T, 2, 2, F32 ? SG_F32_RMAX2 : SG_F64_RMAX2, UNI>{});
-    if (nb1 == 3 && nq1 == 3) return f(Variant<T, 3, 3, F32 ? SG_F32_RMAX3 : 1, UNI>{});
-    return f(Variant<T, 1, 1, 0, UNI>{});
-}
-
-template <typename T, typename F>
-cudaError_t for_variant(const KParams &kp, F &&f)
-{
-    return kp.fast.uni1 ? for_variant_u<T, true>(kp, f) : for_variant_u<T, false>(kp, f);
 }
 
 }  // namespace

@@ -3,12 +3,6 @@
 
 namespace sg {
 
-cudaError_t fast_batch_launch_f32(const KParams &kp_any, const FastBatchLaunch &a)
-{
-    return for_variant<float>(kp_any, [&](auto v) {
-        using V = decltype(v);
-        return batch_t<float, V::NB1, V::NQ1, V::RMAX, V::UNI>(a);
-    });
-}
+cudaError_t fast_batch_launch_f32(const KParams &, const FastBatchLaunch &a) { return batch_t<float>(a); }
 
 }  // namespace sg

@@ -3,12 +3,6 @@
 
 namespace sg {
 
-cudaError_t fast_launch_f64(const KParams &kp, const FastLaunch &a)
-{
-    return for_variant<double>(kp, [&](auto v) {
-        using V = decltype(v);
-        return launch_t<double, V::NB1, V::NQ1, V::RMAX, V::UNI>(kp, a);
-    });
-}
+cudaError_t fast_launch_f64(const KParams &kp, const FastLaunch &a) { return launch_t<double>(kp, a); }
 
 }  // namespace sg

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -41,18 +42,9 @@ __host__ __device__ constexpr int acc_words(bool fp32) { return fp32 ? 1 : kAccD
 
 constexpr int kMaxPairs = 64;  // coupled mode pairs handled by the fast path
 
-// Number of level-1 slots the fast kernel keeps in registers ("inner" slots);
-// the host descriptor builder and the kernel dispatch both use this.
-// Tuning of the fast kernels (FP32 / FP64): register-slot counts for level-1
-// slots of 2 functions and of 3 functions, the shared-memory budget per block
-// that the host plans terms with, the resident blocks per SM the kernels are
-// compiled for, and the vectors per chunk below which a term is sliced.
-#ifndef SG_F32_RMAX2
-#define SG_F32_RMAX2 2
-#endif
-#ifndef SG_F32_RMAX3
-#define SG_F32_RMAX3 2
-#endif
+// Tuning of the fast kernels (FP32 / FP64): the shared-memory budget per
+// block that the host plans terms with, the resident blocks per SM the kernels
+// are compiled for, and the vectors per chunk below which a term is sliced.
 #ifndef SG_F32_SMEM_KB
 #define SG_F32_SMEM_KB 52
 #endif
@@ -65,9 +57,6 @@ constexpr int kMaxPairs = 64;  // coupled mode pairs handled by the fast path
 #ifndef SG_F64_SLICE_VT
 #define SG_F64_SLICE_VT 4
 #endif
-#ifndef SG_F64_RMAX2
-#define SG_F64_RMAX2 2
-#endif
 #ifndef SG_F64_SMEM_KB
 #define SG_F64_SMEM_KB 106
 #endif
@@ -75,17 +64,41 @@ constexpr int kMaxPairs = 64;  // coupled mode pairs handled by the fast path
 #define SG_F64_MINBLOCKS 2
 #endif
 
-inline int fast_rmax(bool fp32, int nb1, int nq1)
+// Inner positions of the fast kernel: up to fast_rmax level-1 modes whose
+// action at each outer grid point is tabulated per term (inner-block table,
+// NBI = nb1^R <= 9 values per inner block).  Level 1 must have the same basis
+// size nb1 in every mode (2 or 3); otherwise no position is inner.
+inline int fast_inner_nb(int nb1) { return nb1 == 2 || nb1 == 3 ? nb1 : 1; }
+inline int fast_rmax(int nb1) { return nb1 == 2 ? 3 : nb1 == 3 ? 2 : 0; }
+
+// Sizes shared by the host planner and the fast kernels.
+// Padding of a buffer of n elements to a multiple of u elements (16 bytes).
+__host__ __device__ inline int64_t pad_elems(int64_t n, int u) { return (n + u - 1) / u * u; }
+// Work-area elements a chunk of vb vectors of one term needs: the gathered
+// basis tensor X (and the slice accumulator Y when the term is sliced), and
+// two buffers of the largest grid stage when the term has a grid; every
+// buffer padded to 16 bytes (u elements).
+__host__ __device__ inline int64_t chunk_need(int64_t NB, int64_t stage, bool sliced, bool grid, int vb, int u)
 {
-    if (nb1 == 2 && (nq1 == 3 || nq1 == 2)) return fp32 ? SG_F32_RMAX2 : SG_F64_RMAX2;
-    if (nb1 == 3 && nq1 == 3) return fp32 ? SG_F32_RMAX3 : 1;
-    return 0;
+    return (sliced ? 2 : 1) * pad_elems(NB * vb, u) + (grid ? 2 * pad_elems(stage * vb, u) : 0);
+}
+// Inner-block table per outer grid point: the upper triangle of the NBI x NBI
+// symmetric block (NBI (NBI+1)/2 values, row by row) in units of mt_unit
+// elements (16 bytes, or one element when NBI = 1).
+__host__ __device__ inline int mt_unit(int NBI, int u) { return NBI == 1 ? 1 : u; }
+__host__ __device__ inline int mt_units(int NBI, int u)
+{
+    const int ue = mt_unit(NBI, u);
+    return (NBI * (NBI + 1) / 2 + ue - 1) / ue;
 }
 
 // Per-term record of the fast kernel, in processing order, 16-byte units:
 // header | positions[m] | active pairs[npair] | induced matrices[nind] (padded).
 // Positions: the inner slots (mode order) first, then the outer slots in the
 // order of fewest multiply-adds (ascending 1/nb - 1/nq, ties in mode order).
+// Induced matrices: the two-mode monomials whose partner mode is collapsed,
+// per position (summed into the term image's H1; listed for the inner-block
+// tables).
 struct alignas(16) FDescHdr {
     int m, R, NB, coef;          // positions, inner positions, basis size, D_l
     int s, npair, nind, gsize;   // slicing depth, active pairs, induced matrices, G-table words
@@ -104,7 +117,6 @@ static_assert(sizeof(FDescHdr) == 48 && sizeof(FDescPos) == 16 && sizeof(FDescPa
 struct FastParams {
     int enabled;
     int nb1, nq1;          // uniform sizes of level 1 (0 if modes differ)
-    int uni1;              // 1 if every mode has the same level-1 tables B, B^T W
     int npairs;            // coupled mode pairs (i < i')
     const int *pair_modes; // [npairs][2]
     const int *h1off;      // [D][L+1]: single-mode matrix (nb x nb) of an active level
@@ -130,11 +142,12 @@ struct FastParams {
     const double *imgd;        // FP64 contexts
     const float *imgf;         // FP32 contexts
     const long long *img_off;  // [n_terms + 1] image starts, in elements
-    // the coupling potential on each term's collapsed grid, evaluated once per
-    // context in the term kernel's layout [slice][inner grid point][outer grid point]
-    const double *vtabd;       // FP64 contexts
-    const float *vtabf;        // FP32 contexts
-    const long long *vt_off;   // [n_terms + 1] starts, in elements (0-size for terms without a grid)
+    // inner-block tables: per term with coupled pairs, the action of its inner
+    // positions at every outer grid point (symmetric NBI x NBI, upper triangle),
+    // formed once per context; layout [slice][unit][outer grid point][unit elements]
+    const double *mtabd;       // FP64 contexts
+    const float *mtabf;        // FP32 contexts
+    const long long *mt_off;   // [n_terms + 1] starts, in elements (16-byte aligned; 0-size without a grid)
 };
 
 // Everything a kernel needs, passed by value.
@@ -195,14 +208,14 @@ struct HostTables {
     std::vector<double> esplit;      // [n_cs]
     // fast path
     bool fast = false;
-    int nb1 = 0, nq1 = 0, uni1 = 0;
+    int nb1 = 0, nq1 = 0;
     std::vector<int> pair_modes, h1off, goff, ioff, soff, spoff;
     std::vector<double> ftab, fsc;
     double c0const = 0.0;
     int fast_cap = 0, fast_maxnb = 0, fast_matcap = 0;
     std::vector<double> fimg;         // per-term shared-memory images (see FastParams)
     std::vector<long long> fimg_off;  // [n_terms + 1]
-    std::vector<long long> fvt_off;   // [n_terms + 1] potential-table starts (see FastParams)
+    std::vector<long long> fvt_off;   // [n_terms + 1] inner-block table starts (see FastParams::mt_off)
     std::vector<int4> fdesc;          // term records
     std::vector<unsigned> fdesc_off;  // [n_terms+1]
     int64_t franks = 0;               // total compact indices (N_s)
@@ -231,8 +244,8 @@ cudaError_t configure_kernels(size_t smem_bytes, bool fp32);
 std::string build_fast_tables(const Problem &p, HostTables *T);
 std::string build_fast_descs(const Problem &p, bool fp32, HostTables *T, int fbudget, int rb);
 cudaError_t launch_build_ranks(const KParams &kp, int *ranks, cudaStream_t stream);
-// Fills the per-term potential tables (FastParams::vtab*) from the term images and records.
-cudaError_t launch_build_vtab(const KParams &kp, bool fp32, cudaStream_t stream);
+// Fills the inner-block tables (FastParams::mtab*) from the records and the FP64 tables.
+cudaError_t launch_build_mtab(const KParams &kp, bool fp32, cudaStream_t stream);
 size_t fast_smem_bytes(const KParams &kp, bool fp32);
 cudaError_t configure_fast_kernels(const KParams &kp, bool fp32);
 cudaError_t launch_apply_fast(const KParams &kp, bool fp32, const double *x, int nvec,
@@ -263,6 +276,13 @@ cudaError_t launch_cheb_iteration(ChebState *st, const long long *prefix, int ni
                                   const double *X, const double *Y, double *P, double *A, cudaStream_t s);
 // Chebyshev spectral interval of a context's H_S (Krylov, as sg_propagate); synchronous.
 sg_status chebyshev_bounds(sg_ctx *ctx, cudaStream_t stream, double *emin, double *emax);
+// Block Davidson of sg_eigs (method SG_DAVIDSON, same start block and
+// iteration) with every application of H_S done by `apply` (x, y device, r
+// vectors; x is ready when it is called, y must be complete when it returns).
+// Vector algebra runs on `stream`.  nconv receives the converged pairs.
+using ApplyFn = std::function<sg_status(const double *x, double *y, int r)>;
+sg_status davidson_routed(sg_ctx *ctx, cudaStream_t stream, const ApplyFn &apply, int nev, int block, double tol,
+                          int max_it, double *evals, double *resid, double *evecs, int *nconv, std::string *err);
 // J_0..J_kmax at x (Miller's backward recurrence).
 std::vector<double> bessel_j(int kmax, double x);
 // Device bytes sg_create would allocate for a planned context (tables, records, M^B).

@@ -1,5 +1,6 @@
-// Propagation server (declared in include/smolyak.h): continuous batching of
-// Chebyshev propagation requests of different D, L and basis sizes.
+// Request server (declared in include/smolyak.h): continuous batching of
+// Chebyshev propagation requests and block-Davidson eigen requests of
+// different D, L and basis sizes.
 //
 // Each engine iteration
 //   1. retires requests whose last step has ended (psi and logs to the host),
@@ -16,14 +17,26 @@
 // applies are bitwise those of the request's own context, the update is
 // elementwise, the logged sums run over the request's own entries in a fixed
 // order), so its results do not depend on the mix.
+//
+// Eigen requests: each runs the block Davidson of sg_eigs on a host thread of
+// its own, with its vector algebra on its own stream.  Its applications of
+// H_S are handed to the engine: a request's block occupies (block + 1) / 2
+// two-vector slots of the batch (its context repeated), so every engine
+// iteration applies the waiting blocks of all eigen requests together with
+// the propagation requests' Chebyshev vectors in one batched apply.  While
+// eigen requests are active the engine runs one iteration at a time (it
+// waits for their blocks); otherwise pairs of iterations replay as a graph.
 #include <algorithm>
 #include <chrono>
 #include <climits>
 #include <cmath>
+#include <condition_variable>
 #include <deque>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "sg_internal.h"
@@ -36,8 +49,13 @@ double now_s()
     return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
 
+enum ReqKind { kProp = 0, kEig = 1 };
+// phases of an eigen request's hand-off with the engine
+enum EigPhase { kRunning = 0, kPosted = 1, kApplied = 2, kFinished = 3 };
+
 struct Req {
     int64_t id = 0;
+    int kind = kProp;
     int state = SG_REQ_QUEUED;
     // problem (deep copy of the request)
     int D = 0, L = 0;
@@ -62,6 +80,18 @@ struct Req {
     std::vector<double> psi, log;
     double t_submit = 0, t_admit = 0, t_done = 0;
     std::string error;
+    // eigen requests
+    int nev = 0, block = 0, eig_max_it = 0, want_vectors = 0;
+    double tol = 0;
+    int nslots = 1;            // two-vector batch slots (propagation: 1)
+    std::thread worker;
+    int phase = kRunning;      // guarded by the server's mutex
+    const double *ex = nullptr;
+    double *ey = nullptr;
+    int er = 0;                // vectors of the posted block
+    sg_status apply_status = SG_OK, eig_status = SG_OK;
+    int nconv = 0;
+    std::vector<double> evals, resid, evecs;
 };
 
 }  // namespace
@@ -89,6 +119,10 @@ struct sg_server {
     const double *graph_x[2] = {nullptr, nullptr};
     int64_t iterations = 0, applications = 0;
     std::string last_error;
+    // hand-off with the eigen requests' threads
+    std::mutex mu;
+    std::condition_variable cv;
+    bool aborting = false;
 };
 
 namespace {
@@ -119,6 +153,7 @@ void free_state(sg_server *s)
 
 void release(sg_server *s, Req *r)
 {
+    if (r->worker.joinable()) r->worker.join();
     if (r->ctx) sg_destroy(r->ctx);
     r->ctx = nullptr;
     if (r->d_log) cudaFree(r->d_log);

@@ -427,20 +427,6 @@ std::string build_fast_tables(const Problem &p, HostTables *Tp)
         for (int i = 1; i < D; i++)
             if (LI(i, 1).nb != T.nb1 || LI(i, 1).nq != T.nq1) { T.nb1 = T.nq1 = 0; break; }
     }
-    // identical level-1 tables in every mode (lets the kernel keep one copy in registers)
-    T.uni1 = 0;
-    if (T.nb1 > 0) {
-        T.uni1 = 1;
-        const LevelInfo &l0 = LI(0, 1);
-        for (int i = 1; i < D && T.uni1; i++) {
-            const LevelInfo &li = LI(i, 1);
-            for (int e = 0; e < l0.nb * l0.nq; e++)
-                if (td[li.offB + e] != td[l0.offB + e] || td[li.offBW + e] != td[l0.offBW + e]) {
-                    T.uni1 = 0;
-                    break;
-                }
-        }
-    }
     // coupled pairs
     std::vector<int> pidx((size_t)D * D, -1);
     T.pair_modes.clear();
@@ -556,11 +542,12 @@ void put(std::vector<int4> &v, size_t unit, size_t byte, const S &x)
 }  // namespace
 
 // Per-term records of the fast kernel (processing order).  For every term:
-// the transformed modes ("positions", the last fast_rmax level-1 modes first as
-// inner register slots, then the others, each group in mode order) with the
-// offsets of their tables, the term constant c0, the active coupled pairs with
-// the offsets of their G tables, the induced single-mode matrices, and the
-// slicing depth for its kernel.  The most expensive terms (a prefix of the
+// the transformed modes ("positions": for a term with coupled pairs, the last
+// fast_rmax level-1 modes first as inner positions, whose action is tabulated
+// per outer grid point; then the outer positions in the order of fewest
+// multiply-adds) with the offsets of their tables, the term constant c0, the
+// active coupled pairs with the offsets of their G tables, the induced
+// single-mode matrices, and the slicing depth for its kernel.  The most expensive terms (a prefix of the
 // processing order) run one per thread block; the small ones at its tail run
 // one per warp, four per block, in a quarter of the block's shared memory
 // each (a term goes to the warp form when a chunk of 4 vectors fits that
@@ -569,7 +556,8 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
 {
     HostTables &T = *Tp;
     const int D = p.D, L = p.L, Lp = L + 1;
-    const int RMAX = fast_rmax(fp32, T.nb1, T.nq1);
+    const int RMAX = fast_rmax(T.nb1);
+    const int U = 16 / rb;  // elements per 16 bytes
     const int np = (int)T.pair_modes.size() / 2;
     auto LI = [&](int i, int l) -> const LevelInfo & { return T.lvl[(size_t)i * Lp + l]; };
 
@@ -593,8 +581,14 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
             if (li.nb > 1) { act[na] = i; l1[na] = li.nb == T.nb1 && li.nq == T.nq1; inner[na] = false; na++; }
             else c0 += T.fsc[T.soff[(size_t)i * Lp + lt[i]]];
         }
+        // the term has a grid when some coupled pair has both modes transformed;
+        // only then are level-1 modes made inner positions
+        bool has_grid = false;
+        for (int P = 0; P < np && !has_grid; P++)
+            has_grid = LI(T.pair_modes[2 * P], lt[T.pair_modes[2 * P]]).nb > 1 &&
+                       LI(T.pair_modes[2 * P + 1], lt[T.pair_modes[2 * P + 1]]).nb > 1;
         int R = 0;
-        for (int a = na - 1; a >= 0 && R < RMAX; a--)
+        for (int a = na - 1; a >= 0 && R < (has_grid ? RMAX : 0); a--)
             if (l1[a]) { inner[a] = true; R++; }
         int pos = 0;
         for (int a = 0; a < na; a++) if (inner[a]) { pos_of_mode[act[a]] = pos; tp.posmode[pos++] = act[a]; }
@@ -647,11 +641,11 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
     // target's vectors per chunk (else half as many, ...)
     const int vt0 = T.slice_vt > 0 ? T.slice_vt : fp32 ? SG_F32_SLICE_VT : SG_F64_SLICE_VT;
     auto depth_for = [&](int t, const TermPlan &tp, int64_t work, int smax) {
-        if (2 * tp.NB > work) return -1;
+        if (chunk_need(tp.NB, 0, false, false, 1, U) > work) return -1;
         if (!tp.grid) return 0;
         for (int vt = vt0; vt >= 1; vt /= 2)
             for (int s = 0; s <= std::min(smax, tp.na - tp.R); s++)
-                if ((2 * tp.NB + 2 * stage_of(t, tp, s)) * vt <= work) return s;
+                if (chunk_need(tp.NB, stage_of(t, tp, s), s > 0, true, vt, U) <= work) return s;
         return -1;
     };
 
@@ -692,7 +686,7 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
     for (int64_t q = 0; q < T.n_terms; q++) {
         plan_term(T.order[q], tp);
         bool ok = work_warp > 0 &&
-                  (2 * tp.NB + (tp.grid ? 2 * stage_of(T.order[q], tp, 0) : 0)) * 4 <= work_warp &&
+                  chunk_need(tp.NB, tp.grid ? stage_of(T.order[q], tp, 0) : 0, false, tp.grid, 4, U) <= work_warp &&
                   (size_t)work_warp * rb >= 16 * (3 + (size_t)tp.na + tp.prs.size() + (tp.inds.size() + 1) / 2);
         if (!ok) n_big = q + 1;
     }
@@ -738,14 +732,17 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
         }
         T.fimg_off[q + 1] = (long long)T.fimg.size();
         {
-            long long ng = 0;  // the term's collapsed grid, when it has coupled pairs
+            // inner-block table: its units per outer grid point, over every
+            // outer grid point (all slices), padded to 16 bytes
+            long long sz = 0;
             if (tp.grid) {
-                ng = 1;
-                for (int j = 0; j < na; j++) ng *= LI(tp.posmode[j], lt[tp.posmode[j]]).nq;
+                long long ngo = 1;
+                for (int j = tp.R; j < na; j++) ngo *= LI(tp.posmode[j], lt[tp.posmode[j]]).nq;
+                const int nbi = (int)tp.NBIn;
+                sz = pad_elems((int64_t)mt_units(nbi, U) * mt_unit(nbi, U) * ngo, U);
             }
-            T.fvt_off[q + 1] = T.fvt_off[q] + ng;
+            T.fvt_off[q + 1] = T.fvt_off[q] + sz;
         }
-        tp.inds.clear();  // summed into the image's H1 matrices
         const int units = 3 + na + (int)tp.prs.size() + ((int)tp.inds.size() + 1) / 2;
         const size_t u0 = T.fdesc.size();
         T.fdesc.resize(u0 + units, int4{0, 0, 0, 0});

@@ -65,11 +65,19 @@ struct Solver {
     cudaStream_t s;
     int64_t n;
     DBuf partial, smalls;  // Gram scratch; small device matrices
+    const ApplyFn *apply_fn = nullptr;  // when set, applications of H_S go through it
     Solver(sg_ctx *c, cudaStream_t st, int kmax)
         : ctx(c), s(st), n(c->host.n_cs), partial(gram_partial_doubles(std::max(kmax, 1))),
           smalls((size_t)std::max(kmax, 1) * kBlk * 2 + 64) {}
 
-    void apply(const double *x, double *y, int r) { ckst(sg_apply_H(ctx, x, y, r, s), ctx); }
+    void apply(const double *x, double *y, int r)
+    {
+        if (!apply_fn) { ckst(sg_apply_H(ctx, x, y, r, s), ctx); return; }
+        // the routed apply reads x and writes y outside this stream: order both
+        ck(cudaStreamSynchronize(s), "apply sync");
+        const sg_status st = (*apply_fn)(x, y, r);
+        if (st != SG_OK) throw SolverError{st, "routed apply failed"};
+    }
     // C (ka x kb host, row-major) = A^T B
     std::vector<double> gram(const double *A, int ka, const double *B, int kb)
     {
@@ -467,6 +475,21 @@ sg_status sg_propagate(sg_ctx *ctx, double *psi, double dt, int nsteps, int orde
 }  // extern "C"
 
 namespace sg {
+
+sg_status davidson_routed(sg_ctx *ctx, cudaStream_t stream, const ApplyFn &apply, int nev, int block, double tol,
+                          int max_it, double *evals, double *resid, double *evecs, int *nconv, std::string *err)
+{
+    const int b = block <= 0 ? std::min(nev, kBlk) : std::min(block, kBlk);
+    try {
+        Solver S(ctx, stream, std::max(3 * nev, nev + 6 * b) + 328);
+        S.apply_fn = &apply;
+        *nconv = block_eigs(S, nev, b, true, tol, max_it, nullptr, 0, evals, evecs, resid);
+    } catch (const SolverError &e) {
+        if (err) *err = e.msg;
+        return e.st;
+    }
+    return SG_OK;
+}
 
 sg_status chebyshev_bounds(sg_ctx *ctx, cudaStream_t stream, double *emin, double *emax)
 {

@@ -65,7 +65,7 @@ extern "C" sg_status sg_tune(sg_ctx *ctx, int nvec, int *slice_vt, double *ms_ou
         }
         if ((e = cudaMemcpy(const_cast<int4 *>(ctx->kp.fast.desc), T.fdesc.data(), rec_bytes,
                             cudaMemcpyHostToDevice)) != cudaSuccess ||
-            (e = sg::launch_build_vtab(ctx->kp, ctx->fp32, s)) != cudaSuccess ||  // layout follows the slicing
+            (e = sg::launch_build_mtab(ctx->kp, ctx->fp32, s)) != cudaSuccess ||  // layout follows the slicing
             (e = cudaStreamSynchronize(s)) != cudaSuccess) { st = SG_ECUDA; break; }
         // one untimed apply, then the median of three
         std::vector<float> t;
@@ -88,7 +88,7 @@ extern "C" sg_status sg_tune(sg_ctx *ctx, int nvec, int *slice_vt, double *ms_ou
     T.fast = true;
     cudaError_t e2 = cudaMemcpy(const_cast<int4 *>(ctx->kp.fast.desc), T.fdesc.data(), rec_bytes,
                                 cudaMemcpyHostToDevice);
-    if (e2 == cudaSuccess) e2 = sg::launch_build_vtab(ctx->kp, ctx->fp32, s);
+    if (e2 == cudaSuccess) e2 = sg::launch_build_mtab(ctx->kp, ctx->fp32, s);
     if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
     if (st == SG_OK && e2 != cudaSuccess) { st = SG_ECUDA; e = e2; }
     if (e0) cudaEventDestroy(e0);

@@ -8,20 +8,35 @@ The element-wise form catches a single wrong entry (a mis-ranked compact
 index, a dropped or doubled term) that the 2-norm would dilute by up to
 sqrt(N_cs).
 
-FP64 mode: both <= 1e-12.
+FP64 mode: both <= 1e-12 against an exact reference (the masked-Galerkin
+closed form where it applies).  The literal oracle sums the terms' D_l y_l in
+floating point; at the compact function k = 0, which every term touches, its
+own rounding reaches u * sum_l |D_l| * max|y_l| (u = 2^-53): 3.3e-12 of
+max|y| at D=12 L=5 against the closed form, measured.  Element-wise
+comparisons with the literal oracle therefore allow max(1e-12, u sum_l |D_l|)
+(literal_elem_tol); norm-wise stays 1e-12.
 Mixed mode (FP32 contractions, exact fixed-point sum): every term's result
 carries FP32 rounding (~6e-8 relative) and the combination coefficients D_l
 (Eq. (8); |D_l| up to 462 at D=12) sum those errors over the terms sharing a
 compact function.  The compact function k = 0 lies in every term, so its
 error is the largest: the element-wise measure is looser than the norm-wise
-one.  MIXED_ELEM_TOL is the measured worst case over the parity cases times
-a margin of about ten (values in the test that uses it).
+one.  Measured on GB300 (mixed vs the oracle): element-wise 1.1e-8 (D=2 L=6),
+2.0e-7 (D=6 L=8), 3.0e-7 (D=12 L=5), 1.4e-7 (general polynomial); norm-wise
+at most 1.2e-7.  MIXED_ELEM_TOL = 5e-6 keeps a margin above 15 over them.
 """
 import numpy as np
 
 FP64_TOL = 1e-12
 MIXED_TOL = 5e-6
-MIXED_ELEM_TOL = 5e-5
+MIXED_ELEM_TOL = 5e-6
+
+
+def literal_elem_tol(p):
+    """Element-wise FP64 tolerance against the literal oracle: its own
+    floating-point compress-add bound u * sum_l |D_l| (Eq. (8)), at least 1e-12."""
+    from oracle import oracle as orc
+    _, c = orc.enumerate_terms(p.D, p.L)
+    return max(FP64_TOL, 2.0 ** -53 * float(np.abs(np.asarray(c, float)).sum()))
 
 
 def norm_rel(y, r):

@@ -1,12 +1,15 @@
 """The algorithmic FLOP count behind bench.py's roofline figure, checked on the CPU.
 
-F_alg must describe the route the kernel takes: per term, the forward chain
-of one-mode contractions over the modes with nb > 1 in the order the host
-plans (ascending 1/nb - 1/nq, ties in mode order), the mirrored backward
-chain, the basis-part matrices, one multiply per grid point and the
-compress-add.  Two checks: the vectorised count equals a per-term loop, and
-the planned order is the cheapest of all orders (brute force over
-permutations), which is what the swap argument for that order claims.
+F_alg must describe the route the kernel takes: per term with a grid (two
+neighbouring modes of the chain both transformed), the last three level-1
+modes are inner positions whose block is applied at every outer grid point;
+the forward chain of one-mode contractions over the other modes with nb > 1
+runs in the order the host plans (ascending 1/nb - 1/nq, ties in mode order)
+on NBI values per site, the backward chain mirrors it; then the single-mode
+matrices of the outer modes and the compress-add.  Two checks: the vectorised
+count equals a per-term loop, and the planned order is the cheapest of all
+orders (brute force over permutations), which is what the swap argument for
+that order claims.
 """
 import itertools
 import math
@@ -37,14 +40,26 @@ def planned_order(nbs, nqs):
 
 def term_flops(levels, rule):
     nbA, nbB, nqA, nqB = rule
-    act = [l for l in levels if nbA + nbB * l > 1]
-    nbs = [nbA + nbB * l for l in act]
-    nqs = [nqA + nqB * l for l in act]
+    nb1 = nbA + nbB
+    rmax = 3 if nb1 == 2 else 2 if nb1 == 3 else 0
+    D = len(levels)
+    active = [nbA + nbB * l > 1 for l in levels]
+    grid = any(active[i] and active[i + 1] for i in range(D - 1))
+    inner = set()
+    if grid:
+        for i in range(D - 1, -1, -1):
+            if len(inner) < rmax and levels[i] == 1 and active[i]:
+                inner.add(i)
+    outer = [i for i in range(D) if active[i] and i not in inner]
+    nbs = [nbA + nbB * levels[i] for i in outer]
+    nqs = [nqA + nqB * levels[i] for i in outer]
+    NBI = math.prod(nbA + nbB * levels[i] for i in inner)
     order = planned_order(nbs, nqs)
-    fwd = chain_fmas([nbs[j] for j in order], [nqs[j] for j in order])
-    NB, NG = math.prod(nbs), math.prod(nqs)
-    kin = NB * sum(nbs)
-    return 2 * (2 * fwd + kin) + NG + 2 * NB
+    fwd = chain_fmas([nbs[j] for j in order], [nqs[j] for j in order]) * NBI
+    NB = NBI * math.prod(nbs)
+    reg = math.prod(nqs) * NBI * NBI if grid else 0
+    basis = NB * (sum(nbs) + (0 if grid else 1))
+    return 2 * (2 * fwd + reg + basis) + 2 * NB
 
 
 @pytest.mark.parametrize("rule", [(1, 1, 2, 1), (1, 1, 1, 1), (2, 1, 3, 1), (1, 2, 1, 2)])
@@ -70,9 +85,9 @@ def test_planned_order_is_the_cheapest(rule):
 
 
 def test_benchmark_workload_count():
-    """D=12 L=10, nb = l+1, nq = l+2: 3.70e10 FLOPs per vector in the planned
-    order (the figure the benchmark's roofline uses)."""
+    """D=12 L=10, nb = l+1, nq = l+2: 1.97e10 FLOPs per vector by the kernel's
+    route (the figure the benchmark's roofline uses)."""
     from oracle import oracle as orc
     lv, _ = orc.enumerate_terms(12, 10)
     f = bench.algorithmic_flops_per_vector(np.asarray(lv))
-    assert f == 37029384645
+    assert f == 19703308878

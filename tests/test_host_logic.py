@@ -98,18 +98,46 @@ def test_c3_plan_sizes():
     sg.sg_destroy(ctx)
 
 
+def inner_block_table_elements(levels, u):
+    """Elements of the inner-block tables at nb = l+1, nq = l+2 (chained
+    coupling): per term with two neighbouring transformed modes, the upper
+    triangle of an NBI x NBI block (NBI = 2^R, R = min(3, its level-1 modes))
+    in 16-byte units (one element when NBI = 1) at every outer grid point,
+    padded to 16 bytes per term."""
+    total = 0
+    for l in levels:
+        act = [v > 0 for v in l]
+        if not any(act[i] and act[i + 1] for i in range(len(l) - 1)):
+            continue
+        R = min(3, sum(1 for v in l if v == 1))
+        nbi = 2 ** R
+        ngo = 1
+        n1 = 0
+        for v in l[::-1]:
+            if v == 1 and n1 < R:
+                n1 += 1
+            elif v > 0:
+                ngo *= v + 2
+        ue = 1 if nbi == 1 else u
+        per = -(-(nbi * (nbi + 1) // 2) // ue) * ue
+        total += -(-(per * ngo) // u) * u
+    return total
+
+
 def test_plan_reports_the_device_bytes_of_sg_create():
     """A planned context holds no device memory but reports what sg_create would
-    allocate. At D=12 L=10 that includes M^B (N_s int32) and the coupling
-    potential at every grid point of the coupled terms: 1,248,275,065 points.
-    Both are in the context's precision for the potential, so FP64 needs more."""
+    allocate.  At D=12 L=10 that includes M^B (N_s int32) and the inner-block
+    tables of the terms with a grid, in the context's precision, so FP64 needs
+    more."""
+    from oracle import oracle as orc
+    lv, _ = orc.enumerate_terms(12, 10)
     p = synth.workload_C3()
     sizes = {}
     for prec, rb in (("mixed", 4), ("fp64", 8)):
         ctx = sg.sg_plan(p, prec)
         b = sg.sg_size(ctx)["bytes_device"]
         sg.sg_destroy(ctx)
-        lower = 131128140 * 4 + 1248275065 * rb
-        assert lower <= b <= lower + 3 * 10 ** 9, (prec, b)
+        lower = 131128140 * 4 + inner_block_table_elements(lv.tolist(), 16 // rb) * rb
+        assert lower <= b <= lower + 3 * 10 ** 9, (prec, b, lower)
         sizes[prec] = b
     assert sizes["fp64"] > sizes["mixed"]

@@ -18,13 +18,14 @@ from oracle import galerkin
 from oracle import oracle as orc
 from paper_2111_13655_gb300 import synth
 
-from helpers import FP64_TOL, assert_parity, elem_rel, norm_rel
+from helpers import FP64_TOL, assert_parity, elem_rel, literal_elem_tol, norm_rel
 
 pytestmark = pytest.mark.gpu
 
 # Mixed mode at D=12 L=10, element-wise: the compact functions of small k lie
-# in most of the 646,646 terms and collect their FP32 rounding.
-C3_MIXED_ELEM_TOL = 1e-3
+# in most of the 646,646 terms and collect their FP32 rounding.  Measured on
+# GB300: 1.3e-5 (norm-wise 5.2e-7); the bound keeps a margin of ten.
+C3_MIXED_ELEM_TOL = 1.5e-4
 
 
 def gpu_apply(p, x, precision="fp64", nvec=None):
@@ -66,7 +67,11 @@ def test_fp64_matches_literal_oracle(name):
     x = synth.random_vectors(n, nvec, 1234)
     y_ref = orc.apply_H(p, x)
     y = gpu_apply(p, x, "fp64")
-    assert_parity(y, y_ref, "fp64", name)
+    n, e = norm_rel(y, y_ref), elem_rel(y, y_ref)
+    assert n <= FP64_TOL and e <= literal_elem_tol(p), (name, n, e)
+    if not galerkin.exactness_violations(p):
+        # the exact closed form applies: element-wise 1e-12
+        assert_parity(y, galerkin.apply_H(p, x), "fp64", name + " (masked Galerkin)")
 
 
 @pytest.mark.parametrize("name", ["C1 D=2 L=6 nq=l+1", "C2 D=6 L=8 nq=l+1", "D=12 L=5 nq=l+2",

@@ -63,7 +63,9 @@ def test_server_matches_sg_propagate():
     assert np.max(np.abs(el - el_ref)) < 1e-11
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+# mixed: measured 3.8e-7 on GB300 (FP32 contractions through 50 steps of
+# order-64 Chebyshev); the bound keeps a margin above ten
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 5e-6)])
 def test_request_matches_exact_propagator_of_the_oracle(prec, tol):
     """A D=6 L=8 coupled request (the 6D propagation configuration, 50 steps of
     0.1) against psi(t) = exp(-i H_S t) psi(0) from the literal oracle's dense
