@@ -208,27 +208,45 @@ void sg_batch_destroy(sg_batch *b);
 /*
  * sg_tune -- measured choice of the term schedule of a context's fast path
  * (no counterpart in the paper, whose scheme balances MPI ranks by timing).
- * A term whose grid leaves room for fewer than `slice_vt` vectors per chunk
- * is sliced over its leading outer positions, else it runs unsliced in more,
- * smaller chunks; the best target depends on the problem's term shapes and on
- * the vectors per apply.  sg_tune re-plans the context for slice_vt = 1, 2, 4,
- * times nvec-vector applies of each (median of three after one warm-up) on
- * `stream` and keeps the fastest.  Only the slicing depths of the term
- * records change; results change by rounding only.  Synchronous; allocates
- * and frees 2 * nvec * N_cs doubles of scratch.  No other work may use the
- * context meanwhile; batches made from it before or after see the tuned plan.
- *   nvec 1..64; slice_vt (out, may be NULL): the target kept (0 when the
- *   context uses the generic kernel, which has no schedule to choose);
+ * Three knobs of the plan are searched one after another, each candidate
+ * timed on nvec-vector applies (median of three after one warm-up) on
+ * `stream`, the fastest kept:
+ *   - the slicing target (1, 2, 4): a term whose grid leaves room for fewer
+ *     than that many vectors per chunk is sliced over its leading outer
+ *     positions, else it runs unsliced in more, smaller chunks;
+ *   - the block/warp split (1, 2, 4): terms that fit a quarter of a block's
+ *     shared memory with that many vectors per chunk run one per warp;
+ *   - the shared-memory budget of a block, in KB (52, 70, 104 for SG_MIXED;
+ *     70, 104 for SG_FP64): more vectors per chunk, fewer resident blocks.
+ * Only the term records, the split and the work-area capacities change;
+ * results change by rounding only.  Synchronous; allocates and frees
+ * 2 * nvec * N_cs doubles of scratch.  No other work may use the context
+ * meanwhile.  A batch made from the context before sg_tune refuses to apply
+ * (SG_EINVAL) until it is recreated.
+ *   nvec 1..64; slice_vt (out, may be NULL): the slicing target kept (0 when
+ *   the context uses the generic kernel, which has no schedule to choose);
  *   ms (out, may be NULL): its time per apply.
+ * sg_tune_plan -- the plan a context uses now (tuned or default): slicing
+ *   target, block/warp split, shared-memory budget in KB (zeros for the
+ *   generic kernel).  Any pointer may be NULL.
  */
 sg_status sg_tune(sg_ctx *ctx, int nvec, int *slice_vt, double *ms, void *stream);
+sg_status sg_tune_plan(const sg_ctx *ctx, int *slice_vt, int *warp_vt, int *smem_kb);
 
 /*
- * Propagation server: continuous batching of Chebyshev propagation requests
- * (the propagator of sg_propagate: Sec. 3, Sec. 5) of different D, L and
- * basis sizes on one device.  Single-threaded: the caller submits requests
- * and drives the engine with sg_server_progress; all calls on one server from
- * one host thread at a time, with the server's device current.
+ * Request server: continuous batching of Chebyshev propagation requests
+ * (the propagator of sg_propagate: Sec. 3, Sec. 5) and eigen requests (the
+ * block Davidson of sg_eigs: Sec. 3, Sec. 4) of different D, L and basis
+ * sizes on one device.  The caller submits requests and drives the engine
+ * with sg_server_progress; all calls on one server from one host thread at a
+ * time, with the server's device current.  Each eigen request runs its
+ * solver on a host thread of its own (vector algebra on its own stream); its
+ * block applications of H_S are handed to the engine, whose iterations then
+ * apply every waiting block and every propagation request's Chebyshev vector
+ * in one sg_apply_H_batch (an eigen block occupies (block + 1) / 2 two-vector
+ * slots of the batch).  With eigen requests active an iteration waits (at
+ * most 600 s, else SG_ETIMEOUT) until each has handed over its next block or
+ * finished.
  *
  * Each engine iteration retires finished requests, admits queued requests
  * first come first served while their planned device memory fits the budget,
@@ -250,15 +268,26 @@ sg_status sg_tune(sg_ctx *ctx, int nvec, int *slice_vt, double *ms, void *stream
  *   N_cs from sg_plan + sg_size, compact order) or, if psi0 is NULL, the real
  *   product state of `factors` (as sg_product_state, leading dimension ld).
  *   Logs: <psi|psi> and <psi|H psi>/<psi|psi> at the start of each step.
+ * sg_server_submit_eigs -- copies and plans an eigen request and queues it;
+ *   SG_EBUDGET if it alone needs more than the budget (context tables, M^B,
+ *   its batch slots, the Davidson basis of max(3 nev, nev + 6 block) vectors
+ *   and its images, Ritz vectors, eigenvectors).
  * sg_server_progress -- runs up to max_iters engine iterations (fewer if
  *   nothing is active); returns the numbers of active and queued requests.
  *   Synchronous.
- * sg_server_query -- state (sg_request_state), N_cs and steps done of a request.
+ * sg_server_query -- state (sg_request_state), N_cs and steps done of a
+ *   request (for an eigen request: block applications so far).
  * sg_server_result -- a finished request's psi (host, 2 * N_cs), logs (host,
  *   nsteps each), times[0] = admission - submission, times[1] = completion -
  *   submission (seconds, steady clock); any output may be NULL.
+ * sg_server_eig_result -- a finished eigen request's eigenvalues (host, nev,
+ *   ascending), residual norms (host, nev), eigenvectors (host, nev * N_cs,
+ *   only if the request asked for them), times as sg_server_result, and the
+ *   number of converged pairs; any output may be NULL.  Returns SG_ENOCONV
+ *   (outputs written) when fewer than nev pairs converged in max_it.
  * sg_server_stats -- engine iterations, real-vector applications of H_S so far
- *   (2 per active request per iteration), planned bytes of the active requests.
+ *   (2 per propagation request per iteration, the vectors of each eigen block),
+ *   planned bytes of the active requests.
  */
 typedef struct sg_server sg_server;
 typedef enum { SG_REQ_QUEUED = 0, SG_REQ_ACTIVE = 1, SG_REQ_DONE = 2, SG_REQ_FAILED = 3 } sg_request_state;
@@ -273,12 +302,30 @@ typedef struct {
     double dt;
     int nsteps, order;         /* steps of length dt; Chebyshev order (reduced as in sg_propagate) */
 } sg_prop_request;
+/* Eigen request: the nev lowest eigenpairs of H_S by the block Davidson of
+ * sg_eigs (method SG_DAVIDSON; Sec. 3's time-independent solver), block 1..8
+ * (<= 0: min(nev, 8)), convergence ||H x - theta x|| <= tol max(1, |theta|),
+ * at most max_it iterations; want_vectors != 0 keeps the eigenvectors for
+ * sg_server_eig_result. */
+typedef struct {
+    int D, L;
+    const sg_basis *basis;     /* D entries */
+    const sg_grid *grids;      /* D entries */
+    const sg_hamiltonian *H;
+    int nev, block;
+    double tol;
+    int max_it;
+    int want_vectors;
+} sg_eig_request;
 sg_status sg_server_create(sg_precision prec, int64_t hbm_budget_bytes, sg_server **out);
 sg_status sg_server_submit(sg_server *s, const sg_prop_request *req, int64_t *id);
+sg_status sg_server_submit_eigs(sg_server *s, const sg_eig_request *req, int64_t *id);
 sg_status sg_server_progress(sg_server *s, int max_iters, int *n_active, int *n_queued);
 sg_status sg_server_query(const sg_server *s, int64_t id, int *state, int64_t *n_cs, int *steps_done);
 sg_status sg_server_result(sg_server *s, int64_t id, double *psi_host, double *norm_log, double *energy_log,
                            double *times);
+sg_status sg_server_eig_result(sg_server *s, int64_t id, double *evals, double *resid, double *evecs_host,
+                               double *times, int *converged);
 sg_status sg_server_stats(const sg_server *s, int64_t *iterations, int64_t *applications, int64_t *bytes_in_use);
 const char *sg_server_last_error(const sg_server *s);
 void sg_server_destroy(sg_server *s);

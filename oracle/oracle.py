@@ -10,7 +10,7 @@ this module.  It builds `smolyak_oracle.c` with gcc on first use (or via
   enumerate_compact(...)        compact basis, lexicographic, first mode slowest (Table 2)
   counts(...)                   n_terms, N_s, N_cs (Table 1)
   term_map(...)                 mapping table M^B (Table 2)
-  apply_H(problem, x, ...)      y = H_S x by Alg. 1 on every term (Eq. (16))
+  apply_H(problem, x, ...)      y = H_S x, Eq. (16), every term through its grid (Eqs. (14)-(15))
 """
 from __future__ import annotations
 
@@ -148,7 +148,7 @@ def n_compact(p) -> int:
 
 
 def apply_H(p, x: np.ndarray, term_subset=None, threads: int = 0) -> np.ndarray:
-    """y = H_S x by the literal Alg. 1 over all terms (or a subset of term
+    """y = H_S x by Eq. (16) over all terms (or a subset of term
     indices in Table 2 order).  x: (nvec, N_cs) or (N_cs,) float64."""
     lib = _load()
     x = np.ascontiguousarray(np.asarray(x, np.float64))

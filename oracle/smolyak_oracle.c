@@ -13,12 +13,15 @@
  *   - Term order, in-term order and compact order as printed in Table 2
  *     (Sec. 3): terms with l_1 varying fastest; inside a term k_1 fastest;
  *     compact basis lexicographic with the first mode slowest.
- *   - Operator action of one term, Alg. 1 / the six steps of Sec. 3:
- *     extract (M^B) -> basis-to-grid, Eq. (15) -> operator on the grid ->
- *     grid-to-basis, Eq. (14) -> weighted compress-add -> all terms, Eq. (16).
- *   - Grid operator ("conventional operator action", Alg. 1): potential
- *     multiplied point-wise, kinetic -omega_j/2 d^2/dq_j^2 applied on the grid
- *     through the second derivatives of the basis functions at the nodes.
+ *   - The operator, Eq. (16): y = sum_l D_l P_l^T A_l P_l x, P_l the
+ *     restriction of the compact basis to term l (the mapping M^B of Table 2),
+ *     A_l = (x_i B_i^T W_i) O_l (x_i B_i): the transfer to the term's
+ *     direct-product grid (Eq. (15)), the operator on that grid, and the
+ *     transfer back (Eq. (14)).
+ *   - The operator on the grid (Sec. 3, "conventional" action on the grid):
+ *     the potential multiplied point by point; the kinetic part
+ *     -omega_j/2 d^2/dq_j^2 through the second derivatives of the basis
+ *     functions at the nodes.
  *
  * Readings where the paper is silent (listed with the design notes):
  *   - primitive basis "Hm": orthonormal Hermite functions
@@ -495,9 +498,9 @@ int orc_apply(int D, int L,
                 }
                 for (int v = 0; v < nvec; v++) {
                     const double *xv = x + (size_t)v * ncs;
-                    /* step 1: extract the term from the compact basis */
+                    /* P_l x: the term's coefficients, looked up in the compact basis (M^B, Table 2) */
                     for (int64_t s = 0; s < nbt; s++) X[s] = xv[rank[s]];
-                    /* step 2: basis -> grid, mode by mode (Eq. (15)) */
+                    /* (x_i B_i) P_l x: the term's function on its direct-product grid (Eq. (15)) */
                     for (int i = 0; i < D; i++) dims[i] = mt[i]->nb;
                     memcpy(T1, X, sizeof(double) * nbt);
                     for (int i = 0; i < D; i++) {
@@ -506,7 +509,7 @@ int orc_apply(int D, int L,
                         double *sw = T1; T1 = T2; T2 = sw;
                     }
                     memcpy(G, T1, sizeof(double) * nqt);
-                    /* step 3: operator on the grid -- potential, point-wise */
+                    /* V(Q) times the grid values, point by point */
                     memset(u, 0, sizeof(int) * D);
                     for (int64_t g = 0; g < nqt; g++) {
                         double V = 0.0;
@@ -521,8 +524,8 @@ int orc_apply(int D, int L,
                         Yg[g] = V * G[g];
                         for (int i = 0; i < D; i++) { if (++u[i] < mt[i]->nq) break; u[i] = 0; }
                     }
-                    /* step 3 (cont.): kinetic -omega_j/2 d^2/dq_j^2 on the grid:
-                     * same transfer chain with b'' in place of b for mode j */
+                    /* plus the kinetic part -omega_j/2 d^2/dq_j^2 on the grid: the
+                     * transfer of Eq. (15) with b'' in place of b for mode j */
                     for (int j = 0; j < D; j++) {
                         if (omega[j] == 0.0) continue;
                         for (int i = 0; i < D; i++) dims[i] = mt[i]->nb;
@@ -535,7 +538,7 @@ int orc_apply(int D, int L,
                         }
                         for (int64_t g = 0; g < nqt; g++) Yg[g] += -0.5 * omega[j] * T1[g];
                     }
-                    /* step 4: grid -> basis, mode by mode (Eq. (14)) */
+                    /* (x_i B_i^T W_i): back to the term's basis (Eq. (14)) */
                     for (int i = 0; i < D; i++) dims[i] = mt[i]->nq;
                     memcpy(T1, Yg, sizeof(double) * nqt);
                     for (int i = 0; i < D; i++) {
@@ -543,7 +546,7 @@ int orc_apply(int D, int L,
                         dims[i] = mt[i]->nb;
                         double *sw = T1; T1 = T2; T2 = sw;
                     }
-                    /* step 5: compress and add D_l * term into the compact result */
+                    /* y += D_l P_l^T (...): the term's share of Eq. (16), D_l of Eq. (8) */
                     double *yv = yp + (size_t)v * ncs;
                     for (int64_t s = 0; s < nbt; s++) yv[rank[s]] += c * T1[s];
                 }

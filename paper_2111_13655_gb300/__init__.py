@@ -74,6 +74,12 @@ class _PropRequest(ctypes.Structure):
                 ("ld", ctypes.c_int), ("dt", ctypes.c_double), ("nsteps", ctypes.c_int), ("order", ctypes.c_int)]
 
 
+class _EigRequest(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_int), ("L", ctypes.c_int), ("basis", ctypes.c_void_p), ("grids", ctypes.c_void_p),
+                ("H", ctypes.c_void_p), ("nev", ctypes.c_int), ("block", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_it", ctypes.c_int), ("want_vectors", ctypes.c_int)]
+
+
 _lib = None
 _lock = threading.Lock()
 _vp, _i64, _i32, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
@@ -104,11 +110,14 @@ SIGNATURES = {
     "sg_batch_last_error": (ctypes.c_char_p, [_vp]),
     "sg_batch_destroy": (None, [_vp]),
     "sg_tune": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_dbl), _vp]),
+    "sg_tune_plan": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "sg_server_create": (_i32, [_i32, _i64, ctypes.POINTER(_vp)]),
     "sg_server_submit": (_i32, [_vp, _vp, _P64]),
+    "sg_server_submit_eigs": (_i32, [_vp, _vp, _P64]),
     "sg_server_progress": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "sg_server_query": (_i32, [_vp, _i64, ctypes.POINTER(_i32), _P64, ctypes.POINTER(_i32)]),
     "sg_server_result": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp]),
+    "sg_server_eig_result": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, ctypes.POINTER(_i32)]),
     "sg_server_stats": (_i32, [_vp, _P64, _P64, _P64]),
     "sg_server_last_error": (ctypes.c_char_p, [_vp]),
     "sg_server_destroy": (None, [_vp]),
@@ -362,11 +371,19 @@ def sg_propagate(ctx: Ctx, psi, dt: float, nsteps: int, order: int = 64, stream=
 
 
 def sg_tune(ctx: Ctx, nvec: int = 8, stream=None):
-    """Measured choice of the fast path's slicing target (1, 2 or 4 vectors per
-    chunk) for nvec-vector applies; returns (slice_vt kept, ms per apply)."""
+    """Measured choice of the fast path's plan (slicing target, block/warp
+    split, shared-memory budget per block) for nvec-vector applies; returns
+    (slicing target kept, ms per apply).  sg_tune_plan reports the whole plan."""
     vt, ms = ctypes.c_int(), ctypes.c_double()
     _check(lib().sg_tune(ctx.ptr, int(nvec), ctypes.byref(vt), ctypes.byref(ms), _stream_ptr(stream)), ctx)
     return vt.value, ms.value
+
+
+def sg_tune_plan(ctx: Ctx) -> dict:
+    """The plan the context uses now: slicing target, block/warp split, KB per block."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().sg_tune_plan(ctx.ptr, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), ctx)
+    return {"slice_vt": a.value, "warp_vt": b.value, "smem_kb": c.value}
 
 
 def sg_product_state(ctx: Ctx, factors) -> np.ndarray:
@@ -433,8 +450,9 @@ SG_REQ_QUEUED, SG_REQ_ACTIVE, SG_REQ_DONE, SG_REQ_FAILED = range(4)
 
 
 class Server:
-    """Propagation server on the current CUDA device (continuous batching of
-    Chebyshev propagation requests; see sg_server_* in include/smolyak.h)."""
+    """Request server on the current CUDA device (continuous batching of
+    Chebyshev propagation requests and block-Davidson eigen requests; see
+    sg_server_* in include/smolyak.h)."""
 
     def __init__(self, precision="fp64", hbm_budget_bytes: int = 150 * 10**9):
         out = _vp()
@@ -444,6 +462,7 @@ class Server:
         self.ptr = out.value
         self.nsteps = {}
         self.n_cs = {}
+        self.nev = {}
 
     def _err(self, st):
         if st != SG_OK:
@@ -470,6 +489,32 @@ class Server:
         st, n, _ = self.query(rid.value)
         self.nsteps[rid.value], self.n_cs[rid.value] = int(nsteps), n
         return rid.value
+
+    def submit_eigs(self, problem, nev: int, block: int = 0, tol: float = 1e-8, max_it: int = 200,
+                    vectors: bool = False) -> int:
+        """Queue the nev lowest eigenpairs of the problem's H_S (block Davidson)."""
+        basis, grids, ham, keep = _marshal(problem)
+        req = _EigRequest(problem.D, problem.L, ctypes.addressof(basis), ctypes.addressof(grids),
+                          ctypes.addressof(ham), int(nev), int(block), float(tol), int(max_it), int(bool(vectors)))
+        rid = ctypes.c_int64()
+        self._err(lib().sg_server_submit_eigs(self.ptr, ctypes.byref(req), ctypes.byref(rid)))
+        st, n, _ = self.query(rid.value)
+        self.n_cs[rid.value], self.nev[rid.value] = n, int(nev)
+        self.nsteps[rid.value] = 0
+        return rid.value
+
+    def eig_result(self, rid: int, vectors: bool = False):
+        """(evals, resid, evecs (nev x N_cs) or None, (queue_s, latency_s), converged pairs)."""
+        n, nev = self.n_cs[rid], self.nev[rid]
+        ev, rs, tm = np.zeros(nev), np.zeros(nev), np.zeros(2)
+        vec = np.zeros((nev, n)) if vectors else None
+        conv = ctypes.c_int()
+        st = lib().sg_server_eig_result(self.ptr, int(rid), ev.ctypes.data, rs.ctypes.data,
+                                        vec.ctypes.data if vec is not None else None, tm.ctypes.data,
+                                        ctypes.byref(conv))
+        if st not in (SG_OK, SG_ENOCONV):
+            self._err(st)
+        return ev, rs, vec, (float(tm[0]), float(tm[1])), conv.value
 
     def progress(self, max_iters: int = 1):
         """Runs up to max_iters engine iterations; returns (active, queued)."""

@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(const KParams P, const doubl
 
     for (int v = 0; v < nvec; v++) {
         const double *xv = x + (size_t)v * P.n_cs;
-        unsigned long long *accv = P.acc + (size_t)v * P.n_cs * fx::Acc<T>::words;
+        unsigned long long *accv = P.acc + (size_t)v * fx::Acc<T>::words;  // entry r at r * nvec
         const long long mbv = maxbits[v];
         for (int e = tid; e < H.NB; e += kThreads) { X[e] = (T)__ldg(xv + rk[e]); Y[e] = T(0); }
         __syncthreads();
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(const KParams P, const doubl
                 const T *Kr = mats + H.oK[j] + kj * nbj;
                 for (int kp = 0; kp < nbj; kp++) acc += Kr[kp] * X[base + kp * H.stride[j]];
             }
-            fx::Acc<T>::add(accv + (size_t)rk[e] * fx::Acc<T>::words, Y[e] + acc, H.coef, mbv, P.err);
+            fx::Acc<T>::add(accv + (size_t)rk[e] * nvec * fx::Acc<T>::words, Y[e] + acc, H.coef, mbv, P.err);
         }
         __syncthreads();
     }
@@ -422,6 +422,7 @@ __device__ __forceinline__ double finalize_value(unsigned long long *a, long lon
 }
 
 // y = (accumulated integer) * 2^E + esplit * x; clears the accumulators
+// (accumulators entry-major: entry r, vector v at r * nvec + v)
 __global__ void k_finalize(const KParams P, const double *__restrict__ x, double *__restrict__ y,
                            const long long *__restrict__ maxbits, int nvec, int fp32)
 {
@@ -429,7 +430,7 @@ __global__ void k_finalize(const KParams P, const double *__restrict__ x, double
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int v = (int)(i / P.n_cs);
         const size_t r = i - (size_t)v * P.n_cs;
-        y[i] = finalize_value(P.acc + i * acc_words(fp32), maxbits[v], fp32) + P.esplit[r] * x[i];
+        y[i] = finalize_value(P.acc + (r * nvec + v) * acc_words(fp32), maxbits[v], fp32) + P.esplit[r] * x[i];
     }
 }
 
@@ -472,7 +473,8 @@ __global__ void k_finalize_batch(const KParams *__restrict__ kps, const long lon
         const size_t i = g - (size_t)nvec * (size_t)cs_prefix[lo];
         const int v = (int)(i / n);
         const size_t r = i - (size_t)v * n;
-        y[g] = finalize_value(acc + g * acc_words(fp32), maxbits[(size_t)lo * nvec + v], fp32) +
+        const size_t a = (size_t)nvec * (size_t)cs_prefix[lo] + r * nvec + v;  // entry-major in its problem
+        y[g] = finalize_value(acc + a * acc_words(fp32), maxbits[(size_t)lo * nvec + v], fp32) +
                kps[lo].esplit[r] * x[g];
     }
 }

@@ -11,8 +11,15 @@
 
 #include "sg_internal.h"
 
+// Order of the batched work items: 0 = by term cost over all problems,
+// 1 = problem-major (problems by total cost, then their terms by cost).
+#ifndef SG_BATCH_ORDER
+#define SG_BATCH_ORDER 0
+#endif
+
 struct sg_batch {
     std::vector<sg_ctx *> ctxs;
+    std::vector<int> plan_versions;    // of the contexts when the batch was made
     int device = 0;
     bool fp32 = false;
     std::vector<long long> cs_prefix;  // host copy
@@ -80,6 +87,7 @@ extern "C" sg_status sg_batch_create(sg_ctx *const *ctxs, int n, sg_batch **out)
         b->device = c->device;
         b->fp32 = c->fp32;
         b->ctxs.push_back(c);
+        b->plan_versions.push_back(c->plan_version);
     }
     int cur = -1;
     if (cudaGetDevice(&cur) != cudaSuccess || cur != b->device) { delete b; return SG_EINVAL; }
@@ -123,7 +131,18 @@ extern "C" sg_status sg_batch_create(sg_ctx *const *ctxs, int n, sg_batch **out)
                 if (p1 > p0) part = std::max(part, sg::fast_part_bytes(ctxs[j]->kp, b->fp32, f == 1));
                 for (int64_t p = p0; p < p1; p++) it.push_back({T.pcost[p], j, (int)p});
             }
-            std::stable_sort(it.begin(), it.end(), [](const Item &a, const Item &c) { return a.cost > c.cost; });
+            if (SG_BATCH_ORDER == 0) {
+                std::stable_sort(it.begin(), it.end(), [](const Item &a, const Item &c) { return a.cost > c.cost; });
+            } else {
+                // problem-major: problems by decreasing total cost, each problem's
+                // terms by decreasing cost (a few problems in flight at a time)
+                std::map<int, int64_t> tot;
+                for (const Item &t : it) tot[t.j] += t.cost;
+                std::stable_sort(it.begin(), it.end(), [&](const Item &a, const Item &c) {
+                    if (a.j != c.j) return tot[a.j] != tot[c.j] ? tot[a.j] > tot[c.j] : a.j < c.j;
+                    return a.cost > c.cost;
+                });
+            }
             std::vector<int2> items(it.size());
             for (size_t q = 0; q < it.size(); q++) items[q] = make_int2(it[q].j, it[q].p);
             if (it.size() > (size_t)0x7FFFFFFF) { free_all(b); delete b; return SG_EUNSUPPORTED; }
@@ -167,6 +186,10 @@ extern "C" sg_status sg_apply_H_batch(sg_batch *b, const double *x, double *y, i
     if ((x < y + total) && (y < x + total)) return bfail(b, SG_EINVAL, "x and y overlap");
     if ((size_t)nprob * nvec > 65535u * 65535u) return bfail(b, SG_EUNSUPPORTED, "too many vectors");
     if (nvec > 65535) return bfail(b, SG_EUNSUPPORTED, "nvec > 65535");
+    for (int j = 0; j < nprob; j++)
+        if (b->ctxs[j]->plan_version != b->plan_versions[j])
+            return bfail(b, SG_EINVAL, "problem " + std::to_string(j) +
+                                           " was re-planned by sg_tune after the batch was made: recreate the batch");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
     if (nvec > b->acc_nvec) {

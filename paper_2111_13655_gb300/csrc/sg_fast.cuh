@@ -367,14 +367,23 @@ __device__ void bwd_pass(const T *in, T *out, int C, int PW, int nq, int nb, con
 // Register phase: at every outer grid point g of the slice, every vector's
 // inner block z (NBI values) becomes M_g z, in place in Z[g][v][i].  M_g is
 // read from the inner-block table tab ([unit][g][unit elements], this slice).
+// One (grid point, vector) pair per work item; M_g is read once per item (the
+// items of one grid point share its cache lines).  When an inner block spans
+// two 16-byte units, they are read and written in an order that alternates
+// per group of four threads, which keeps a quarter warp's 16-byte accesses on
+// distinct banks.
 template <typename T, int NBI, int GS>
 __device__ void reg_phase(const T *__restrict__ tab, T *Z, int NGs, int vb, int tid)
 {
     constexpr int U = vunit<T>();
     constexpr int UE = NBI == 1 ? 1 : U;
     constexpr int NEU = (NBI * (NBI + 1) / 2 + UE - 1) / UE;
+    constexpr bool TWO = NBI == 2 * U;  // the block is exactly two 16-byte units
     constexpr int ZW = (NBI * (int)sizeof(T)) % 16 == 0 ? U : NBI == 2 && sizeof(T) == 4 ? 2 : 1;
-    for (int g = tid; g < NGs; g += GS) {
+    const int total = NGs * vb;
+    const unsigned vmag = rmag((unsigned)vb);
+    for (int w = tid; w < total; w += GS) {
+        const int g = fdiv(w, vb, vmag);
         T mm[NEU * UE];
 #pragma unroll
         for (int q = 0; q < NEU; q++) {
@@ -382,22 +391,36 @@ __device__ void reg_phase(const T *__restrict__ tab, T *Z, int NGs, int vb, int 
 #pragma unroll
             for (int e = 0; e < UE; e++) mm[q * UE + e] = t.v[e];
         }
-        T *zp = Z + (size_t)g * vb * NBI;
-        for (int v = 0; v < vb; v++, zp += NBI) {
-            T z[NBI], y[NBI];
+        T *zp = Z + (size_t)w * NBI;
+        T z[NBI], y[NBI];
+        if constexpr (TWO) {
+            const bool h = (w >> 2) & 1;
+            const VecT<T, U> a = vld<T, U>(zp + (h ? U : 0)), b = vld<T, U>(zp + (h ? 0 : U));
+#pragma unroll
+            for (int e = 0; e < U; e++) { z[e] = h ? b.v[e] : a.v[e]; z[U + e] = h ? a.v[e] : b.v[e]; }
+        } else {
 #pragma unroll
             for (int i = 0; i < NBI; i += ZW) {
                 const VecT<T, ZW> t = vld<T, ZW>(zp + i);
 #pragma unroll
                 for (int e = 0; e < ZW; e++) z[i + e] = t.v[e];
             }
+        }
 #pragma unroll
-            for (int r = 0; r < NBI; r++) {
-                T acc = T(0);
+        for (int r = 0; r < NBI; r++) {
+            T acc = T(0);
 #pragma unroll
-                for (int c = 0; c < NBI; c++) acc = fma_t(mm[tri_index(r, c, NBI)], z[c], acc);
-                y[r] = acc;
-            }
+            for (int c = 0; c < NBI; c++) acc = fma_t(mm[tri_index(r, c, NBI)], z[c], acc);
+            y[r] = acc;
+        }
+        if constexpr (TWO) {
+            const bool h = (w >> 2) & 1;
+            VecT<T, U> a, b;
+#pragma unroll
+            for (int e = 0; e < U; e++) { a.v[e] = h ? y[U + e] : y[e]; b.v[e] = h ? y[e] : y[U + e]; }
+            vst<T, U>(zp + (h ? U : 0), a);
+            vst<T, U>(zp + (h ? 0 : U), b);
+        } else {
 #pragma unroll
             for (int i = 0; i < NBI; i += ZW) {
                 VecT<T, ZW> t;
@@ -474,16 +497,21 @@ __device__ void gather(const FHdr &H, const KParams &P, const double *x, const i
 
 // Final step of a chunk, fused: y = F + (c0 X when the term has no grid) +
 // sum over outer positions j of H1_j x_j X, then the exact compress-add of
-// D_l * y into the accumulators.  Work item = (outer site o, unit of W payload
-// elements); F may be NULL (no grid).
+// D_l * y into the accumulators.  First pass: work item = (outer site o, unit
+// of W payload elements); y is written to `dst` in the payload layout
+// [o][v][i] (dst = F, each unit in place -- only its own item reads it -- or,
+// without a grid, a separate basis-sized area).  A barrier.  Second pass: one
+// element per item in the order [o][i][v] (inner index, then vector), so the
+// lanes of a warp that share a compact entry add into consecutive words (the
+// accumulators are entry-major: entry r, vector v at r * nvec + v).
 template <typename T, int W, int GS>
 __device__ void combine_add(const FHdr &H, const KParams &P, const int *__restrict__ rk,
-                            const long long *__restrict__ maxbits, unsigned long long *acc, const T *X,
-                            const T *F, const T *mats, int vb, int tid)
+                            const long long *__restrict__ maxbits, unsigned long long *acc, int nvec, int v0,
+                            const T *X, const T *F, T *dst, const T *mats, int vb, int tid)
 {
     const int NBI = H.NBI, Pl = NBI * vb, PW = Pl / W, total = H.NBo * PW;
     const int m = H.m, R = H.R;
-    const unsigned pwmag = rmag((unsigned)PW), nbimag = rmag((unsigned)NBI);
+    const unsigned pwmag = rmag((unsigned)PW);
     const T c0 = H.grid ? T(0) : (T)H.c0;
     for (int w = tid; w < total; w += GS) {
         const int o = fdiv(w, PW, pwmag), pw = w - o * PW;
@@ -513,14 +541,20 @@ __device__ void combine_add(const FHdr &H, const KParams &P, const int *__restri
                 for (int e = 0; e < W; e++) a[e] = fma_t(hv, xv.v[e], a[e]);
             }
         }
-        // element e of the unit is payload element pw * W + e = v * NBI + i
+        VecT<T, W> out;
 #pragma unroll
-        for (int e = 0; e < W; e++) {
-            const int pe = pw * W + e;
-            const int v = fdiv(pe, NBI, nbimag), i = pe - v * NBI;
-            const int r = __ldg(rk + (size_t)o * NBI + i);
-            fx::Acc<T>::add(acc + ((size_t)v * P.n_cs + r) * fx::Acc<T>::words, a[e], H.coef, maxbits[v], P.err);
-        }
+        for (int e = 0; e < W; e++) out.v[e] = a[e];
+        vst<T, W>(dst + eoff, out);
+    }
+    gsync<GS>();
+    const int n = H.NB * vb;
+    const unsigned vmag = rmag((unsigned)vb), nbimag = rmag((unsigned)NBI);
+    for (int w = tid; w < n; w += GS) {
+        const int oi = fdiv(w, vb, vmag), v = w - oi * vb;  // oi = o * NBI + i
+        const int o = fdiv(oi, NBI, nbimag), i = oi - o * NBI;
+        const int r = __ldg(rk + oi);
+        fx::Acc<T>::add(acc + ((size_t)r * nvec + v0 + v) * fx::Acc<T>::words, dst[(size_t)o * Pl + v * NBI + i],
+                        H.coef, maxbits[v0 + v], P.err);
     }
 }
 
@@ -528,7 +562,8 @@ __device__ void combine_add(const FHdr &H, const KParams &P, const int *__restri
 // threads: GS = 128 (a whole block) or GS = 32 (one warp; no block-wide
 // barriers).  `base` is the group's shared-memory partition (part_bytes of P
 // with `work_cap` work elements), `accp` the problem's fixed-point
-// accumulators, `x` and `maxbits` its input vectors and their exponents.
+// accumulators (entry-major, nvec vectors), `x` and `maxbits` its input
+// vectors and their exponents.
 template <typename T, int GS>
 __device__ __forceinline__ void fast_term(const KParams &P, const double *__restrict__ x,
                                           unsigned long long *accp, const long long *__restrict__ maxbits,
@@ -678,9 +713,10 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
             if (sliced) F = Y;
         }
         // basis part of the outer positions and exact compress-add of D_l * y_l
-        unsigned long long *acc = accp + (size_t)v0 * P.n_cs * fx::Acc<T>::words;
-        if (WW == U) combine_add<T, U, GS>(H, P, rk, maxbits + v0, acc, X, F, mats, vb, tid);
-        else combine_add<T, 1, GS>(H, P, rk, maxbits + v0, acc, X, F, mats, vb, tid);
+        // (y in place of F; a term without a grid uses the area after X)
+        T *dst = F ? const_cast<T *>(F) : Y;
+        if (WW == U) combine_add<T, U, GS>(H, P, rk, maxbits, accp, nvec, v0, X, F, dst, mats, vb, tid);
+        else combine_add<T, 1, GS>(H, P, rk, maxbits, accp, nvec, v0, X, F, dst, mats, vb, tid);
         gsync<GS>();
     }
 }

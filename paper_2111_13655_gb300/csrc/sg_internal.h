@@ -57,11 +57,21 @@ constexpr int kMaxPairs = 64;  // coupled mode pairs handled by the fast path
 #ifndef SG_F64_SLICE_VT
 #define SG_F64_SLICE_VT 4
 #endif
+// Warp form: terms that fit a quarter of the block's shared memory with a
+// chunk of SG_WARP_VT vectors (sliced when SG_WARP_SLICE is 1) run one per warp.
+// Measured at D=12 L=10 (mixed): 1 vector 31.29 ms per 8-vector apply, 4
+// vectors 31.85; slicing in the warp form 43-60 ms.
+#ifndef SG_WARP_VT
+#define SG_WARP_VT 1
+#endif
+#ifndef SG_WARP_SLICE
+#define SG_WARP_SLICE 0
+#endif
 #ifndef SG_F64_SMEM_KB
-#define SG_F64_SMEM_KB 106
+#define SG_F64_SMEM_KB 70
 #endif
 #ifndef SG_F64_MINBLOCKS
-#define SG_F64_MINBLOCKS 2
+#define SG_F64_MINBLOCKS 3
 #endif
 
 // Inner positions of the fast kernel: up to fast_rmax level-1 modes whose
@@ -76,11 +86,12 @@ inline int fast_rmax(int nb1) { return nb1 == 2 ? 3 : nb1 == 3 ? 2 : 0; }
 __host__ __device__ inline int64_t pad_elems(int64_t n, int u) { return (n + u - 1) / u * u; }
 // Work-area elements a chunk of vb vectors of one term needs: the gathered
 // basis tensor X (and the slice accumulator Y when the term is sliced), and
-// two buffers of the largest grid stage when the term has a grid; every
-// buffer padded to 16 bytes (u elements).
+// two buffers of the largest grid stage when the term has a grid (a term
+// without a grid has a second basis-sized buffer instead, for the staged
+// compress-add); every buffer padded to 16 bytes (u elements).
 __host__ __device__ inline int64_t chunk_need(int64_t NB, int64_t stage, bool sliced, bool grid, int vb, int u)
 {
-    return (sliced ? 2 : 1) * pad_elems(NB * vb, u) + (grid ? 2 * pad_elems(stage * vb, u) : 0);
+    return (sliced || !grid ? 2 : 1) * pad_elems(NB * vb, u) + (grid ? 2 * pad_elems(stage * vb, u) : 0);
 }
 // Inner-block table per outer grid point: the upper triangle of the NBI x NBI
 // symmetric block (NBI (NBI+1)/2 values, row by row) in units of mt_unit
@@ -171,7 +182,7 @@ struct KParams {
     const int *mfpow;        // [sum nfac]
     const int *harm_mono;    // [D] monomial holding the harmonic part of mode i (-1: not split)
     const double *esplit;    // [n_cs] sum over split modes of omega_i s_i^2 (k_i + 1/2)
-    unsigned long long *acc; // [nvec][n_cs][acc_words] fixed-point accumulators
+    unsigned long long *acc; // [n_cs][nvec][acc_words] fixed-point accumulators (entry-major)
     FastParams fast;
     // capacities of the per-CTA shared-memory areas (elements)
     int cap;       // each of the two grid ping-pong buffers
@@ -221,6 +232,7 @@ struct HostTables {
     int64_t franks = 0;               // total compact indices (N_s)
     int fdesccap = 0, fgcap = 0, fnbocap = 1, fn_big = 0, fwork_cta = 0, fwork_warp = 0;
     int slice_vt = 0;                 // slicing target the records were planned with (0: default)
+    int warp_vt = 0;                  // warp-form threshold the records were planned with (0: default)
     int fbudget = 0;                  // shared-memory budget the records were planned with
     int cap = 0, maxnb = 0, matcap = 0, vtabcap = 0;
     int64_t flops_per_vec = 0;       // FMA-counted work of one real apply (2 flops per FMA)
@@ -321,6 +333,7 @@ struct sg_ctx {
     unsigned long long *acc = nullptr;
     long long *maxbits = nullptr;
     int acc_nvec = 0;
+    int plan_version = 0;     // incremented whenever sg_tune installs a plan
     std::string last_error;
 };
 

@@ -15,7 +15,10 @@
 
 namespace {
 
-constexpr int kChains = 16;
+#ifndef SG_PEAK_CHAINS
+#define SG_PEAK_CHAINS 16
+#endif
+constexpr int kChains = SG_PEAK_CHAINS;
 constexpr int kPeakThreads = 256;
 constexpr int kPeakBlocksPerSM = 4;
 

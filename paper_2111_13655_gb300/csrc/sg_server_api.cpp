@@ -110,6 +110,7 @@ struct sg_server {
     // state buffers over the active requests (batch layout, nvec = 2)
     double *X = nullptr, *Y = nullptr, *P = nullptr, *A = nullptr;
     int64_t total = 0;
+    int nslots = 0;
     sg::ChebState *d_state = nullptr;
     long long *d_prefix = nullptr;
     // two engine iterations (roles X -> P, then back), replayed between changes of
@@ -190,13 +191,30 @@ sg_status prepare(sg_server *s, Req *r)
     return SG_OK;
 }
 
-// New layout over the active requests; copies the surviving states and uploads new ones.
+// New layout over the active requests' batch slots (a propagation request has
+// one two-vector slot, an eigen request (block + 1) / 2); copies the surviving
+// propagation states and uploads new ones.
 sg_status relayout(sg_server *s)
 {
     cudaError_t e;
     if (s->batch) { sg_batch_destroy(s->batch); s->batch = nullptr; }
-    std::vector<long long> prefix(s->active.size() + 1, 0);
-    for (size_t j = 0; j < s->active.size(); j++) prefix[j + 1] = prefix[j] + s->active[j]->n_cs;
+    std::vector<long long> prefix(1, 0);
+    std::vector<sg_ctx *> ctxs;
+    std::vector<sg::ChebState> state;
+    std::vector<int64_t> first_slot(s->active.size());
+    for (size_t j = 0; j < s->active.size(); j++) {
+        Req *r = s->active[j];
+        first_slot[j] = prefix.back();
+        for (int q = 0; q < r->nslots; q++) {
+            prefix.push_back(prefix.back() + r->n_cs);
+            ctxs.push_back(r->ctx);
+            if (r->kind == kProp)
+                state.push_back(sg::ChebState{r->k, r->K, r->step, r->nsteps, r->ebar, 1.0 / r->de, r->cph, r->sph,
+                                              r->d_c, r->d_log});
+            else  // never updated: the recurrence passes the slot through
+                state.push_back(sg::ChebState{0, 1, 0, 0, 0.0, 1.0, 1.0, 0.0, nullptr, nullptr});
+        }
+    }
     const int64_t total = prefix.back();
     double *nb[4] = {nullptr, nullptr, nullptr, nullptr};
     if (total > 0) {
@@ -209,19 +227,21 @@ sg_status relayout(sg_server *s)
     double *old[4] = {s->X, s->Y, s->P, s->A};
     for (size_t j = 0; j < s->active.size(); j++) {
         Req *r = s->active[j];
-        const size_t bytes = sizeof(double) * 2 * (size_t)r->n_cs;
-        const int64_t no = prefix[j];
-        if (r->fresh) {
-            e = cudaMemcpyAsync(nb[0] + 2 * no, r->psi0.data(), bytes, cudaMemcpyHostToDevice, s->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // psi0 may be released next
-            if (e != cudaSuccess) return sfail(s, SG_ECUDA, std::string("psi0 upload: ") + cudaGetErrorString(e));
-            r->fresh = false;
-            std::vector<double>().swap(r->psi0);
-        } else {
-            for (int b : {0, 2, 3})
-                if ((e = cudaMemcpyAsync(nb[b] + 2 * no, old[b] + 2 * r->off, bytes, cudaMemcpyDeviceToDevice,
-                                         s->stream)) != cudaSuccess)
-                    return sfail(s, SG_ECUDA, std::string("state move: ") + cudaGetErrorString(e));
+        const int64_t no = first_slot[j];
+        if (r->kind == kProp) {
+            const size_t bytes = sizeof(double) * 2 * (size_t)r->n_cs;
+            if (r->fresh) {
+                e = cudaMemcpyAsync(nb[0] + 2 * no, r->psi0.data(), bytes, cudaMemcpyHostToDevice, s->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // psi0 may be released next
+                if (e != cudaSuccess) return sfail(s, SG_ECUDA, std::string("psi0 upload: ") + cudaGetErrorString(e));
+                r->fresh = false;
+                std::vector<double>().swap(r->psi0);
+            } else {
+                for (int b : {0, 2, 3})
+                    if ((e = cudaMemcpyAsync(nb[b] + 2 * no, old[b] + 2 * r->off, bytes, cudaMemcpyDeviceToDevice,
+                                             s->stream)) != cudaSuccess)
+                        return sfail(s, SG_ECUDA, std::string("state move: ") + cudaGetErrorString(e));
+            }
         }
         r->off = no;
     }
@@ -230,13 +250,8 @@ sg_status relayout(sg_server *s)
     free_state(s);
     s->X = nb[0]; s->Y = nb[1]; s->P = nb[2]; s->A = nb[3];
     s->total = total;
-    const size_t na = std::max<size_t>(1, s->active.size());
-    std::vector<sg::ChebState> state(s->active.size());
-    for (size_t j = 0; j < s->active.size(); j++) {
-        const Req *r = s->active[j];
-        state[j] = sg::ChebState{r->k, r->K, r->step, r->nsteps, r->ebar, 1.0 / r->de, r->cph, r->sph,
-                                 r->d_c, r->d_log};
-    }
+    s->nslots = (int)state.size();
+    const size_t na = std::max<size_t>(1, state.size());
     if ((e = cudaMalloc(&s->d_state, sizeof(sg::ChebState) * na)) != cudaSuccess ||
         (e = cudaMalloc(&s->d_prefix, sizeof(long long) * (na + 1))) != cudaSuccess)
         return sfail(s, SG_ENOMEM, std::string("server tables cudaMalloc: ") + cudaGetErrorString(e));
@@ -245,9 +260,7 @@ sg_status relayout(sg_server *s)
         (!state.empty() && (e = cudaMemcpy(s->d_state, state.data(), sizeof(sg::ChebState) * state.size(),
                                            cudaMemcpyHostToDevice)) != cudaSuccess))
         return sfail(s, SG_ECUDA, std::string("server tables upload: ") + cudaGetErrorString(e));
-    if (!s->active.empty()) {
-        std::vector<sg_ctx *> ctxs;
-        for (Req *r : s->active) ctxs.push_back(r->ctx);
+    if (!ctxs.empty()) {
         sg_status st = sg_batch_create(ctxs.data(), (int)ctxs.size(), &s->batch);
         if (st != SG_OK) return sfail(s, st, "sg_batch_create over the active requests failed");
     }
@@ -255,16 +268,37 @@ sg_status relayout(sg_server *s)
     return SG_OK;
 }
 
+// Whether an active request has finished: a propagation request after its
+// last step, an eigen request when its solver thread has ended.
+bool finished(sg_server *s, const Req *r)
+{
+    if (r->kind == kProp) return r->step >= r->nsteps;
+    std::lock_guard<std::mutex> lk(s->mu);
+    return r->phase == kFinished;
+}
+
 void retire(sg_server *s)
 {
     bool any = false;
-    for (const Req *r : s->active) any |= r->step >= r->nsteps;
+    for (const Req *r : s->active) any |= finished(s, r);
     if (!any) return;
     // the iterations run asynchronously on the server's (non-blocking) stream
     const cudaError_t es = cudaStreamSynchronize(s->stream);
     std::vector<Req *> keep;
     for (Req *r : s->active) {
-        if (r->step < r->nsteps) { keep.push_back(r); continue; }
+        if (!finished(s, r)) { keep.push_back(r); continue; }
+        if (r->kind == kEig) {
+            if (r->worker.joinable()) r->worker.join();
+            int derr = 0;
+            if (r->eig_status == SG_OK || r->eig_status == SG_ENOCONV) sg_device_error(r->ctx, &derr);
+            r->state = (r->eig_status == SG_OK || r->eig_status == SG_ENOCONV) && derr == 0 ? SG_REQ_DONE
+                                                                                           : SG_REQ_FAILED;
+            if (derr) r->error = "device error " + std::to_string(derr);
+            r->t_done = now_s();
+            release(s, r);
+            s->dirty = true;
+            continue;
+        }
         r->psi.resize(2 * (size_t)r->n_cs);
         r->log.resize(2 * (size_t)r->nsteps);
         cudaError_t e = es;
@@ -284,13 +318,67 @@ void retire(sg_server *s)
     s->active.swap(keep);
 }
 
+// Host thread of an eigen request: the block Davidson of sg_eigs on the
+// request's context, vector algebra on a stream of its own, every application
+// of H_S handed to the engine (at most 2 * nslots vectors per engine
+// iteration) and waited for.
+void eig_worker(sg_server *s, Req *r)
+{
+    cudaSetDevice(s->device);
+    cudaStream_t st = nullptr;
+    sg_status res = SG_OK;
+    std::string err;
+    double *evecs = nullptr;
+    const int64_t n = r->n_cs;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { res = SG_ECUDA; err = "stream"; }
+    if (res == SG_OK && r->want_vectors &&
+        cudaMalloc(&evecs, sizeof(double) * (size_t)n * r->nev) != cudaSuccess) { res = SG_ENOMEM; err = "eigenvectors"; }
+    r->evals.assign(r->nev, 0.0);
+    r->resid.assign(r->nev, 0.0);
+    if (res == SG_OK) {
+        const int cap = 2 * r->nslots;
+        sg::ApplyFn fn = [s, r, n, cap](const double *x, double *y, int nr) -> sg_status {
+            for (int j0 = 0; j0 < nr; j0 += cap) {
+                std::unique_lock<std::mutex> lk(s->mu);
+                r->ex = x + (size_t)j0 * n;
+                r->ey = y + (size_t)j0 * n;
+                r->er = std::min(cap, nr - j0);
+                r->phase = kPosted;
+                s->cv.notify_all();
+                s->cv.wait(lk, [&] { return r->phase == kApplied || s->aborting; });
+                if (s->aborting) return SG_ECUDA;
+                r->phase = kRunning;
+                if (r->apply_status != SG_OK) return r->apply_status;
+            }
+            return SG_OK;
+        };
+        int nconv = 0;
+        res = sg::davidson_routed(r->ctx, st, fn, r->nev, r->block, r->tol, r->eig_max_it, r->evals.data(),
+                                  r->resid.data(), evecs, &nconv, &err);
+        r->nconv = nconv;
+        if (res == SG_OK && nconv < r->nev) res = SG_ENOCONV;
+        if (evecs && (res == SG_OK || res == SG_ENOCONV)) {
+            r->evecs.resize((size_t)n * r->nev);
+            if (cudaMemcpy(r->evecs.data(), evecs, sizeof(double) * r->evecs.size(), cudaMemcpyDeviceToHost) !=
+                cudaSuccess) { res = SG_ECUDA; err = "eigenvector copy"; }
+        }
+    }
+    if (evecs) cudaFree(evecs);
+    if (st) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->eig_status = res;
+    if (res != SG_OK && res != SG_ENOCONV) r->error = err.empty() ? "eigen solver failed" : err;
+    r->phase = kFinished;
+    s->cv.notify_all();
+}
+
 sg_status admit(sg_server *s)
 {
     while (!s->queue.empty() && s->used + s->queue.front()->bytes <= s->budget) {
         Req *r = s->queue.front();
         s->queue.pop_front();
         r->t_admit = now_s();
-        if (r->nsteps == 0) {  // nothing to propagate: the result is the initial state
+        if (r->kind == kProp && r->nsteps == 0) {  // nothing to propagate: the result is the initial state
             r->psi.swap(r->psi0);
             r->state = SG_REQ_DONE;
             r->t_done = now_s();
@@ -298,6 +386,22 @@ sg_status admit(sg_server *s)
         }
         s->used += r->bytes;
         sg_status st = make_ctx(r, s->prec, true, &r->ctx);
+        if (r->kind == kEig) {
+            if (st != SG_OK) {
+                r->state = SG_REQ_FAILED;
+                r->error = sg_last_error(nullptr);
+                r->t_done = now_s();
+                release(s, r);
+                continue;
+            }
+            r->state = SG_REQ_ACTIVE;
+            r->phase = kRunning;
+            r->step = 0;
+            s->active.push_back(r);
+            s->dirty = true;
+            r->worker = std::thread(eig_worker, s, r);
+            continue;
+        }
         if (st == SG_OK) st = prepare(s, r);
         cudaError_t e = cudaSuccess;
         if (st == SG_OK) {
@@ -378,17 +482,86 @@ sg_status iterate(sg_server *s, int64_t n)
             else r->k++;
         }
     s->iterations += n;
-    s->applications += 2 * (int64_t)s->active.size() * n;
+    s->applications += 2 * (int64_t)s->active.size() * n;  // propagation requests only here
     return SG_OK;
 }
 
-// Iterations until the first active request finishes its last step.
+// Iterations until the first active propagation request finishes its last step.
 int64_t until_first_finish(const sg_server *s)
 {
     int64_t m = INT64_MAX;
     for (const Req *r : s->active)
-        m = std::min<int64_t>(m, (int64_t)(r->nsteps - r->step - 1) * r->K + (r->K - r->k));
+        if (r->kind == kProp) m = std::min<int64_t>(m, (int64_t)(r->nsteps - r->step - 1) * r->K + (r->K - r->k));
     return m;
+}
+
+bool has_eig(const sg_server *s)
+{
+    for (const Req *r : s->active)
+        if (r->kind == kEig) return true;
+    return false;
+}
+
+// Waits (at most 600 s) until every active eigen request has handed over a
+// block or finished; *any_finished tells whether some finished.
+sg_status wait_eig(sg_server *s, bool *any_finished)
+{
+    std::unique_lock<std::mutex> lk(s->mu);
+    const bool ok = s->cv.wait_for(lk, std::chrono::seconds(600), [&] {
+        for (const Req *r : s->active)
+            if (r->kind == kEig && r->phase != kPosted && r->phase != kFinished) return false;
+        return true;
+    });
+    if (!ok) return sfail(s, SG_ETIMEOUT, "an eigen request did not hand over its block within 600 s");
+    *any_finished = false;
+    for (const Req *r : s->active) *any_finished |= r->kind == kEig && r->phase == kFinished;
+    return SG_OK;
+}
+
+// One engine iteration with eigen requests active: their blocks go into
+// their slots of X (unused vectors of a slot zero), one batched apply and
+// recurrence update for everyone, the eigen results back to the requests.
+sg_status eig_iteration(sg_server *s)
+{
+    cudaError_t e = cudaSuccess;
+    for (const Req *r : s->active) {
+        if (r->kind != kEig) continue;
+        const size_t n = (size_t)r->n_cs;
+        double *dst = s->X + 2 * r->off;
+        e = cudaMemcpyAsync(dst, r->ex, sizeof(double) * n * r->er, cudaMemcpyDeviceToDevice, s->stream);
+        if (e == cudaSuccess && r->er < 2 * r->nslots)
+            e = cudaMemsetAsync(dst + n * r->er, 0, sizeof(double) * n * (2 * r->nslots - r->er), s->stream);
+        if (e != cudaSuccess) return sfail(s, SG_ECUDA, std::string("eigen block copy: ") + cudaGetErrorString(e));
+    }
+    sg_status st = enqueue_iteration(s, s->X, s->P);
+    if (st == SG_OK)
+        for (const Req *r : s->active)
+            if (r->kind == kEig && e == cudaSuccess)
+                e = cudaMemcpyAsync(r->ey, s->Y + 2 * r->off, sizeof(double) * (size_t)r->n_cs * r->er,
+                                    cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (st == SG_OK && e != cudaSuccess) st = sfail(s, SG_ECUDA, std::string("eigen iteration: ") + cudaGetErrorString(e));
+    std::swap(s->X, s->P);
+    int64_t apps = 0;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (Req *r : s->active) {
+            if (r->kind == kProp) {
+                apps += 2;
+                if (r->k + 1 == r->K) { r->k = 0; r->step++; }
+                else r->k++;
+            } else {
+                apps += r->er;
+                r->apply_status = st;
+                r->phase = kApplied;
+                r->step++;
+            }
+        }
+    }
+    s->cv.notify_all();
+    s->iterations += 1;
+    s->applications += apps;
+    return st;
 }
 
 }  // namespace
@@ -470,6 +643,92 @@ sg_status sg_server_submit(sg_server *s, const sg_prop_request *q, int64_t *id)
     return SG_OK;
 }
 
+sg_status sg_server_submit_eigs(sg_server *s, const sg_eig_request *q, int64_t *id)
+{
+    if (!s) return SG_EINVAL;
+    if (!q || !id || !q->basis || !q->grids || !q->H || !q->H->omega || q->nev < 1 || !(q->tol > 0) ||
+        q->max_it < 1)
+        return sfail(s, SG_EINVAL, "sg_server_submit_eigs: invalid request");
+    if (q->D < 1 || q->D > sg::kMaxD) return sfail(s, SG_EINVAL, "sg_server_submit_eigs: D out of range");
+    Req *r = new (std::nothrow) Req;
+    if (!r) return SG_ENOMEM;
+    r->kind = kEig;
+    r->D = q->D;
+    r->L = q->L;
+    r->basis.assign(q->basis, q->basis + r->D);
+    r->grids.assign(q->grids, q->grids + r->D);
+    r->omega.assign(q->H->omega, q->H->omega + r->D);
+    const sg_poly &V = q->H->V;
+    int nf = 0;
+    for (int m = 0; m < V.nterms; m++) nf += V.nfac[m];
+    r->coef.assign(V.coef, V.coef + V.nterms);
+    r->nfac.assign(V.nfac, V.nfac + V.nterms);
+    r->mode.assign(V.mode, V.mode + nf);
+    r->power.assign(V.power, V.power + nf);
+    r->nev = q->nev;
+    r->block = q->block <= 0 ? std::min(q->nev, 8) : std::min(q->block, 8);
+    r->nslots = (r->block + 1) / 2;
+    r->tol = q->tol;
+    r->eig_max_it = q->max_it;
+    r->want_vectors = q->want_vectors ? 1 : 0;
+    sg_ctx *plan = nullptr;
+    sg_status st = make_ctx(r, s->prec, false, &plan);
+    if (st != SG_OK) {
+        delete r;
+        return sfail(s, st, std::string("sg_server_submit_eigs: ") + sg_last_error(nullptr));
+    }
+    int64_t n_cs = 0, n_terms = 0;
+    sg_size(plan, &n_cs, &n_terms, nullptr, nullptr, nullptr);
+    const int64_t pb = sg::planned_device_bytes(plan);
+    sg_destroy(plan);
+    r->n_cs = n_cs;
+    if (r->nev > n_cs) {
+        delete r;
+        return sfail(s, SG_EINVAL, "sg_server_submit_eigs: nev exceeds N_cs");
+    }
+    // tables + M^B + batch items per slot + 4 state vectors and the batch
+    // workspace per slot + the Davidson basis and its images (2 kmax vectors),
+    // Ritz vectors, residuals and directions, eigenvectors, Gram scratch
+    const int64_t kmax = std::max(3 * r->nev, r->nev + 6 * r->block);
+    const int64_t vecs = 2 * kmax + 2 * std::max(r->nev, r->block) + r->block + (r->want_vectors ? r->nev : 0);
+    r->bytes = pb + r->nslots * (8 * n_terms + 2 * n_cs * (4 * 8 + 32)) + 8 * vecs * n_cs + ((int64_t)4 << 20);
+    if (r->bytes > s->budget) {
+        const int64_t b = r->bytes;
+        delete r;
+        return sfail(s, SG_EBUDGET, "sg_server_submit_eigs: request needs " + std::to_string(b) +
+                                        " bytes of device memory, over the budget");
+    }
+    r->id = s->next_id++;
+    r->t_submit = now_s();
+    s->all[r->id] = r;
+    s->queue.push_back(r);
+    *id = r->id;
+    return SG_OK;
+}
+
+sg_status sg_server_eig_result(sg_server *s, int64_t id, double *evals, double *resid, double *evecs_host,
+                               double *times, int *converged)
+{
+    if (!s) return SG_EINVAL;
+    auto f = s->all.find(id);
+    if (f == s->all.end()) return sfail(s, SG_EINVAL, "sg_server_eig_result: unknown id");
+    Req *r = f->second;
+    if (r->kind != kEig) return sfail(s, SG_EINVAL, "sg_server_eig_result: a propagation request (sg_server_result)");
+    if (r->state == SG_REQ_FAILED) return sfail(s, SG_ECUDA, "request failed: " + r->error);
+    if (r->state != SG_REQ_DONE) return sfail(s, SG_EINVAL, "sg_server_eig_result: request not finished");
+    if (evecs_host && !r->want_vectors)
+        return sfail(s, SG_EINVAL, "sg_server_eig_result: the request did not ask for eigenvectors");
+    if (evals) std::copy(r->evals.begin(), r->evals.end(), evals);
+    if (resid) std::copy(r->resid.begin(), r->resid.end(), resid);
+    if (evecs_host) std::copy(r->evecs.begin(), r->evecs.end(), evecs_host);
+    if (times) {
+        times[0] = r->t_admit - r->t_submit;
+        times[1] = r->t_done - r->t_submit;
+    }
+    if (converged) *converged = r->nconv;
+    return r->eig_status;
+}
+
 sg_status sg_server_progress(sg_server *s, int max_iters, int *n_active, int *n_queued)
 {
     if (!s || max_iters < 0) return SG_EINVAL;
@@ -483,6 +742,14 @@ sg_status sg_server_progress(sg_server *s, int max_iters, int *n_active, int *n_
         admit(s);
         if (s->dirty && (st = relayout(s)) != SG_OK) break;
         if (s->active.empty()) break;
+        if (has_eig(s)) {
+            bool fin = false;
+            if ((st = wait_eig(s, &fin)) != SG_OK) break;
+            if (fin) continue;  // retire the finished eigen requests first
+            if ((st = eig_iteration(s)) != SG_OK) break;
+            done += 1;
+            continue;
+        }
         const int64_t n = std::min<int64_t>(max_iters - done, until_first_finish(s));
         if ((st = iterate(s, n)) != SG_OK) break;
         done += n;
@@ -514,6 +781,7 @@ sg_status sg_server_result(sg_server *s, int64_t id, double *psi_host, double *n
     auto f = s->all.find(id);
     if (f == s->all.end()) return sfail(s, SG_EINVAL, "sg_server_result: unknown id");
     Req *r = f->second;
+    if (r->kind != kProp) return sfail(s, SG_EINVAL, "sg_server_result: an eigen request (sg_server_eig_result)");
     if (r->state == SG_REQ_FAILED) return sfail(s, SG_ECUDA, "request failed: " + r->error);
     if (r->state != SG_REQ_DONE) return sfail(s, SG_EINVAL, "sg_server_result: request not finished");
     if (psi_host) std::copy(r->psi.begin(), r->psi.end(), psi_host);
@@ -545,6 +813,11 @@ const char *sg_server_last_error(const sg_server *s)
 void sg_server_destroy(sg_server *s)
 {
     if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->aborting = true;
+    }
+    s->cv.notify_all();
     if (s->stream) cudaStreamSynchronize(s->stream);
     for (Req *r : s->active) release(s, r);
     if (s->batch) sg_batch_destroy(s->batch);

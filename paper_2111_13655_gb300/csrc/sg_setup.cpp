@@ -640,12 +640,20 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
     // slicing depth for a work area: the smallest leaving room for the slicing
     // target's vectors per chunk (else half as many, ...)
     const int vt0 = T.slice_vt > 0 ? T.slice_vt : fp32 ? SG_F32_SLICE_VT : SG_F64_SLICE_VT;
+    // (sliced blocks larger than nbocap functions are not used: their slice
+    // weights would not fit the group's head)
+    const int nbocap = 64;
     auto depth_for = [&](int t, const TermPlan &tp, int64_t work, int smax) {
-        if (chunk_need(tp.NB, 0, false, false, 1, U) > work) return -1;
-        if (!tp.grid) return 0;
-        for (int vt = vt0; vt >= 1; vt /= 2)
-            for (int s = 0; s <= std::min(smax, tp.na - tp.R); s++)
+        if (!tp.grid) return chunk_need(tp.NB, 0, false, false, 1, U) <= work ? 0 : -1;
+        const uint8_t *lt = &T.levels[(size_t)t * T.Dpad];
+        for (int vt = vt0; vt >= 1; vt /= 2) {
+            int64_t nbo = 1;
+            for (int s = 0; s <= std::min(smax, tp.na - tp.R); s++) {
+                if (s > 0) nbo *= LI(tp.posmode[tp.R + s - 1], lt[tp.posmode[tp.R + s - 1]]).nb;
+                if (nbo > nbocap) break;
                 if (chunk_need(tp.NB, stage_of(t, tp, s), s > 0, true, vt, U) <= work) return s;
+            }
+        }
         return -1;
     };
 
@@ -665,7 +673,6 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
         mcap = std::max(mcap, mat);
         img_total += (size_t)mat + tp.gsize;
     }
-    const int nbocap = 64;  // sliced blocks larger than this are not used
     const size_t head = ((size_t)rb * (mcap + gcap + 2 * nbocap) + 15) & ~(size_t)15;
     const size_t hdr_static = 4 * 1024;  // per-group header in static shared memory (kHdrBytes)
     const int64_t work_cta = ((int64_t)fbudget - (int64_t)head - 1024) / rb;
@@ -680,15 +687,24 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
     T.fwork_cta = (int)work_cta;
     T.fwork_warp = (int)std::max<int64_t>(work_warp, 0);
     T.fast_cap = T.fwork_cta;
-    // split: terms that fit a warp's quarter unsliced with a chunk of 4 vectors
-    // run one per warp; the last term that does not ends the block-form prefix
+    // split: terms that fit a warp's quarter with a chunk of warp_vt vectors
+    // (unsliced, or sliced when warp-form slicing is on) run one per warp; the
+    // last term that does not ends the block-form prefix
+    const int warp_vt = T.warp_vt > 0 ? T.warp_vt : SG_WARP_VT;
+    const int warp_smax = SG_WARP_SLICE ? kMaxD : 0;
+    auto fits_warp = [&](int t, const TermPlan &tp) {
+        if (work_warp <= 0 ||
+            (size_t)work_warp * rb < 16 * (3 + (size_t)tp.na + tp.prs.size() + (tp.inds.size() + 1) / 2))
+            return false;
+        if (!tp.grid) return chunk_need(tp.NB, 0, false, false, warp_vt, U) <= work_warp;
+        for (int s = 0; s <= std::min(warp_smax, tp.na - tp.R); s++)
+            if (chunk_need(tp.NB, stage_of(t, tp, s), s > 0, true, warp_vt, U) <= work_warp) return true;
+        return false;
+    };
     int64_t n_big = 0;
     for (int64_t q = 0; q < T.n_terms; q++) {
         plan_term(T.order[q], tp);
-        bool ok = work_warp > 0 &&
-                  chunk_need(tp.NB, tp.grid ? stage_of(T.order[q], tp, 0) : 0, false, tp.grid, 4, U) <= work_warp &&
-                  (size_t)work_warp * rb >= 16 * (3 + (size_t)tp.na + tp.prs.size() + (tp.inds.size() + 1) / 2);
-        if (!ok) n_big = q + 1;
+        if (!fits_warp(T.order[q], tp)) n_big = q + 1;
     }
     T.fn_big = (int)n_big;
     // pass 2: records
@@ -705,7 +721,7 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
         const uint8_t *lt = &T.levels[(size_t)t * T.Dpad];
         plan_term(t, tp);
         const bool big = q < n_big;
-        int sv = depth_for(t, tp, big ? work_cta : work_warp, big ? kMaxD : 0);
+        int sv = depth_for(t, tp, big ? work_cta : work_warp, big ? kMaxD : warp_smax);
         if (sv < 0) { T.fast = false; T.fdesc.clear(); return ""; }  // generic kernel instead
         int64_t nbo = 1;
         for (int j = tp.R; j < tp.R + sv; j++) nbo *= LI(tp.posmode[j], lt[tp.posmode[j]]).nb;

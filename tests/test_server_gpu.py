@@ -156,3 +156,87 @@ def test_request_without_steps_returns_its_initial_state():
         srv.run()
         psi, nl, el, _ = srv.result(rid)
     assert np.array_equal(psi, psi0) and nl.size == 0 and el.size == 0
+
+
+# --- eigen requests -------------------------------------------------------
+
+def test_eigen_request_equals_sg_eigs_bitwise():
+    """An eigen request runs the block Davidson of sg_eigs with its block
+    applications batched by the engine; batched applies are bitwise those of
+    the request's own context, so the eigenpairs are bitwise those of sg_eigs."""
+    p = synth.workload_C2()
+    with sg.sg_create(p, "fp64") as ctx:
+        ev, rs, vec, ok = sg.sg_eigs(ctx, 6, "davidson", block=4, tol=1e-9, max_it=300, vectors=True)
+    assert ok
+    with sg.Server("fp64") as srv:
+        rid = srv.submit_eigs(p, 6, block=4, tol=1e-9, max_it=300, vectors=True)
+        srv.run()
+        ev2, rs2, vec2, _, nconv = srv.eig_result(rid, vectors=True)
+    assert nconv == 6
+    assert np.array_equal(ev2, ev) and np.array_equal(rs2, rs)
+    assert np.array_equal(vec2, vec.cpu().numpy())
+
+
+def test_eigen_request_matches_the_oracle_spectrum():
+    """D=2 L=6 Henon-Heiles: the 10 lowest eigenvalues against the literal
+    oracle's dense H_S, FP64 server and mixed-precision server (the mixed
+    result carries the FP32 contractions' error, reported per eigenvalue)."""
+    p = synth.workload_C1()
+    ref = np.linalg.eigvalsh(dense_oracle(p))[:10]
+    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-5)):
+        with sg.Server(prec) as srv:
+            rid = srv.submit_eigs(p, 10, block=4, tol=1e-10 if prec == "fp64" else 1e-6, max_it=300)
+            srv.run()
+            ev, rs, _, _, nconv = srv.eig_result(rid)
+        err = np.abs(ev - ref)
+        print(f"server {prec} eigen request D=2 L=6: max |E - E_oracle| = {err.max():.2e}")
+        assert err.max() <= tol, (prec, err)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_eigen_and_propagation_requests_identical_alone_and_in_a_mix(prec):
+    P = mix_problems()
+    alone = {}
+    with sg.Server(prec) as srv:
+        rid = srv.submit_eigs(P["A"], 4, block=2, tol=1e-7, max_it=200)
+        srv.run()
+        alone["eA"] = srv.eig_result(rid)[:2]
+    with sg.Server(prec) as srv:
+        rid = srv.submit_eigs(P["B"], 3, block=3, tol=1e-7, max_it=200)
+        srv.run()
+        alone["eB"] = srv.eig_result(rid)[:2]
+    for name in ("R", "C"):
+        with sg.Server(prec) as srv:
+            rid = srv.submit(P[name], 0.1, 3, order=32, factors=packet(P[name]))
+            srv.run()
+            alone[name] = srv.result(rid)[:3]
+    with sg.Server(prec) as srv:
+        ids = {"R": srv.submit(P["R"], 0.1, 3, order=32, factors=packet(P["R"]))}
+        srv.progress(4)                                    # R runs alone first
+        ids["eA"] = srv.submit_eigs(P["A"], 4, block=2, tol=1e-7, max_it=200)
+        srv.progress(3)                                    # eA joins R
+        ids["C"] = srv.submit(P["C"], 0.1, 3, order=32, factors=packet(P["C"]))
+        ids["eB"] = srv.submit_eigs(P["B"], 3, block=3, tol=1e-7, max_it=200)
+        seen = set()
+        while True:
+            a, q = srv.progress(2)
+            seen.add(a)
+            if a == 0 and q == 0:
+                break
+        assert max(seen) >= 3
+        for name, rid in ids.items():
+            if name.startswith("e"):
+                ev, rs = srv.eig_result(rid)[:2]
+                assert np.array_equal(ev, alone[name][0]) and np.array_equal(rs, alone[name][1]), name
+            else:
+                psi, nl, el, _ = srv.result(rid)
+                assert np.array_equal(psi, alone[name][0]), name
+                assert np.array_equal(nl, alone[name][1]) and np.array_equal(el, alone[name][2]), name
+        assert srv.stats()["bytes_in_use"] == 0
+
+
+def test_eigen_request_over_the_budget_is_refused():
+    with sg.Server("fp64", hbm_budget_bytes=1 << 20) as srv:
+        with pytest.raises(sg.SgError) as ei:
+            srv.submit_eigs(mix_problems()["B"], 4, block=4)
+        assert ei.value.status == sg.SG_EBUDGET

@@ -34,6 +34,9 @@ def test_tuned_context_keeps_parity_and_determinism(prec, which):
         x = torch.from_numpy(xn).cuda().contiguous().view(-1)
         vt, ms = sg.sg_tune(ctx, nvec)
         assert vt in (1, 2, 4) and ms > 0.0
+        plan = sg.sg_tune_plan(ctx)
+        assert plan["slice_vt"] == vt and plan["warp_vt"] in (1, 2, 4)
+        assert plan["smem_kb"] in ((52, 70, 104) if prec == "mixed" else (70, 104))
         y1, y2 = torch.empty_like(x), torch.empty_like(x)
         sg.sg_apply_H(ctx, x, y1, nvec)
         sg.sg_apply_H(ctx, x, y2, nvec)
@@ -48,3 +51,22 @@ def test_generic_path_has_nothing_to_tune():
                                  [(0.05, [(0, 1), (1, 1), (2, 1)]), (0.2, [(0, 2), (1, 2)])])
     with sg.sg_create(p, "fp64") as ctx:
         assert sg.sg_tune(ctx, 2) == (0, 0.0)
+
+
+def test_batch_made_before_tuning_refuses_until_recreated():
+    p = synth.workload_C2()
+    with sg.sg_create(p, "mixed") as ctx:
+        x = torch.from_numpy(synth.random_vectors(ctx.n_cs, 2, 3)).cuda().contiguous().view(-1)
+        y0, y1 = torch.empty_like(x), torch.empty_like(x)
+        b = sg.sg_batch_create([ctx])
+        sg.sg_tune(ctx, 2)
+        with pytest.raises(sg.SgError) as ei:
+            sg.sg_apply_H_batch(b, x, y0, 2)
+        assert ei.value.status == sg.SG_EINVAL and "recreate" in str(ei.value)
+        sg.sg_batch_destroy(b)
+        b = sg.sg_batch_create([ctx])
+        sg.sg_apply_H_batch(b, x, y0, 2)
+        sg.sg_apply_H(ctx, x, y1, 2)
+        torch.cuda.synchronize()
+        assert torch.equal(y0, y1)
+        sg.sg_batch_destroy(b)
