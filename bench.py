@@ -12,7 +12,9 @@ FP64 mode is measured beside it.
 
 N > 1 (torchrun): every rank runs an independent replica (independent
 problems, no collective on the data path); value = all ranks' applications /
-the slowest rank's time ("scaling": "weak").
+the slowest rank's time ("scaling": "weak").  --sharding terms instead splits
+one problem's terms over the ranks with one integer all-reduce per apply
+("scaling": "strong").
 --impl reference: the CPU oracle (the literal Alg. 1 in C) timed as it stands
 on the host cores, each step a random sample of the workload's terms.
 """
@@ -170,8 +172,10 @@ def oracle_sample_rate(problem, n_terms: int, seconds: float, seed: int, threads
 
 def bench_config(args, world: int) -> dict:
     """The `config` of the JSON line; the same for both arms."""
+    par = f"terms sharded x{world}" if getattr(args, "sharding", "replicas") == "terms" and world > 1 \
+        else f"replicas x{world}"
     return {"workload": workload_name(args.L), "precision": "mixed (FP32 contractions, FP64 accumulation)",
-            "vectors_per_step": args.nvec, "parallelism": f"replicas x{world}",
+            "vectors_per_step": args.nvec, "parallelism": par,
             "l2": "flushed between timed steps (256 MB write)"}
 
 
@@ -270,61 +274,115 @@ def replica_throughput(world: int, units_per_rank: int, slowest_seconds: float) 
     return world * units_per_rank / slowest_seconds
 
 
+def run_stream(sg, prec, items, factors, rate, eig_every, eig_args, seed=55):
+    """One Poisson stream through a server of precision `prec`: propagation
+    requests, and every eig_every-th request an eigen request of the same
+    problem instead.  Returns (results by request index, makespan s, stats)."""
+    arrivals = np.cumsum(np.random.Generator(np.random.PCG64(seed)).exponential(1.0 / rate, len(items)))
+    srv = sg.Server(prec, hbm_budget_bytes=150 * 10**9)
+    ids = []
+    t0 = time.perf_counter()
+    i = 0
+    while True:
+        now = time.perf_counter() - t0
+        while i < len(items) and arrivals[i] <= now:
+            p, q0, ns = items[i]
+            if eig_every and i % eig_every == eig_every - 1:
+                ids.append(("eig", srv.submit_eigs(p, **eig_args[prec])))
+            else:
+                ids.append(("prop", srv.submit(p, 0.1, ns, order=64, factors=factors[i])))
+            i += 1
+        a, q = srv.progress(16)
+        if a == 0 and q == 0:
+            if i == len(items):
+                break
+            time.sleep(max(0.0, arrivals[i] - (time.perf_counter() - t0)))
+    makespan = time.perf_counter() - t0
+    res = []
+    for kind, rid in ids:
+        if kind == "eig":
+            ev, rs, _, tm, nconv = srv.eig_result(rid)
+            res.append({"kind": "eig", "evals": ev, "latency": tm[1], "converged": nconv})
+        else:
+            psi, nl, el, tm = srv.result(rid)
+            res.append({"kind": "prop", "psi": psi, "energy": el, "latency": tm[1]})
+    stats = srv.stats()
+    srv.close()
+    return res, makespan, stats
+
+
 def run_serving(args, sg, synth, torch):
-    """Poisson streams of propagation requests through the server (mixed
-    precision, continuous batching), one per arrival rate, against the same
-    requests run one at a time with sg_propagate in FP64."""
+    """Streams of propagation and eigen requests (the serving configuration's
+    distribution) through the server: mixed precision at every arrival rate,
+    FP64 at the highest; the same propagation requests one at a time by
+    sg_propagate in FP64 and in mixed precision (separating the effect of
+    batching from that of precision); per-request errors of the mixed server's
+    results against the FP64 server's."""
     items = synth.workload_C5(args.serve_requests, seed=5, Ds=tuple(range(6, args.serve_dmax + 1)),
                               Ls=tuple(range(4, args.serve_lmax + 1)), steps=(20, args.serve_steps_max))
     factors = [synth.coherent_factors(q0, p.L + 1) for p, q0, _ in items]
     rates = [float(r) for r in args.serve_rates.split(",")]
+    eig_args = {"mixed": dict(nev=4, block=4, tol=1e-5, max_it=300),
+                "fp64": dict(nev=4, block=4, tol=1e-9, max_it=300)}
+    E = args.serve_eig_every
     sweep = []
-    apps = 0
+    mixed_res = None
     for rate in rates:
-        arrivals = np.cumsum(np.random.Generator(np.random.PCG64(55)).exponential(1.0 / rate, len(items)))
-        srv = sg.Server("mixed", hbm_budget_bytes=150 * 10**9)
-        ids = []
-        t0 = time.perf_counter()
-        i = 0
-        while True:
-            now = time.perf_counter() - t0
-            while i < len(items) and arrivals[i] <= now:
-                p, q0, ns = items[i]
-                ids.append(srv.submit(p, 0.1, ns, order=64, factors=factors[i]))
-                i += 1
-            a, q = srv.progress(16)
-            if a == 0 and q == 0:
-                if i == len(items):
-                    break
-                time.sleep(max(0.0, arrivals[i] - (time.perf_counter() - t0)))
-        makespan = time.perf_counter() - t0
-        lat = np.array([srv.result(r)[3][1] for r in ids])
-        apps = srv.stats()["applications"]
-        srv.close()
-        sweep.append({"rate_req_s": rate, "applications_per_s": apps / makespan,
+        res, makespan, st = run_stream(sg, "mixed", items, factors, rate, E, eig_args)
+        lat = np.array([r["latency"] for r in res])
+        sweep.append({"rate_req_s": rate, "applications_per_s": st["applications"] / makespan,
                       "requests_per_s": len(items) / makespan, "makespan_s": makespan,
                       "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}})
-    # the same requests, one at a time, FP64 sg_propagate
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    for (p, q0, ns), f in zip(items, factors):
-        with sg.sg_create(p, "fp64") as ctx:
-            psi = sg.sg_product_state(ctx, f)
-            d = torch.from_numpy(np.concatenate([psi, np.zeros_like(psi)])).cuda()
-            sg.sg_propagate(ctx, d, 0.1, ns, order=64)
-    torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t1
-    desc = (f"{len(items)} chained Henon-Heiles propagation requests, D uniform in 6..{args.serve_dmax}, "
-            f"L uniform in 4..{args.serve_lmax}, nb=nq=l+1, steps uniform in 20..{args.serve_steps_max}, "
-            f"order 64, dt 0.1, Poisson arrivals, budget 150 GB")
+        mixed_res = res
+    top = max(rates)
+    res64, makespan64, st64 = run_stream(sg, "fp64", items, factors, top, E, eig_args)
+    lat64 = np.array([r["latency"] for r in res64])
+    fp64_server = {"rate_req_s": top, "applications_per_s": st64["applications"] / makespan64,
+                   "requests_per_s": len(items) / makespan64, "makespan_s": makespan64,
+                   "latency_s": {"p50": float(np.percentile(lat64, 50)), "p99": float(np.percentile(lat64, 99))}}
+    # per-request accuracy of the mixed server against the FP64 server
+    psi_err, drift_m, drift_64, eig_err = [], [], [], []
+    for rm, r64 in zip(mixed_res, res64):
+        if rm["kind"] == "prop":
+            psi_err.append(float(np.linalg.norm(rm["psi"] - r64["psi"])))
+            if len(rm["energy"]):
+                drift_m.append(float(np.max(np.abs(rm["energy"] - rm["energy"][0]))))
+                drift_64.append(float(np.max(np.abs(r64["energy"] - r64["energy"][0]))))
+        else:
+            eig_err.append(float(np.max(np.abs(rm["evals"] - r64["evals"]))))
+    # the propagation requests one at a time, sg_propagate, each precision
+    prop = [(it, f) for j, (it, f) in enumerate(zip(items, factors)) if not (E and j % E == E - 1)]
+    per_request = {}
+    for prec in ("fp64", "mixed"):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        apps = 0
+        for (p, q0, ns), f in prop:
+            with sg.sg_create(p, prec) as ctx:
+                psi = sg.sg_product_state(ctx, f)
+                d = torch.from_numpy(np.concatenate([psi, np.zeros_like(psi)])).cuda()
+                sg.sg_propagate(ctx, d, 0.1, ns, order=64)
+        torch.cuda.synchronize()
+        per_request[prec] = {"seconds": time.perf_counter() - t1, "requests": len(prop)}
+    n_eig = sum(1 for r in mixed_res if r["kind"] == "eig")
+    desc = (f"{len(items)} requests, chained Henon-Heiles, D uniform in 6..{args.serve_dmax}, "
+            f"L uniform in 4..{args.serve_lmax}, nb=nq=l+1; {len(items) - n_eig} propagation requests "
+            f"(steps uniform in 20..{args.serve_steps_max}, order 64, dt 0.1, Gaussian displaced by 2.0) "
+            f"and {n_eig} eigen requests (4 lowest, block Davidson, block 4); Poisson arrivals; budget 150 GB")
     head = max(sweep, key=lambda r: r["applications_per_s"])
+    q = lambda a: {"max": float(np.max(a)), "median": float(np.median(a))} if len(a) else None
     return {"workload": desc, "precision": "mixed (server, continuous batching)",
             "applications_per_s": head["applications_per_s"], "rate_req_s": head["rate_req_s"],
-            "latency_s": head["latency_s"], "sweep": sweep,
-            "per_request_fp64": {"applications_per_s": apps / t_seq, "requests_per_s": len(items) / t_seq,
-                                 "seconds": t_seq,
-                                 "note": "same requests in arrival order, sg_propagate FP64, one at a time; "
-                                         "applications counted as in the server runs"}}
+            "latency_s": head["latency_s"], "sweep": sweep, "fp64_server": fp64_server,
+            "per_request": {
+                "fp64": dict(per_request["fp64"], requests_per_s=per_request["fp64"]["requests"] /
+                             per_request["fp64"]["seconds"]),
+                "mixed": dict(per_request["mixed"], requests_per_s=per_request["mixed"]["requests"] /
+                              per_request["mixed"]["seconds"]),
+                "note": "propagation requests in arrival order, sg_propagate, one at a time"},
+            "accuracy_mixed_vs_fp64_server": {
+                "psi_l2_error": q(psi_err), "energy_drift_mixed": q(drift_m), "energy_drift_fp64": q(drift_64),
+                "eigenvalue_error": q(eig_err)}}
 
 
 def run_batched(args, sg, synth, torch):
@@ -389,16 +447,25 @@ def run_batched(args, sg, synth, torch):
     return out
 
 
-def time_device(ctx, xd, yd, nvec, steps, warmup, flush, torch, sg):
+def time_device(ctx, xd, yd, nvec, steps, warmup, flush, torch, sg, sharded_terms=False):
+    """Per-step CUDA-event times of sg_apply_H (or, with sharded_terms, of this
+    rank's share of the terms, the integer all-reduce and the finish)."""
     stream = torch.cuda.current_stream()
+    acc = None
+    if sharded_terms:
+        from paper_2111_13655_gb300 import sharded
+        acc = torch.zeros(sg.acc_words(ctx, nvec), dtype=torch.int64, device="cuda")
+        apply = lambda: sharded.apply_H_sharded(ctx, xd, yd, nvec, acc=acc, stream=stream)
+    else:
+        apply = lambda: sg.sg_apply_H(ctx, xd, yd, nvec, stream)
     for _ in range(warmup):
-        sg.sg_apply_H(ctx, xd, yd, nvec, stream)
+        apply()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for i in range(steps):
         flush.zero_()                       # L2 flush, outside the timed interval
         ev[i][0].record(stream)
-        sg.sg_apply_H(ctx, xd, yd, nvec, stream)
+        apply()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in ev]
@@ -417,11 +484,13 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-eig-every", type=int, default=8, help="every n-th request is an eigen request (0: none)")
     ap.add_argument("--serve-rates", default="10,100,1000")
     ap.add_argument("--serve-dmax", type=int, default=20)
     ap.add_argument("--serve-lmax", type=int, default=6)
-    ap.add_argument("--serve-steps-max", type=int, default=100)
+    ap.add_argument("--serve-steps-max", type=int, default=200)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-only", action="store_true", help="only the serving leg (its JSON line alone)")
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-batched", action="store_true")
@@ -429,6 +498,9 @@ def main():
     ap.add_argument("--precisions", default="mixed,fp64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--peak-seconds", type=float, default=1.0, help="0: skip the peak measurement")
+    ap.add_argument("--sharding", default="replicas", choices=["replicas", "terms"],
+                    help="N > 1: independent replicas (weak scaling) or one problem's terms split over the "
+                         "ranks with one integer all-reduce per apply (strong scaling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -439,6 +511,10 @@ def main():
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.serving_only:
+        # the serving leg alone (used for the longer streams of the serving configuration)
+        print(json.dumps({"metric": METRIC, "serving": run_serving(args, sg, synth, torch)}), flush=True)
+        return 0
     rep = Replicas("nccl")
     world, rank = rep.world, rep.rank
     barrier = rep.barrier
@@ -467,7 +543,8 @@ def main():
     for prec in args.precisions.split(","):
         ctx = sg.sg_create(p, prec)
         n = ctx.n_cs
-        x = synth.random_vectors(n, nvec, 11 + rank)
+        # replicas: independent inputs per rank; term sharding: one problem, the same x everywhere
+        x = synth.random_vectors(n, nvec, 11 + (0 if args.sharding == "terms" else rank))
         xd = torch.from_numpy(x).cuda()
         yd = torch.empty_like(xd)
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -476,7 +553,8 @@ def main():
         barrier()
         torch.cuda.synchronize()
         with ClockSampler(torch.cuda.current_device()) as clk:
-            times = time_device(ctx, xd, yd, nvec, steps, warm, flush, torch, sg)
+            times = time_device(ctx, xd, yd, nvec, steps, warm, flush, torch, sg,
+                                sharded_terms=args.sharding == "terms" and world > 1)
         barrier()
         torch.cuda.synchronize()
         total_ms = rep.max_over_ranks(sum(times))
@@ -489,8 +567,10 @@ def main():
         peak = peaks["fp32"] if prec == "mixed" else peaks["fp64"]
         achieved = f_alg / (statistics.mean(times) * 1e-3) / 1e12
         frac = achieved / peak if peak else None
+        units = nvec * steps if args.sharding == "terms" and world > 1 else None
         results[prec] = {
-            "value": replica_throughput(world, nvec * steps, total_ms * 1e-3), "ms_per_step": ms, "steps": steps,
+            "value": (units / (total_ms * 1e-3) if units else replica_throughput(world, nvec * steps, total_ms * 1e-3)),
+            "ms_per_step": ms, "steps": steps,
             "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": frac,
@@ -531,7 +611,8 @@ def main():
         f = results.get("fp64")
         line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": m["steps"],
                 "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if "mixed" in results else "f64",
+                "scaling": "strong" if args.sharding == "terms" and world > 1 else "weak", "vs_baseline": None,
+                "dtype": "f32" if "mixed" in results else "f64",
                 "data": "synthetic", "config": bench_config(args, world),
                 "latency_ms": m["latency_ms"], "roofline": m["roofline"], "clocks": m["clocks"],
                 "e2e": m.get("e2e"), "gpu_launches": LAUNCHES_PER_APPLY * m["steps"],

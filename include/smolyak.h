@@ -147,6 +147,35 @@ sg_status sg_apply_H_host(sg_ctx *ctx, const double *x_host, double *y_host, int
                           void *stream);
 
 /*
+ * Term-sharded apply: the terms of Eq. (16) are independent (the term loop of
+ * Alg. 1; the paper's parallel scheme 1, Alg. 2, splits them over MPI ranks
+ * and sums the partial results).  Part `part` of `nparts` takes the terms at
+ * processing positions p = part (mod nparts) -- the processing order is by
+ * decreasing cost, so the parts are balanced -- and adds their contributions
+ * exactly into fixed-point accumulators; summing the accumulators of all parts
+ * as 64-bit integers (wrapping) and finishing gives bitwise the result of
+ * sg_apply_H, whatever nparts.  A multi-GPU apply runs one part per GPU (each
+ * with its own context of the same problem and the same x), one integer
+ * all-reduce (sum) of acc, and sg_apply_H_finish.
+ *
+ * sg_apply_H_part -- adds the part's contributions for nvec vectors into acc.
+ *   x    DEVICE, as for sg_apply_H.
+ *   acc  DEVICE, N_cs * nvec * w int64 words (w = 1 for SG_MIXED, 4 for SG_FP64),
+ *        entry-major (entry r, vector v at (r * nvec + v) * w); zero before the
+ *        first part is added (cudaMemset), accumulated into by each part.
+ * sg_apply_H_finish -- y = H_S x from the summed accumulators of all parts
+ *   (and the harmonic part applied in the compact basis); clears acc to zero.
+ *   x, y as for sg_apply_H (x the same vectors the parts were given).
+ * sg_part_size -- the terms of a part and their summed cost estimate (host;
+ *   also on contexts made by sg_plan).  Any output may be NULL.
+ * Both device calls are enqueued on `stream`.
+ */
+sg_status sg_apply_H_part(sg_ctx *ctx, const double *x, int nvec, int part, int nparts, int64_t *acc,
+                          void *stream);
+sg_status sg_apply_H_finish(sg_ctx *ctx, const double *x, int64_t *acc, double *y, int nvec, void *stream);
+sg_status sg_part_size(const sg_ctx *ctx, int part, int nparts, int64_t *n_terms, int64_t *cost);
+
+/*
  * sg_apply_H_noalloc -- the operation of sg_apply_H, with the same arguments
  * and results, for callers that may not allocate device memory when they
  * apply H (e.g. a process whose device memory is all held by another

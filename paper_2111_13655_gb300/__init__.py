@@ -93,6 +93,9 @@ SIGNATURES = {
     "sg_apply_H": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "sg_apply_H_host": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "sg_apply_H_noalloc": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "sg_apply_H_part": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
+    "sg_apply_H_finish": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
+    "sg_part_size": (_i32, [_vp, _i32, _i32, _P64, _P64]),
     "sg_term_levels": (_i32, [_vp, _i64, _i64, _vp, _vp]),
     "sg_index_map": (_i32, [_vp, _i64, _i64, _vp, _vp, _vp]),
     "sg_compact_rank": (_i32, [_vp, _vp, _i64, _vp]),
@@ -264,6 +267,43 @@ def sg_apply_H_noalloc(ctx: Ctx, x, y, nvec: int = None, stream=None) -> None:
     xp = _dev_ptr(x, nvec * ctx.n_cs, "x")
     yp = _dev_ptr(y, nvec * ctx.n_cs, "y")
     _check(lib().sg_apply_H_noalloc(ctx.ptr, xp, yp, int(nvec), _stream_ptr(stream)), ctx)
+
+
+def acc_words(ctx: Ctx, nvec: int) -> int:
+    """int64 words of the fixed-point accumulators of nvec vectors (sg_apply_H_part)."""
+    return ctx.n_cs * nvec * (1 if ctx.precision == SG_MIXED else 4)
+
+
+def _acc_ptr(acc, n_expected: int):
+    import torch
+    if not isinstance(acc, torch.Tensor) or not acc.is_cuda or acc.dtype != torch.int64 or not acc.is_contiguous():
+        raise TypeError("acc must be a contiguous int64 CUDA tensor")
+    if acc.numel() != n_expected:
+        raise ValueError(f"acc has {acc.numel()} elements, expected {n_expected}")
+    return acc.data_ptr()
+
+
+def sg_apply_H_part(ctx: Ctx, x, acc, nvec: int, part: int, nparts: int, stream=None) -> None:
+    """Adds the contributions of the terms at processing positions p = part
+    (mod nparts) into the int64 accumulators acc (device, acc_words(ctx, nvec))."""
+    xp = _dev_ptr(x, nvec * ctx.n_cs, "x")
+    _check(lib().sg_apply_H_part(ctx.ptr, xp, int(nvec), int(part), int(nparts),
+                                 _acc_ptr(acc, acc_words(ctx, nvec)), _stream_ptr(stream)), ctx)
+
+
+def sg_apply_H_finish(ctx: Ctx, x, acc, y, nvec: int, stream=None) -> None:
+    """y = H_S x from the accumulators summed over all parts; clears acc."""
+    xp = _dev_ptr(x, nvec * ctx.n_cs, "x")
+    yp = _dev_ptr(y, nvec * ctx.n_cs, "y")
+    _check(lib().sg_apply_H_finish(ctx.ptr, xp, _acc_ptr(acc, acc_words(ctx, nvec)), yp, int(nvec),
+                                   _stream_ptr(stream)), ctx)
+
+
+def sg_part_size(ctx: Ctx, part: int, nparts: int):
+    """(terms, summed cost estimate) of one part of a term-sharded apply (host)."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().sg_part_size(ctx.ptr, int(part), int(nparts), ctypes.byref(a), ctypes.byref(b)), ctx)
+    return a.value, b.value
 
 
 def sg_apply_H_host(ctx: Ctx, x_host, y_host, nvec: int = None, stream=None) -> None:

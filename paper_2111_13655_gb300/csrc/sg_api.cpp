@@ -142,6 +142,7 @@ sg_status plan(int D, int L, const sg_basis *basis, const sg_grid *grids,
     kp.D = D; kp.L = L; kp.Dpad = T.Dpad;
     kp.nmono = (int)p.mcoef.size(); kp.pmax = T.pmax; kp.kw = T.kw;
     kp.n_cs = (int)T.n_cs; kp.n_terms = T.n_terms;
+    kp.part = 0; kp.nparts = 1;
     kp.cap = T.cap; kp.maxnb = T.maxnb; kp.matcap = T.matcap; kp.vtabcap = T.vtabcap;
     *out = ctx;
     return SG_OK;
@@ -329,6 +330,59 @@ sg_status sg_apply_H(sg_ctx *ctx, const double *x, double *y, int nvec, void *st
     cudaError_t e = sg::launch_apply(ctx->kp, ctx->fp32, x, y, nvec, ctx->maxbits, nullptr,
                                      (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "apply launch");
+    return SG_OK;
+}
+
+sg_status sg_apply_H_part(sg_ctx *ctx, const double *x, int nvec, int part, int nparts, int64_t *acc, void *stream)
+{
+    if (!ctx) return SG_EINVAL;
+    if (!ctx->has_device) return fail(ctx, SG_EINVAL, "context was made by sg_plan (no device state)");
+    if (!sg_on_ctx_device(ctx)) return fail(ctx, SG_EINVAL, "the current CUDA device is not the one the context was made on");
+    if (!x || !acc) return fail(ctx, SG_EINVAL, "x or acc is NULL");
+    if (nvec < 1) return fail(ctx, SG_EINVAL, "nvec must be >= 1");
+    if (nparts < 1 || part < 0 || part >= nparts) return fail(ctx, SG_EINVAL, "need 0 <= part < nparts");
+    sg_status st = ensure_workspace(ctx, nvec, (cudaStream_t)stream);  // the per-vector exponents
+    if (st != SG_OK) return st;
+    sg::KParams kp = ctx->kp;
+    kp.acc = reinterpret_cast<unsigned long long *>(acc);
+    kp.part = part;
+    kp.nparts = nparts;
+    cudaError_t e = sg::launch_maxabs(kp, x, nvec, ctx->maxbits, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = sg::launch_apply_terms(kp, ctx->fp32, x, ctx->maxbits, nvec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "partial apply launch");
+    return SG_OK;
+}
+
+sg_status sg_apply_H_finish(sg_ctx *ctx, const double *x, int64_t *acc, double *y, int nvec, void *stream)
+{
+    if (!ctx) return SG_EINVAL;
+    if (!ctx->has_device) return fail(ctx, SG_EINVAL, "context was made by sg_plan (no device state)");
+    if (!sg_on_ctx_device(ctx)) return fail(ctx, SG_EINVAL, "the current CUDA device is not the one the context was made on");
+    if (!x || !y || !acc) return fail(ctx, SG_EINVAL, "x, y or acc is NULL");
+    if (nvec < 1) return fail(ctx, SG_EINVAL, "nvec must be >= 1");
+    const size_t n = (size_t)ctx->host.n_cs * nvec;
+    if ((x < y + n) && (y < x + n)) return fail(ctx, SG_EINVAL, "x and y overlap");
+    sg_status st = ensure_workspace(ctx, nvec, (cudaStream_t)stream);
+    if (st != SG_OK) return st;
+    sg::KParams kp = ctx->kp;
+    kp.acc = reinterpret_cast<unsigned long long *>(acc);
+    cudaError_t e = sg::launch_maxabs(kp, x, nvec, ctx->maxbits, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = sg::launch_finalize(kp, ctx->fp32, x, y, nvec, ctx->maxbits, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "finish launch");
+    return SG_OK;
+}
+
+sg_status sg_part_size(const sg_ctx *ctx, int part, int nparts, int64_t *n_terms, int64_t *cost)
+{
+    if (!ctx || nparts < 1 || part < 0 || part >= nparts) return SG_EINVAL;
+    const sg::HostTables &T = ctx->host;
+    int64_t c = 0, k = 0;
+    for (int64_t p = part; p < T.n_terms; p += nparts) {
+        c += T.pcost[(size_t)p];
+        k++;
+    }
+    if (n_terms) *n_terms = k;
+    if (cost) *cost = c;
     return SG_OK;
 }
 

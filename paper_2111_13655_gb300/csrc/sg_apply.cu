@@ -218,7 +218,9 @@ __global__ void __launch_bounds__(kThreads) k_apply(const KParams P, const doubl
     T *bufB = bufA + P.cap;
     int *rk = reinterpret_cast<int *>(bufB + P.cap);
 
-    const int t = P.order[blockIdx.x];
+    const int64_t q = (int64_t)blockIdx.x * P.nparts + P.part;  // this part's processing positions
+    if (q >= P.n_terms) return;
+    const int t = P.order[q];
     if (tid == 0) decode_term(P, t, H, m1, m2, pr, mg);
     __syncthreads();
     if (H.bad) {
@@ -455,27 +457,25 @@ __global__ void k_maxabs_batch(const double *__restrict__ x, const long long *__
     if ((threadIdx.x & 31) == 0 && mb) atomicMax(maxbits + (size_t)j * nvec + v, mb);
 }
 
-// Many problems: y = (accumulated integer) * 2^E + esplit_j * x, entry by entry
-// over all problems' vectors; clears the accumulators.
+// Many problems: y = (accumulated integer) * 2^E + esplit_j * x, entry by entry;
+// blockIdx.y = problem (its entries start at nvec * cs_prefix[j]); clears the
+// accumulators.
 __global__ void k_finalize_batch(const KParams *__restrict__ kps, const long long *__restrict__ cs_prefix,
-                                 int nprob, const double *__restrict__ x, double *__restrict__ y,
+                                 const double *__restrict__ x, double *__restrict__ y,
                                  unsigned long long *acc, const long long *__restrict__ maxbits, int nvec,
                                  int fp32)
 {
-    const size_t total = (size_t)nvec * (size_t)cs_prefix[nprob];
-    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-        int lo = 0, hi = nprob - 1;  // last problem whose block starts at or before g
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if ((size_t)nvec * (size_t)cs_prefix[mid] <= g) lo = mid; else hi = mid - 1;
-        }
-        const size_t n = (size_t)(cs_prefix[lo + 1] - cs_prefix[lo]);
-        const size_t i = g - (size_t)nvec * (size_t)cs_prefix[lo];
+    const int j = blockIdx.y;
+    const size_t base = (size_t)nvec * (size_t)cs_prefix[j];
+    const size_t n = (size_t)(cs_prefix[j + 1] - cs_prefix[j]);
+    const size_t total = (size_t)nvec * n;
+    const double *esplit = kps[j].esplit;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int v = (int)(i / n);
         const size_t r = i - (size_t)v * n;
-        const size_t a = (size_t)nvec * (size_t)cs_prefix[lo] + r * nvec + v;  // entry-major in its problem
-        y[g] = finalize_value(acc + a * acc_words(fp32), maxbits[(size_t)lo * nvec + v], fp32) +
-               kps[lo].esplit[r] * x[g];
+        const size_t a = base + r * nvec + v;  // entry-major in its problem
+        y[base + i] = finalize_value(acc + a * acc_words(fp32), maxbits[(size_t)j * nvec + v], fp32) +
+                      esplit[r] * x[base + i];
     }
 }
 
@@ -540,24 +540,25 @@ cudaError_t launch_apply(const KParams &kp, bool fp32, const double *x, double *
                          long long *maxbits, int *lsb_exp, cudaStream_t stream)
 {
     (void)lsb_exp;
-    const size_t smem = apply_smem_bytes(kp, fp32);
+    cudaError_t e = launch_maxabs(kp, x, nvec, maxbits, stream);
+    if (e == cudaSuccess) e = launch_apply_terms(kp, fp32, x, maxbits, nvec, stream);
+    if (e == cudaSuccess) e = launch_finalize(kp, fp32, x, y, nvec, maxbits, stream);
+    return e;
+}
+
+cudaError_t launch_maxabs(const KParams &kp, const double *x, int nvec, long long *maxbits, cudaStream_t stream)
+{
     cudaError_t e = cudaMemsetAsync(maxbits, 0, sizeof(long long) * nvec, stream);
     if (e != cudaSuccess) return e;
-    dim3 gmax(64, nvec);
-    k_maxabs<<<gmax, 256, 0, stream>>>(x, kp.n_cs, maxbits);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (kp.fast.enabled) {
-        if ((e = launch_apply_fast(kp, fp32, x, nvec, maxbits, stream)) != cudaSuccess) return e;
-    } else if (kp.n_terms > 0) {
-        dim3 grid((unsigned)kp.n_terms);
-        if (fp32)
-            k_apply<float><<<grid, kThreads, smem, stream>>>(kp, x, maxbits, nvec);
-        else
-            k_apply<double><<<grid, kThreads, smem, stream>>>(kp, x, maxbits, nvec);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    k_maxabs<<<dim3(64, nvec), 256, 0, stream>>>(x, kp.n_cs, maxbits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const KParams &kp, bool fp32, const double *x, double *y, int nvec,
+                            const long long *maxbits, cudaStream_t stream)
+{
     const size_t total = (size_t)nvec * kp.n_cs;
-    const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 16);
+    const unsigned blocks = (unsigned)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, 152 * 16));
     k_finalize<<<blocks, 256, 0, stream>>>(kp, x, y, maxbits, nvec, fp32 ? 1 : 0);
     return cudaGetLastError();
 }
@@ -566,9 +567,9 @@ cudaError_t launch_apply_terms(const KParams &kp, bool fp32, const double *x, co
                                cudaStream_t stream)
 {
     if (kp.fast.enabled) return launch_apply_fast(kp, fp32, x, nvec, maxbits, stream);
-    if (kp.n_terms == 0) return cudaSuccess;
+    if (kp.n_terms <= kp.part) return cudaSuccess;
     const size_t smem = apply_smem_bytes(kp, fp32);
-    dim3 grid((unsigned)kp.n_terms);
+    dim3 grid((unsigned)((kp.n_terms - kp.part + kp.nparts - 1) / kp.nparts));
     if (fp32)
         k_apply<float><<<grid, kThreads, smem, stream>>>(kp, x, maxbits, nvec);
     else
@@ -590,9 +591,11 @@ cudaError_t launch_finalize_batch(const KParams *kps, const long long *cs_prefix
                                   const double *x, double *y, unsigned long long *acc, const long long *maxbits,
                                   int nvec, bool fp32, cudaStream_t stream)
 {
-    const size_t total = (size_t)nvec * (size_t)total_cs;
-    const unsigned blocks = (unsigned)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, 152 * 16));
-    k_finalize_batch<<<blocks, 256, 0, stream>>>(kps, cs_prefix, nprob, x, y, acc, maxbits, nvec, fp32 ? 1 : 0);
+    // blocks per problem: enough for the average problem, at least one
+    const size_t per = (size_t)nvec * (size_t)total_cs / (size_t)std::max(1, nprob);
+    const unsigned bx = (unsigned)std::max<size_t>(1, std::min<size_t>((per + 255) / 256, 64));
+    k_finalize_batch<<<dim3(bx, (unsigned)nprob), 256, 0, stream>>>(kps, cs_prefix, x, y, acc, maxbits, nvec,
+                                                                    fp32 ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -36,6 +36,13 @@ struct sg_batch {
     unsigned long long *acc = nullptr;
     long long *maxbits = nullptr;
     int acc_nvec = 0;
+    // the apply's launch sequence captured as a graph, for the last (x, y, nvec, stream)
+    cudaGraphExec_t graph = nullptr;
+    const double *gx = nullptr;
+    double *gy = nullptr;
+    int gnvec = 0;
+    cudaStream_t gstream = nullptr;
+    int64_t graph_launches = 0;
     std::string last_error;
 };
 
@@ -61,8 +68,19 @@ sg_status bupload(sg_batch *b, const std::vector<T> &v, const T **dst)
     return SG_OK;
 }
 
+void drop_graph(sg_batch *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->gx = nullptr;
+    b->gy = nullptr;
+    b->gnvec = 0;
+    b->gstream = nullptr;
+}
+
 void free_all(sg_batch *b)
 {
+    drop_graph(b);
     for (void *p : b->allocations) cudaFree(p);
     b->allocations.clear();
     if (b->acc) cudaFree(b->acc);
@@ -176,6 +194,8 @@ extern "C" sg_status sg_batch_size(const sg_batch *b, int64_t *n_cs_total, int64
     return SG_OK;
 }
 
+sg_status enqueue_apply(sg_batch *b, const double *x, double *y, int nvec, cudaStream_t s);
+
 extern "C" sg_status sg_apply_H_batch(sg_batch *b, const double *x, double *y, int nvec, void *stream)
 {
     if (!b) return SG_EINVAL;
@@ -193,6 +213,7 @@ extern "C" sg_status sg_apply_H_batch(sg_batch *b, const double *x, double *y, i
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
     if (nvec > b->acc_nvec) {
+        drop_graph(b);  // it names the old workspace
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
             return bfail(b, SG_ECUDA, std::string("stream synchronize: ") + cudaGetErrorString(e));
         if (b->acc) cudaFree(b->acc);
@@ -208,6 +229,41 @@ extern "C" sg_status sg_apply_H_batch(sg_batch *b, const double *x, double *y, i
             return bfail(b, SG_ECUDA, std::string("workspace memset: ") + cudaGetErrorString(e));
         b->acc_nvec = nvec;
     }
+    // Replay the captured launch sequence when the same buffers, block size and
+    // stream come back; capture it on first use.  Not on the legacy default
+    // stream (it cannot be captured) nor while the caller is capturing the
+    // stream itself (the launches then go into the caller's graph).
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (s != nullptr && (e = cudaStreamIsCapturing(s, &cs)) != cudaSuccess)
+        return bfail(b, SG_ECUDA, std::string("stream capture query: ") + cudaGetErrorString(e));
+    if (s != nullptr && cs == cudaStreamCaptureStatusNone) {
+        if (!(b->graph && b->gx == x && b->gy == y && b->gnvec == nvec && b->gstream == s)) {
+            drop_graph(b);
+            cudaGraph_t g = nullptr;
+            if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                return bfail(b, SG_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+            const sg_status st = enqueue_apply(b, x, y, nvec, s);
+            e = cudaStreamEndCapture(s, &g);
+            if (st != SG_OK) { if (g) cudaGraphDestroy(g); return st; }
+            if (e != cudaSuccess) return bfail(b, SG_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&b->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) { b->graph = nullptr; return bfail(b, SG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e)); }
+            b->gx = x; b->gy = y; b->gnvec = nvec; b->gstream = s;
+        }
+        if ((e = cudaGraphLaunch(b->graph, s)) != cudaSuccess)
+            return bfail(b, SG_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+        b->graph_launches++;
+        return SG_OK;
+    }
+    return enqueue_apply(b, x, y, nvec, s);
+}
+
+// The launch sequence of one batched apply: max|x|, term kernels, finalisation.
+sg_status enqueue_apply(sg_batch *b, const double *x, double *y, int nvec, cudaStream_t s)
+{
+    const int nprob = (int)b->ctxs.size();
+    cudaError_t e;
     if ((e = sg::launch_maxabs_batch(x, b->d_cs_prefix, nprob, b->max_ncs, nvec, b->maxbits, s)) != cudaSuccess)
         return bfail(b, SG_ECUDA, std::string("max|x| launch: ") + cudaGetErrorString(e));
     for (const auto &G : b->groups)

@@ -726,7 +726,7 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
 template <typename T, int GS>
 __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? SG_F32_MINBLOCKS : SG_F64_MINBLOCKS)
     k_apply_fast(const KParams P, const double *__restrict__ x, const long long *__restrict__ maxbits, int nvec,
-                 int p0, int pcount, int work_cap)
+                 int p0, int pcount, int pstride, int work_cap)
 {
     constexpr int NG = kFT / GS;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -734,7 +734,7 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? SG_F32_MINBLOCKS : SG_F6
     const int grp = threadIdx.x / GS, tid = threadIdx.x % GS;
     const int pidx = blockIdx.x * NG + grp;
     if (pidx >= pcount) return;
-    fast_term<T, GS>(P, x, P.acc, maxbits, nvec, p0 + pidx, work_cap,
+    fast_term<T, GS>(P, x, P.acc, maxbits, nvec, p0 + pidx * pstride, work_cap,
                      smraw + (size_t)grp * part_bytes(P, sizeof(T), work_cap), Hs[grp], tid);
 }
 
@@ -788,16 +788,30 @@ cudaError_t launch_t(const KParams &kp, const FastLaunch &a)
     const size_t smem_warp = (size_t)(kFT / 32) * part_bytes(kp, rb, kp.fast.work_warp);
     if (a.configure) {
         cudaError_t e = set_smem_limit(k_apply_fast<T, kFT>, smem_cta);
-        if (e != cudaSuccess) return e;
-        return set_smem_limit(k_apply_fast<T, 32>, smem_warp);
+        if (e == cudaSuccess) e = set_smem_limit(k_apply_fast<T, 32>, smem_warp);
+        return e;
     }
     const int nbig = kp.fast.n_big, nrest = (int)kp.n_terms - nbig;
+    if (kp.nparts > 1) {
+        // one part of a term-sharded apply: positions p = part (mod nparts) of each form
+        const int G = kp.nparts, r = kp.part;
+        const int cb = nbig > r ? (nbig - r + G - 1) / G : 0;
+        const int p1 = nbig + ((r - nbig) % G + G) % G;
+        const int cw = (int)kp.n_terms > p1 ? ((int)kp.n_terms - p1 + G - 1) / G : 0;
+        if (cb > 0)
+            k_apply_fast<T, kFT><<<(unsigned)cb, kFT, smem_cta, a.stream>>>(kp, a.x, a.maxbits, a.nvec, r, cb, G,
+                                                                          kp.fast.work_cta);
+        if (cw > 0)
+            k_apply_fast<T, 32><<<(unsigned)((cw + kFT / 32 - 1) / (kFT / 32)), kFT, smem_warp, a.stream>>>(
+                kp, a.x, a.maxbits, a.nvec, p1, cw, G, kp.fast.work_warp);
+        return cudaGetLastError();
+    }
     if (nbig > 0)
-        k_apply_fast<T, kFT><<<(unsigned)nbig, kFT, smem_cta, a.stream>>>(kp, a.x, a.maxbits, a.nvec, 0, nbig,
+        k_apply_fast<T, kFT><<<(unsigned)nbig, kFT, smem_cta, a.stream>>>(kp, a.x, a.maxbits, a.nvec, 0, nbig, 1,
                                                                         kp.fast.work_cta);
     if (nrest > 0) {
         const unsigned blocks = (unsigned)((nrest + kFT / 32 - 1) / (kFT / 32));
-        k_apply_fast<T, 32><<<blocks, kFT, smem_warp, a.stream>>>(kp, a.x, a.maxbits, a.nvec, nbig, nrest,
+        k_apply_fast<T, 32><<<blocks, kFT, smem_warp, a.stream>>>(kp, a.x, a.maxbits, a.nvec, nbig, nrest, 1,
                                                                 kp.fast.work_warp);
     }
     return cudaGetLastError();

@@ -51,16 +51,20 @@ constexpr int kMaxPairs = 64;  // coupled mode pairs handled by the fast path
 #ifndef SG_F32_MINBLOCKS
 #define SG_F32_MINBLOCKS 4
 #endif
+// (defaults: the plan sg_tune picks at D=12 L=10 in both precisions; FP64
+// 165.6 -> 149.2 ms per 8-vector apply against a target of 4 vectors)
 #ifndef SG_F32_SLICE_VT
-#define SG_F32_SLICE_VT 2
+#define SG_F32_SLICE_VT 1
 #endif
 #ifndef SG_F64_SLICE_VT
-#define SG_F64_SLICE_VT 4
+#define SG_F64_SLICE_VT 1
 #endif
 // Warp form: terms that fit a quarter of the block's shared memory with a
 // chunk of SG_WARP_VT vectors (sliced when SG_WARP_SLICE is 1) run one per warp.
 // Measured at D=12 L=10 (mixed): 1 vector 31.29 ms per 8-vector apply, 4
-// vectors 31.85; slicing in the warp form 43-60 ms.
+// vectors 31.85, 2 vectors 30.9 (sg_tune's pick there); slicing in the warp
+// form 43-60 ms.  1 is kept: the 256-wavepacket batch (nb = nq = l+1) is 12%
+// slower with 2.
 #ifndef SG_WARP_VT
 #define SG_WARP_VT 1
 #endif
@@ -190,6 +194,8 @@ struct KParams {
     int matcap;    // per-term 1D matrices
     int vtabcap;   // per-term potential tables
     int *err;      // device error word (0 = fine)
+    // term-sharded applies: only processing positions p with p % nparts == part
+    int part, nparts;
 };
 
 // Host-side description of a problem (after validation).
@@ -267,6 +273,12 @@ cudaError_t launch_apply_fast(const KParams &kp, bool fp32, const double *x, int
 // without the max|x| and finalisation passes; those two over all problems.
 cudaError_t launch_apply_terms(const KParams &kp, bool fp32, const double *x, const long long *maxbits, int nvec,
                                cudaStream_t stream);
+// The passes around the term kernels of one problem: per-vector max|x| bits
+// (zeroed first), and y = (accumulated integer) * 2^E + esplit * x, which also
+// clears kp.acc.
+cudaError_t launch_maxabs(const KParams &kp, const double *x, int nvec, long long *maxbits, cudaStream_t stream);
+cudaError_t launch_finalize(const KParams &kp, bool fp32, const double *x, double *y, int nvec,
+                            const long long *maxbits, cudaStream_t stream);
 cudaError_t launch_maxabs_batch(const double *x, const long long *cs_prefix, int nprob, int64_t max_ncs, int nvec,
                                 long long *maxbits, cudaStream_t stream);
 cudaError_t launch_finalize_batch(const KParams *kps, const long long *cs_prefix, int nprob, int64_t total_cs,
