@@ -334,15 +334,18 @@ def run_serving(args, sg, synth, torch):
                       "requests_per_s": len(items) / makespan, "makespan_s": makespan,
                       "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}})
         mixed_res = res
+    arms = set(args.serve_arms.split(","))
     top = max(rates)
-    res64, makespan64, st64 = run_stream(sg, "fp64", items, factors, top, E, eig_args)
-    lat64 = np.array([r["latency"] for r in res64])
-    fp64_server = {"rate_req_s": top, "applications_per_s": st64["applications"] / makespan64,
-                   "requests_per_s": len(items) / makespan64, "makespan_s": makespan64,
-                   "latency_s": {"p50": float(np.percentile(lat64, 50)), "p99": float(np.percentile(lat64, 99))}}
+    fp64_server, res64 = None, None
+    if "fp64" in arms:
+        res64, makespan64, st64 = run_stream(sg, "fp64", items, factors, top, E, eig_args)
+        lat64 = np.array([r["latency"] for r in res64])
+        fp64_server = {"rate_req_s": top, "applications_per_s": st64["applications"] / makespan64,
+                       "requests_per_s": len(items) / makespan64, "makespan_s": makespan64,
+                       "latency_s": {"p50": float(np.percentile(lat64, 50)), "p99": float(np.percentile(lat64, 99))}}
     # per-request accuracy of the mixed server against the FP64 server
     psi_err, drift_m, drift_64, eig_err = [], [], [], []
-    for rm, r64 in zip(mixed_res, res64):
+    for rm, r64 in zip(mixed_res, res64 or []):
         if rm["kind"] == "prop":
             psi_err.append(float(np.linalg.norm(rm["psi"] - r64["psi"])))
             if len(rm["energy"]):
@@ -353,7 +356,7 @@ def run_serving(args, sg, synth, torch):
     # the propagation requests one at a time, sg_propagate, each precision
     prop = [(it, f) for j, (it, f) in enumerate(zip(items, factors)) if not (E and j % E == E - 1)]
     per_request = {}
-    for prec in ("fp64", "mixed"):
+    for prec in (("fp64", "mixed") if "per_request" in arms else ()):
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         apps = 0
@@ -374,12 +377,13 @@ def run_serving(args, sg, synth, torch):
     return {"workload": desc, "precision": "mixed (server, continuous batching)",
             "applications_per_s": head["applications_per_s"], "rate_req_s": head["rate_req_s"],
             "latency_s": head["latency_s"], "sweep": sweep, "fp64_server": fp64_server,
-            "per_request": {
+            "per_request": ({
                 "fp64": dict(per_request["fp64"], requests_per_s=per_request["fp64"]["requests"] /
                              per_request["fp64"]["seconds"]),
                 "mixed": dict(per_request["mixed"], requests_per_s=per_request["mixed"]["requests"] /
                               per_request["mixed"]["seconds"]),
-                "note": "propagation requests in arrival order, sg_propagate, one at a time"},
+                "note": "propagation requests in arrival order, sg_propagate, one at a time"}
+                if per_request else None),
             "accuracy_mixed_vs_fp64_server": {
                 "psi_l2_error": q(psi_err), "energy_drift_mixed": q(drift_m), "energy_drift_fp64": q(drift_64),
                 "eigenvalue_error": q(eig_err)}}
@@ -485,6 +489,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve-eig-every", type=int, default=8, help="every n-th request is an eigen request (0: none)")
+    ap.add_argument("--serve-arms", default="mixed,fp64,per_request",
+                    help="serving arms: mixed (server at every rate), fp64 (server at the top rate), per_request")
     ap.add_argument("--serve-rates", default="10,100,1000")
     ap.add_argument("--serve-dmax", type=int, default=20)
     ap.add_argument("--serve-lmax", type=int, default=6)

@@ -163,7 +163,7 @@ int64_t planned_device_bytes(const sg_ctx *ctx)
     if (T.fast)
         bytes += b(T.pair_modes) + b(T.h1off) + b(T.goff) + b(T.ioff) + b(T.soff) + b(T.spoff) + b(T.fsc) +
                  b(T.ftab) * 3 / 2 + b(T.fdesc) + b(T.fdesc_off) + T.franks * (int64_t)sizeof(int) +
-                 b(T.fimg) / (ctx->fp32 ? 2 : 1) + b(T.fimg_off) + b(T.fvt_off) +
+                 b(T.fimg) / (ctx->fp32 ? 2 : 1) + b(T.fimg_off) + b(T.fvt_off) + b(T.frank_start) +
                  (T.fvt_off.empty() ? 0 : T.fvt_off.back()) * (ctx->fp32 ? 4 : 8);
     return bytes;
 }
@@ -230,6 +230,7 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
                     (st = upload(ctx, T.fdesc_off, &kp.fast.desc_off)) != SG_OK ||
                     (st = upload(ctx, T.fimg_off, &kp.fast.img_off)) != SG_OK ||
                     (st = upload(ctx, T.fvt_off, &kp.fast.mt_off)) != SG_OK ||
+                    (st = upload(ctx, T.frank_start, &kp.fast.rank_start)) != SG_OK ||
                     (ctx->fp32 ? (st = upload(ctx, std::vector<float>(T.fimg.begin(), T.fimg.end()),
                                               &kp.fast.imgf)) != SG_OK
                                : (st = upload(ctx, T.fimg, &kp.fast.imgd)) != SG_OK)))) {

@@ -458,7 +458,7 @@ __device__ __forceinline__ void gather_t(const FHdr &H, const KParams &P, const 
         const double *xv = x + (size_t)v * P.n_cs;
         T val[NBI];
 #pragma unroll
-        for (int i = 0; i < NBI; i++) val[i] = (T)__ldg(xv + __ldg(rp + i));
+        for (int i = 0; i < NBI; i++) val[i] = (T)__ldg(xv + rp[i]);
         T *dst = X + (size_t)w * NBI;
 #pragma unroll
         for (int i = 0; i < NBI; i += ZW) {
@@ -479,7 +479,7 @@ __device__ void gather_rt(const FHdr &H, const KParams &P, const double *__restr
     for (int w = tid; w < total; w += GS) {
         const int o = fdiv(w, vb, vmag), v = w - o * vb;
         for (int i = 0; i < NBI; i++)
-            X[(size_t)w * NBI + i] = (T)__ldg(x + (size_t)v * P.n_cs + __ldg(rk + (size_t)o * NBI + i));
+            X[(size_t)w * NBI + i] = (T)__ldg(x + (size_t)v * P.n_cs + rk[(size_t)o * NBI + i]);
     }
 }
 
@@ -552,7 +552,7 @@ __device__ void combine_add(const FHdr &H, const KParams &P, const int *__restri
     for (int w = tid; w < n; w += GS) {
         const int oi = fdiv(w, vb, vmag), v = w - oi * vb;  // oi = o * NBI + i
         const int o = fdiv(oi, NBI, nbimag), i = oi - o * NBI;
-        const int r = __ldg(rk + oi);
+        const int r = rk[oi];
         fx::Acc<T>::add(acc + ((size_t)r * nvec + v0 + v) * fx::Acc<T>::words, dst[(size_t)o * Pl + v * NBI + i],
                         H.coef, maxbits[v0 + v], P.err);
     }
@@ -589,17 +589,26 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
             l2_prefetch_bulk(reinterpret_cast<const unsigned char *>(FTab<T>::mt(P)) + b0, (unsigned)(b1 - b0));
         }
     }
-    // the term's image (B, B^T W, H1 per position, then its G tables) is copied
-    // as it lies while warp 0 decodes the record
+    // the term's image (B, B^T W, H1 per position, then its G tables) and its
+    // compact indices (M^B) are copied as they lie while warp 0 decodes the
+    // record (into a scratch at the end of the work area)
+    int *rks = reinterpret_cast<int *>(work);
     {
         const long long i0 = P.fast.img_off[p];
         const int isz = (int)(P.fast.img_off[p + 1] - i0);
         const T *img = FTab<T>::img(P) + i0;
         if (isz <= P.matcap + P.fast.gcap)
             for (int e = tid; e < isz; e += GS) mats[e] = img[e];
+        const long long r0 = P.fast.rank_start[p];
+        const int nr = (int)(P.fast.rank_start[p + 1] - r0);
+        if (ranks_elems(nr, U) <= work_cap)
+            for (int e = tid; e < nr; e += GS) rks[e] = __ldg(P.fast.ranks + r0 + e);
     }
     if (tid < 32) {
-        load_record(P, p, reinterpret_cast<int4 *>(work), H);
+        load_record(P, p,
+                    reinterpret_cast<int4 *>(reinterpret_cast<unsigned char *>(work) +
+                                             record_scratch_offset((int64_t)work_cap * rb, P.fast.desccap)),
+                    H);
         derive_layout<T>(P, nvec, work_cap, H);
     }
     gsync<GS>();
@@ -608,7 +617,7 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
         return;
     }
     const int m = H.m, R = H.R, NB = H.NB, NBI = H.NBI;
-    const int *rk = P.fast.ranks + H.rank_off;
+    const int *rk = rks;  // the term's compact indices, in shared memory
     const bool sliced = H.s > 0;
     const int ps = R + H.s;  // first non-sliced outer position
 
@@ -617,7 +626,7 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
         const int Pl = NBI * vb;                       // payload elements per site
         const int WW = Pl % U == 0 ? U : 1;            // unit of the vector accesses
         const int PW = Pl / WW;
-        T *X = work;
+        T *X = work + ranks_elems(NB, U);
         T *Y = X + pad_elems((int64_t)NB * vb, U);
         T *A = sliced ? Y + pad_elems((int64_t)NB * vb, U) : Y;
         T *Bf = A + pad_elems((int64_t)NBI * H.NGs * vb, U);

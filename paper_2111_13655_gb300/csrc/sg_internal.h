@@ -88,14 +88,27 @@ inline int fast_rmax(int nb1) { return nb1 == 2 ? 3 : nb1 == 3 ? 2 : 0; }
 // Sizes shared by the host planner and the fast kernels.
 // Padding of a buffer of n elements to a multiple of u elements (16 bytes).
 __host__ __device__ inline int64_t pad_elems(int64_t n, int u) { return (n + u - 1) / u * u; }
-// Work-area elements a chunk of vb vectors of one term needs: the gathered
-// basis tensor X (and the slice accumulator Y when the term is sliced), and
-// two buffers of the largest grid stage when the term has a grid (a term
-// without a grid has a second basis-sized buffer instead, for the staged
-// compress-add); every buffer padded to 16 bytes (u elements).
+// Elements (of a type with u per 16 bytes) that hold a term's NB int32
+// compact indices, padded to 16 bytes.
+__host__ __device__ inline int64_t ranks_elems(int64_t NB, int u) { return pad_elems((NB * u + 3) / 4, u); }
+// Work-area elements a chunk of vb vectors of one term needs: the term's
+// compact indices, the gathered basis tensor X (and the slice accumulator Y
+// when the term is sliced), and two buffers of the largest grid stage when the
+// term has a grid (a term without a grid has a second basis-sized buffer
+// instead, for the staged compress-add); every buffer padded to 16 bytes (u
+// elements).
 __host__ __device__ inline int64_t chunk_need(int64_t NB, int64_t stage, bool sliced, bool grid, int vb, int u)
 {
-    return (sliced || !grid ? 2 : 1) * pad_elems(NB * vb, u) + (grid ? 2 * pad_elems(stage * vb, u) : 0);
+    return ranks_elems(NB, u) + (sliced || !grid ? 2 : 1) * pad_elems(NB * vb, u) +
+           (grid ? 2 * pad_elems(stage * vb, u) : 0);
+}
+// Byte offset, inside a work area of `work_bytes`, of the scratch copy of a
+// term record (at most desccap 16-byte units) taken during the prologue: the
+// end of the area, 16-byte aligned.  The term's compact indices, copied at the
+// same time, occupy the start; the planner keeps the two apart.
+__host__ __device__ inline int64_t record_scratch_offset(int64_t work_bytes, int desccap)
+{
+    return ((work_bytes - 16 * (int64_t)desccap) / 16) * 16;
 }
 // Inner-block table per outer grid point: the upper triangle of the NBI x NBI
 // symmetric block (NBI (NBI+1)/2 values, row by row) in units of mt_unit
@@ -147,6 +160,7 @@ struct FastParams {
     const int4 *desc;      // term records (processing order)
     const unsigned *desc_off;  // [n_terms+1] record starts, in 16-byte units
     const int *ranks;      // compact index of every basis function of every term (layout order)
+    const long long *rank_start;  // [n_terms + 1] start of each term's indices in ranks (processing order)
     int desccap;           // largest record, in 16-byte units
     int gcap;              // largest set of a term's G tables, in words
     int nbocap;            // largest sliced outer block (slice weights)
@@ -236,6 +250,7 @@ struct HostTables {
     std::vector<int4> fdesc;          // term records
     std::vector<unsigned> fdesc_off;  // [n_terms+1]
     int64_t franks = 0;               // total compact indices (N_s)
+    std::vector<long long> frank_start;  // [n_terms + 1] start of each term's indices
     int fdesccap = 0, fgcap = 0, fnbocap = 1, fn_big = 0, fwork_cta = 0, fwork_warp = 0;
     int slice_vt = 0;                 // slicing target the records were planned with (0: default)
     int warp_vt = 0;                  // warp-form threshold the records were planned with (0: default)

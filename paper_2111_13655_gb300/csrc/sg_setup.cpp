@@ -643,7 +643,14 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
     // (sliced blocks larger than nbocap functions are not used: their slice
     // weights would not fit the group's head)
     const int nbocap = 64;
+    // the term's compact indices (start of the work area) and the record's
+    // scratch copy (its end) are written at the same time in the prologue
+    int rec_units = 1;  // largest record, in 16-byte units (pass 1)
+    auto ranks_fit = [&](const TermPlan &tp, int64_t work) {
+        return 4 * tp.NB <= record_scratch_offset(work * rb, rec_units);
+    };
     auto depth_for = [&](int t, const TermPlan &tp, int64_t work, int smax) {
+        if (!ranks_fit(tp, work)) return -1;
         if (!tp.grid) return chunk_need(tp.NB, 0, false, false, 1, U) <= work ? 0 : -1;
         const uint8_t *lt = &T.levels[(size_t)t * T.Dpad];
         for (int vt = vt0; vt >= 1; vt /= 2) {
@@ -664,6 +671,7 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
     for (int64_t q = 0; q < T.n_terms; q++) {
         plan_term(T.order[q], tp);
         gcap = std::max(gcap, tp.gsize);
+        rec_units = std::max(rec_units, 3 + tp.na + (int)tp.prs.size() + ((int)tp.inds.size() + 1) / 2);
         const uint8_t *lt = &T.levels[(size_t)T.order[q] * T.Dpad];
         int mat = 0;
         for (int j = 0; j < tp.na; j++) {
@@ -693,9 +701,7 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
     const int warp_vt = T.warp_vt > 0 ? T.warp_vt : SG_WARP_VT;
     const int warp_smax = SG_WARP_SLICE ? kMaxD : 0;
     auto fits_warp = [&](int t, const TermPlan &tp) {
-        if (work_warp <= 0 ||
-            (size_t)work_warp * rb < 16 * (3 + (size_t)tp.na + tp.prs.size() + (tp.inds.size() + 1) / 2))
-            return false;
+        if (work_warp <= 0 || !ranks_fit(tp, work_warp)) return false;
         if (!tp.grid) return chunk_need(tp.NB, 0, false, false, warp_vt, U) <= work_warp;
         for (int s = 0; s <= std::min(warp_smax, tp.na - tp.R); s++)
             if (chunk_need(tp.NB, stage_of(t, tp, s), s > 0, true, warp_vt, U) <= work_warp) return true;
@@ -715,6 +721,7 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
     T.fimg.reserve(img_total);
     T.fimg_off.assign(T.n_terms + 1, 0);
     T.fvt_off.assign(T.n_terms + 1, 0);
+    T.frank_start.assign(T.n_terms + 1, 0);
     int64_t rank_off = 0;
     for (int64_t q = 0; q < T.n_terms; q++) {
         const int t = T.order[q];
@@ -780,6 +787,7 @@ std::string build_fast_descs(const Problem &p, bool fp32, HostTables *Tp, int fb
         T.fdesc_off[q + 1] = (unsigned)(u0 + units);
         T.fdesccap = std::max(T.fdesccap, units);
         rank_off += tp.NB;
+        T.frank_start[q + 1] = rank_off;
     }
     if (T.fdesc.size() >= ((size_t)1 << 32)) return "fast-path records too large";
     T.franks = rank_off;

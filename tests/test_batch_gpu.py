@@ -127,3 +127,34 @@ def test_batch_rejects_mixed_precisions():
     finally:
         sg.sg_destroy(a)
         sg.sg_destroy(c)
+
+
+def test_graph_replays_on_a_stream_stay_bitwise_per_context():
+    """On a non-default stream the batched apply captures its launch sequence
+    once per (x, y, nvec, stream) and replays it: new input values, new
+    buffers and a new block size must all give each context's own result."""
+    probs = [synth.workload_C2(), synth.workload_C3(L=5), synth.chained_henon_heiles(5, 4, synth.draw_omega(5, 8), 0.2)]
+    for prec in ("mixed", "fp64"):
+        ctxs = [sg.sg_create(p, prec) for p in probs]
+        b = sg.sg_batch_create(ctxs)
+        s = torch.cuda.Stream()
+        try:
+            for call, nvec in enumerate((2, 2, 2, 3, 3)):
+                xs = [torch.from_numpy(synth.random_vectors(c.n_cs, nvec, 500 + 10 * call + j)).cuda().contiguous().view(-1)
+                      for j, c in enumerate(ctxs)]
+                x = torch.cat(xs)
+                if call == 2:
+                    x = x.clone()                  # new buffers at call 2
+                y = torch.full_like(x, float("nan"))
+                torch.cuda.synchronize()
+                with torch.cuda.stream(s):
+                    sg.sg_apply_H_batch(b, x, y, nvec, s)
+                s.synchronize()
+                ref = per_context(ctxs, xs, nvec)
+                for j in range(len(ctxs)):
+                    got = y[nvec * int(b.offsets[j]):nvec * int(b.offsets[j + 1])]
+                    assert torch.equal(got, ref[j]), (prec, call, j)
+        finally:
+            sg.sg_batch_destroy(b)
+            for c in ctxs:
+                sg.sg_destroy(c)
