@@ -300,12 +300,15 @@ def run_stream(sg, prec, items, factors, rate, eig_every, eig_args, seed=55):
     makespan = time.perf_counter() - t0
     res = []
     for kind, rid in ids:
-        if kind == "eig":
-            ev, rs, _, tm, nconv = srv.eig_result(rid)
-            res.append({"kind": "eig", "evals": ev, "latency": tm[1], "converged": nconv})
-        else:
-            psi, nl, el, tm = srv.result(rid)
-            res.append({"kind": "prop", "psi": psi, "energy": el, "latency": tm[1]})
+        try:
+            if kind == "eig":
+                ev, rs, _, tm, nconv = srv.eig_result(rid)
+                res.append({"kind": "eig", "evals": ev, "latency": tm[1], "converged": nconv})
+            else:
+                psi, nl, el, tm = srv.result(rid)
+                res.append({"kind": "prop", "psi": psi, "energy": el, "latency": tm[1]})
+        except sg.SgError as e:  # a refused or failed request is reported, not fatal
+            res.append({"kind": kind, "failed": str(e), "latency": None})
     stats = srv.stats()
     srv.close()
     return res, makespan, stats
@@ -321,31 +324,42 @@ def run_serving(args, sg, synth, torch):
     items = synth.workload_C5(args.serve_requests, seed=5, Ds=tuple(range(6, args.serve_dmax + 1)),
                               Ls=tuple(range(4, args.serve_lmax + 1)), steps=(20, args.serve_steps_max))
     factors = [synth.coherent_factors(q0, p.L + 1) for p, q0, _ in items]
-    rates = [float(r) for r in args.serve_rates.split(",")]
+    # "rate" or "rate:n" (a stream of the first n requests at that rate)
+    rates = [(float(r.split(":")[0]), min(len(items), int(r.split(":")[1])) if ":" in r else len(items))
+             for r in args.serve_rates.split(",")]
     eig_args = {"mixed": dict(nev=4, block=4, tol=1e-5, max_it=300),
                 "fp64": dict(nev=4, block=4, tol=1e-9, max_it=300)}
     E = args.serve_eig_every
     sweep = []
     mixed_res = None
-    for rate in rates:
-        res, makespan, st = run_stream(sg, "mixed", items, factors, rate, E, eig_args)
-        lat = np.array([r["latency"] for r in res])
-        sweep.append({"rate_req_s": rate, "applications_per_s": st["applications"] / makespan,
-                      "requests_per_s": len(items) / makespan, "makespan_s": makespan,
+    for rate, nreq in rates:
+        res, makespan, st = run_stream(sg, "mixed", items[:nreq], factors[:nreq], rate, E, eig_args)
+        lat = np.array([r["latency"] for r in res if "failed" not in r])
+        sweep.append({"rate_req_s": rate, "requests": nreq, "failed": sum("failed" in r for r in res),
+                      "applications_per_s": st["applications"] / makespan,
+                      "requests_per_s": nreq / makespan, "makespan_s": makespan,
                       "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}})
-        mixed_res = res
+        print("serving mixed:", json.dumps(sweep[-1]), file=sys.stderr, flush=True)
+        if mixed_res is None or len(res) > len(mixed_res):
+            mixed_res = res
     arms = set(args.serve_arms.split(","))
-    top = max(rates)
+    top = max(r for r, _ in rates)
     fp64_server, res64 = None, None
+    n64 = min(len(items), args.serve_fp64_requests) if args.serve_fp64_requests > 0 else len(items)
     if "fp64" in arms:
-        res64, makespan64, st64 = run_stream(sg, "fp64", items, factors, top, E, eig_args)
-        lat64 = np.array([r["latency"] for r in res64])
-        fp64_server = {"rate_req_s": top, "applications_per_s": st64["applications"] / makespan64,
-                       "requests_per_s": len(items) / makespan64, "makespan_s": makespan64,
+        res64, makespan64, st64 = run_stream(sg, "fp64", items[:n64], factors[:n64], top, E, eig_args)
+        lat64 = np.array([r["latency"] for r in res64 if "failed" not in r])
+        fp64_server = {"rate_req_s": top, "requests": n64, "failed": sum("failed" in r for r in res64),
+                       "applications_per_s": st64["applications"] / makespan64,
+                       "requests_per_s": n64 / makespan64, "makespan_s": makespan64,
                        "latency_s": {"p50": float(np.percentile(lat64, 50)), "p99": float(np.percentile(lat64, 99))}}
-    # per-request accuracy of the mixed server against the FP64 server
+        print("serving fp64:", json.dumps(fp64_server), file=sys.stderr, flush=True)
+    # per-request accuracy of the mixed server against the FP64 server (the
+    # requests both ran: the FP64 stream is the mixed one's first n64)
     psi_err, drift_m, drift_64, eig_err = [], [], [], []
     for rm, r64 in zip(mixed_res, res64 or []):
+        if "failed" in rm or "failed" in r64:
+            continue
         if rm["kind"] == "prop":
             psi_err.append(float(np.linalg.norm(rm["psi"] - r64["psi"])))
             if len(rm["energy"]):
@@ -354,7 +368,7 @@ def run_serving(args, sg, synth, torch):
         else:
             eig_err.append(float(np.max(np.abs(rm["evals"] - r64["evals"]))))
     # the propagation requests one at a time, sg_propagate, each precision
-    prop = [(it, f) for j, (it, f) in enumerate(zip(items, factors)) if not (E and j % E == E - 1)]
+    prop = [(it, f) for j, (it, f) in enumerate(zip(items[:n64], factors[:n64])) if not (E and j % E == E - 1)]
     per_request = {}
     for prec in (("fp64", "mixed") if "per_request" in arms else ()):
         torch.cuda.synchronize()
@@ -492,6 +506,8 @@ def main():
     ap.add_argument("--serve-arms", default="mixed,fp64,per_request",
                     help="serving arms: mixed (server at every rate), fp64 (server at the top rate), per_request")
     ap.add_argument("--serve-rates", default="10,100,1000")
+    ap.add_argument("--serve-fp64-requests", type=int, default=0,
+                    help="FP64 server and one-at-a-time arms on the stream's first n requests (0: all)")
     ap.add_argument("--serve-dmax", type=int, default=20)
     ap.add_argument("--serve-lmax", type=int, default=6)
     ap.add_argument("--serve-steps-max", type=int, default=200)

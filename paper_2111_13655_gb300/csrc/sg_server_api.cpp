@@ -430,13 +430,14 @@ sg_status admit(sg_server *s)
 }
 
 // One engine iteration with the current roles of X and P: Y = H X over all
-// active requests, then logs, recurrence update (into P) and state advance.
+// active requests, then logs, recurrence update (into P) and state advance,
+// over every two-vector slot (an eigen request holds several).
 sg_status enqueue_iteration(sg_server *s, double *X, double *P)
 {
     sg_status st = sg_apply_H_batch(s->batch, X, s->Y, 2, s->stream);
     if (st != SG_OK) return sfail(s, st, std::string("batched apply: ") + sg_batch_last_error(s->batch));
-    cudaError_t e = sg::launch_cheb_iteration(s->d_state, s->d_prefix, (int)s->active.size(), s->total, X, s->Y, P,
-                                              s->A, s->stream);
+    cudaError_t e = sg::launch_cheb_iteration(s->d_state, s->d_prefix, s->nslots, s->total, X, s->Y, P, s->A,
+                                              s->stream);
     if (e != cudaSuccess) return sfail(s, SG_ECUDA, std::string("recurrence update: ") + cudaGetErrorString(e));
     return SG_OK;
 }

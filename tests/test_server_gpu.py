@@ -2,7 +2,8 @@
 
 Checks: the closed-form phases at zero coupling; agreement with sg_propagate
 on the same problem; every request's result bitwise the same alone and in a
-mix whose membership changes while it runs (FP64 and mixed); admission by the
+mix whose membership changes while it runs (FP64 and mixed), also behind an
+eigen request that holds several batch slots; admission by the
 device-memory budget; requests without steps.
 """
 import numpy as np
@@ -215,8 +216,9 @@ def test_eigen_and_propagation_requests_identical_alone_and_in_a_mix(prec):
         srv.progress(4)                                    # R runs alone first
         ids["eA"] = srv.submit_eigs(P["A"], 4, block=2, tol=1e-7, max_it=200)
         srv.progress(3)                                    # eA joins R
-        ids["C"] = srv.submit(P["C"], 0.1, 3, order=32, factors=packet(P["C"]))
+        # eB holds two batch slots; C comes after it in slot order
         ids["eB"] = srv.submit_eigs(P["B"], 3, block=3, tol=1e-7, max_it=200)
+        ids["C"] = srv.submit(P["C"], 0.1, 3, order=32, factors=packet(P["C"]))
         seen = set()
         while True:
             a, q = srv.progress(2)
