@@ -43,9 +43,10 @@ WORKLOAD = "chained Henon-Heiles D=12 L=10 nb=l+1 nq=l+2 (N_cs=646646, 646646 te
 TRAFFIC_BYTES = {"mixed": None, "fp64": None}
 # FP32 lanes per SM (the unit count of the derived FP32 peak)
 FP32_LANES_PER_SM = 128
-# kernels of one sg_apply_H at this workload: k_maxabs, k_apply_fast (block form
-# over the large terms), k_apply_fast (warp form over the small terms), k_finalize
-LAUNCHES_PER_APPLY = 4
+# kernels of one sg_apply_H at this workload: k_maxabs, k_stage_x (entry-major
+# input copy), k_apply_fast (block form over the large terms), k_apply_fast
+# (warp form over the small terms), k_finalize
+LAUNCHES_PER_APPLY = 5
 
 
 def algorithmic_flops_per_vector(levels: np.ndarray, nbA=1, nbB=1, nqA=2, nqB=1, rmax=None) -> int:

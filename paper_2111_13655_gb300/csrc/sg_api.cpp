@@ -49,13 +49,16 @@ void free_all(sg_ctx *ctx)
     ctx->stage_x = ctx->stage_y = nullptr;
     if (ctx->acc) cudaFree(ctx->acc);
     if (ctx->maxbits) cudaFree(ctx->maxbits);
+    if (ctx->xs) cudaFree(ctx->xs);
     ctx->acc = nullptr;
     ctx->maxbits = nullptr;
+    ctx->xs = nullptr;
     ctx->acc_nvec = 0;
 }
 
 // Apply workspace for nvec vectors: fixed-point accumulators (zeroed here and
-// left zeroed by every apply) and the per-vector max|x| words.
+// left zeroed by every apply), the per-vector max|x| words and, for the fast
+// path, the entry-major input copy.
 sg_status ensure_workspace(sg_ctx *ctx, int nvec, cudaStream_t s)
 {
     if (nvec <= ctx->acc_nvec) return SG_OK;
@@ -63,13 +66,26 @@ sg_status ensure_workspace(sg_ctx *ctx, int nvec, cudaStream_t s)
     if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
     if (ctx->acc) cudaFree(ctx->acc);
     if (ctx->maxbits) cudaFree(ctx->maxbits);
+    if (ctx->xs) cudaFree(ctx->xs);
     ctx->acc = nullptr;
     ctx->maxbits = nullptr;
+    ctx->xs = nullptr;
+    ctx->kp.xs = nullptr;
+    ctx->kp.xs_nvec = 0;
     ctx->acc_nvec = 0;
     const size_t words = (size_t)ctx->host.n_cs * nvec * sg::acc_words(ctx->fp32);
     if ((e = cudaMalloc(&ctx->acc, words * sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMalloc(&ctx->maxbits, sizeof(long long) * nvec)) != cudaSuccess)
         return fail(ctx, SG_ENOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+#if SG_STAGE_X
+    if (ctx->kp.fast.enabled) {
+        const size_t xs_bytes = (size_t)ctx->host.n_cs * sg::xs_stride(nvec) * (ctx->fp32 ? 4 : 8);
+        if ((e = cudaMalloc(&ctx->xs, xs_bytes)) != cudaSuccess)
+            return fail(ctx, SG_ENOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+        ctx->kp.xs = ctx->xs;
+        ctx->kp.xs_nvec = nvec;
+    }
+#endif
     if ((e = cudaMemsetAsync(ctx->acc, 0, words * sizeof(unsigned long long), s)) != cudaSuccess)
         return cuda_fail(ctx, e, "workspace memset");
     ctx->acc_nvec = nvec;

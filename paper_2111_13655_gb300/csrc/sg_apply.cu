@@ -398,6 +398,49 @@ __global__ void k_maxabs(const double *__restrict__ x, int n, long long *__restr
     if ((threadIdx.x & 31) == 0 && mb) atomicMax(maxbits + v, mb);
 }
 
+// Entry-major copy of the input vectors in the contraction type (rows of
+// `stride` elements, a multiple of 4): thread r reads x_v[r] for every vector
+// (coalesced across threads per vector) and writes the first xs_stride(nvec)
+// values of its row (zero beyond nvec) as 16-byte stores.
+template <typename T>
+__device__ __forceinline__ void stage_rows(const double *__restrict__ x, long long n, int nvec, int stride,
+                                           T *__restrict__ xs, long long r0, long long rstep)
+{
+    constexpr int U = 16 / (int)sizeof(T);
+    const int w = xs_stride(nvec);
+    for (long long r = r0; r < n; r += rstep) {
+        T *row = xs + (size_t)r * stride;
+        for (int v0 = 0; v0 < w; v0 += U) {
+            T t[U];
+#pragma unroll
+            for (int e = 0; e < U; e++) t[e] = v0 + e < nvec ? (T)x[(size_t)(v0 + e) * n + r] : T(0);
+            if constexpr (U == 4)
+                *reinterpret_cast<float4 *>(row + v0) = make_float4(t[0], t[1], t[2], t[3]);
+            else
+                *reinterpret_cast<double2 *>(row + v0) = make_double2(t[0], t[1]);
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_stage_x(const double *__restrict__ x, int n, int nvec, int stride, T *__restrict__ xs)
+{
+    stage_rows<T>(x, n, nvec, stride, xs, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                  (long long)gridDim.x * blockDim.x);
+}
+
+// Many problems (blockIdx.z = problem j, its vectors from nvec * cs_prefix[j],
+// its rows from cs_prefix[j]).
+template <typename T>
+__global__ void k_stage_x_batch(const double *__restrict__ x, const long long *__restrict__ cs_prefix, int nvec,
+                                int stride, T *__restrict__ xs)
+{
+    const int j = blockIdx.z;
+    const long long c0 = cs_prefix[j], n = cs_prefix[j + 1] - c0;
+    stage_rows<T>(x + (size_t)nvec * c0, n, nvec, stride, xs + (size_t)c0 * stride,
+                  blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
 // The accumulated integer of one entry times 2^E (E from the vector's max|x|
 // bits; NaN when x held a non-finite value); clears the accumulator words.
 // FP32 contexts: one signed word; FP64: four signed 32-bit digits.
@@ -554,6 +597,32 @@ cudaError_t launch_maxabs(const KParams &kp, const double *x, int nvec, long lon
     return cudaGetLastError();
 }
 
+cudaError_t launch_stage_x(const KParams &kp, bool fp32, const double *x, int nvec, cudaStream_t stream)
+{
+    if (!kp.xs || nvec > kp.xs_nvec) return cudaErrorInvalidValue;
+    const int stride = xs_stride(kp.xs_nvec);
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((kp.n_cs + 255) / 256, 152 * 16));
+    void *xs = const_cast<void *>(kp.xs);
+    if (fp32) k_stage_x<float><<<blocks, 256, 0, stream>>>(x, kp.n_cs, nvec, stride, static_cast<float *>(xs));
+    else k_stage_x<double><<<blocks, 256, 0, stream>>>(x, kp.n_cs, nvec, stride, static_cast<double *>(xs));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage_x_batch(bool fp32, const double *x, const long long *cs_prefix, int nprob, int64_t max_ncs,
+                                 int nvec, int xs_nvec, void *xs, cudaStream_t stream)
+{
+    if (!xs || nvec > xs_nvec) return cudaErrorInvalidValue;
+    const int stride = xs_stride(xs_nvec);
+    const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (max_ncs + 255) / 256));
+    if (fp32)
+        k_stage_x_batch<float><<<dim3(bx, 1, nprob), 256, 0, stream>>>(x, cs_prefix, nvec, stride,
+                                                                       static_cast<float *>(xs));
+    else
+        k_stage_x_batch<double><<<dim3(bx, 1, nprob), 256, 0, stream>>>(x, cs_prefix, nvec, stride,
+                                                                        static_cast<double *>(xs));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const KParams &kp, bool fp32, const double *x, double *y, int nvec,
                             const long long *maxbits, cudaStream_t stream)
 {
@@ -566,7 +635,15 @@ cudaError_t launch_finalize(const KParams &kp, bool fp32, const double *x, doubl
 cudaError_t launch_apply_terms(const KParams &kp, bool fp32, const double *x, const long long *maxbits, int nvec,
                                cudaStream_t stream)
 {
-    if (kp.fast.enabled) return launch_apply_fast(kp, fp32, x, nvec, maxbits, stream);
+    if (kp.fast.enabled) {
+        if (kp.xs && nvec <= kp.xs_nvec) {
+            cudaError_t e = launch_stage_x(kp, fp32, x, nvec, stream);
+            return e == cudaSuccess ? launch_apply_fast(kp, fp32, x, nvec, maxbits, stream) : e;
+        }
+        KParams k2 = kp;  // no staged copy of this size: the term kernels read x
+        k2.xs = nullptr;
+        return launch_apply_fast(k2, fp32, x, nvec, maxbits, stream);
+    }
     if (kp.n_terms <= kp.part) return cudaSuccess;
     const size_t smem = apply_smem_bytes(kp, fp32);
     dim3 grid((unsigned)((kp.n_terms - kp.part + kp.nparts - 1) / kp.nparts));

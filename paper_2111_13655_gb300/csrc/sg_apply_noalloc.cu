@@ -103,6 +103,7 @@ extern "C" sg_status sg_apply_H_noalloc(sg_ctx *ctx, const double *x, double *y,
 
     sg::KParams kp = ctx->kp;
     kp.acc = acc;
+    kp.xs = nullptr;  // no staged input copy: the term kernels read x
     e = sg::launch_apply(kp, ctx->fp32, x, y, nvec, maxbits, nullptr, s);
     if (e != cudaSuccess) return noalloc_fail(ctx, SG_ECUDA, std::string("apply launch: ") + cudaGetErrorString(e));
     return SG_OK;

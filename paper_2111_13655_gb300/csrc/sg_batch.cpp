@@ -33,8 +33,10 @@ struct sg_batch {
     std::vector<Group> groups;
     std::vector<int> generic;          // problems outside the fast path: one launch each
     std::vector<void *> allocations;
+    std::vector<sg::KParams> h_kps;    // host copy of d_kps (the input-copy pointers change with the workspace)
     unsigned long long *acc = nullptr;
     long long *maxbits = nullptr;
+    void *xs = nullptr;                // entry-major input copies of the fast-path problems
     int acc_nvec = 0;
     // the apply's launch sequence captured as a graph, for the last (x, y, nvec, stream)
     cudaGraphExec_t graph = nullptr;
@@ -85,8 +87,10 @@ void free_all(sg_batch *b)
     b->allocations.clear();
     if (b->acc) cudaFree(b->acc);
     if (b->maxbits) cudaFree(b->maxbits);
+    if (b->xs) cudaFree(b->xs);
     b->acc = nullptr;
     b->maxbits = nullptr;
+    b->xs = nullptr;
 }
 
 }  // namespace
@@ -119,6 +123,8 @@ extern "C" sg_status sg_batch_create(sg_ctx *const *ctxs, int n, sg_batch **out)
         b->n_terms += c->host.n_terms;
         kps[j] = c->kp;
         kps[j].acc = nullptr;  // the batch kernels take the batch's accumulators explicitly
+        kps[j].xs = nullptr;   // set with the workspace (the batch's own input copies)
+        kps[j].xs_nvec = 0;
     }
 
     // every fast-path problem (of the batch's one precision) shares the launches
@@ -129,6 +135,7 @@ extern "C" sg_status sg_batch_create(sg_ctx *const *ctxs, int n, sg_batch **out)
         else b->generic.push_back(j);
     }
     sg_status st;
+    b->h_kps = kps;
     if ((st = bupload(b, kps, &b->d_kps)) != SG_OK || (st = bupload(b, b->cs_prefix, &b->d_cs_prefix)) != SG_OK) {
         free_all(b);
         delete b;
@@ -137,6 +144,7 @@ extern "C" sg_status sg_batch_create(sg_ctx *const *ctxs, int n, sg_batch **out)
     for (auto &kv : by_variant) {
         sg_batch::Group G{};
         G.kp_any = ctxs[kv.second[0]]->kp;
+        G.kp_any.xs = nullptr;
         G.g.kps = b->d_kps;
         for (int f = 0; f < 2; f++) {
             struct Item { int64_t cost; int j, p; };
@@ -183,7 +191,7 @@ extern "C" sg_status sg_batch_size(const sg_batch *b, int64_t *n_cs_total, int64
     if (n_cs_total) *n_cs_total = b->cs_prefix.back();
     if (n_terms_total) *n_terms_total = b->n_terms;
     if (launches_per_apply) {
-        int l = 2;  // max|x| and finalisation
+        int l = 2 + (SG_STAGE_X && !b->groups.empty());  // max|x|, finalisation, the input copies
         for (const auto &G : b->groups) l += (G.g.count[0] > 0) + (G.g.count[1] > 0);
         for (int j : b->generic) {
             const sg::KParams &kp = b->ctxs[j]->kp;
@@ -218,13 +226,31 @@ extern "C" sg_status sg_apply_H_batch(sg_batch *b, const double *x, double *y, i
             return bfail(b, SG_ECUDA, std::string("stream synchronize: ") + cudaGetErrorString(e));
         if (b->acc) cudaFree(b->acc);
         if (b->maxbits) cudaFree(b->maxbits);
+        if (b->xs) cudaFree(b->xs);
         b->acc = nullptr;
         b->maxbits = nullptr;
+        b->xs = nullptr;
         b->acc_nvec = 0;
         const size_t words = total * sg::acc_words(b->fp32);
         if ((e = cudaMalloc(&b->acc, words * sizeof(unsigned long long))) != cudaSuccess ||
             (e = cudaMalloc(&b->maxbits, sizeof(long long) * (size_t)nprob * nvec)) != cudaSuccess)
             return bfail(b, SG_ENOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+#if SG_STAGE_X
+        if (!b->groups.empty()) {
+            // the fast-path problems gather from entry-major copies, problem j's rows from cs_prefix[j]
+            const size_t rb = b->fp32 ? 4 : 8, stride = (size_t)sg::xs_stride(nvec);
+            if ((e = cudaMalloc(&b->xs, (size_t)b->cs_prefix.back() * stride * rb)) != cudaSuccess)
+                return bfail(b, SG_ENOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+            for (int j = 0; j < nprob; j++) {
+                if (!b->ctxs[j]->kp.fast.enabled) continue;
+                b->h_kps[j].xs = static_cast<unsigned char *>(b->xs) + (size_t)b->cs_prefix[j] * stride * rb;
+                b->h_kps[j].xs_nvec = nvec;
+            }
+            if ((e = cudaMemcpy(const_cast<sg::KParams *>(b->d_kps), b->h_kps.data(),
+                                sizeof(sg::KParams) * b->h_kps.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+                return bfail(b, SG_ECUDA, std::string("parameter upload: ") + cudaGetErrorString(e));
+        }
+#endif
         if ((e = cudaMemsetAsync(b->acc, 0, words * sizeof(unsigned long long), s)) != cudaSuccess)
             return bfail(b, SG_ECUDA, std::string("workspace memset: ") + cudaGetErrorString(e));
         b->acc_nvec = nvec;
@@ -266,6 +292,9 @@ sg_status enqueue_apply(sg_batch *b, const double *x, double *y, int nvec, cudaS
     cudaError_t e;
     if ((e = sg::launch_maxabs_batch(x, b->d_cs_prefix, nprob, b->max_ncs, nvec, b->maxbits, s)) != cudaSuccess)
         return bfail(b, SG_ECUDA, std::string("max|x| launch: ") + cudaGetErrorString(e));
+    if (b->xs && (e = sg::launch_stage_x_batch(b->fp32, x, b->d_cs_prefix, nprob, b->max_ncs, nvec, b->acc_nvec,
+                                               b->xs, s)) != cudaSuccess)
+        return bfail(b, SG_ECUDA, std::string("input copy launch: ") + cudaGetErrorString(e));
     for (const auto &G : b->groups)
         if ((e = sg::launch_fast_batch(G.kp_any, b->fp32, G.g, x, b->acc, b->maxbits, b->d_cs_prefix, nvec, s)) !=
             cudaSuccess)
@@ -274,6 +303,7 @@ sg_status enqueue_apply(sg_batch *b, const double *x, double *y, int nvec, cudaS
         sg::KParams kp = b->ctxs[j]->kp;
         const size_t off = (size_t)nvec * (size_t)b->cs_prefix[j];
         kp.acc = b->acc + off * sg::acc_words(b->fp32);
+        kp.xs = nullptr;  // the context's own input copy is not the batch's
         if ((e = sg::launch_apply_terms(kp, b->fp32, x + off, b->maxbits + (size_t)j * nvec, nvec, s)) !=
             cudaSuccess)
             return bfail(b, SG_ECUDA, std::string("term launch: ") + cudaGetErrorString(e));

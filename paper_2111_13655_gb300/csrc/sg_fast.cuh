@@ -39,6 +39,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "sg_fixed.cuh"
 #include "sg_internal.h"
@@ -122,6 +123,19 @@ static __device__ __forceinline__ void l2_prefetch_bulk(const void *p, unsigned 
 }
 // at most this much of a term's inner-block table is prefetched at entry
 constexpr int kMtPrefetchBytes = 32768;
+// Bulk prefetch of the 16-byte units inside [p0, p1) bytes of a buffer that
+// starts 16-byte aligned (the ends are rounded inwards, never outside it),
+// at most `cap` bytes.
+static __device__ __forceinline__ void l2_prefetch_span(const void *base, size_t p0, size_t p1, size_t cap)
+{
+    const size_t b0 = (p0 + 15) & ~(size_t)15, b1 = p1 & ~(size_t)15;
+    if (b1 <= b0) return;
+    const size_t n = b1 - b0 < cap ? b1 - b0 : cap;
+    l2_prefetch_bulk(reinterpret_cast<const unsigned char *>(base) + b0, (unsigned)n);
+}
+#ifndef SG_LOOKAHEAD
+#define SG_LOOKAHEAD 1
+#endif
 
 template <typename T> struct FTab;
 template <> struct FTab<double> {
@@ -444,9 +458,12 @@ __host__ __device__ inline size_t part_bytes(const KParams &P, size_t rb, int wo
 }
 
 // Gather of one chunk: X[o][v][i] = x_v[rank(o, i)] (M^B holds the ranks in
-// the order [outer site][inner index]).
-template <typename T, int NBI, int GS>
-__device__ __forceinline__ void gather_t(const FHdr &H, const KParams &P, const double *__restrict__ x,
+// the order [outer site][inner index]).  The source is either the
+// entry-major copy xs (ST: element (r, v) at r * stride + v, in T; the
+// threads of consecutive vectors read consecutive words) or x itself (vector
+// v at v * n_cs, FP64).
+template <typename T, int NBI, int GS, bool ST>
+__device__ __forceinline__ void gather_t(const FHdr &H, const void *__restrict__ src, size_t stride,
                                          const int *__restrict__ rk, T *X, int vb, int tid)
 {
     constexpr int ZW = (NBI * (int)sizeof(T)) % 16 == 0 ? vunit<T>() : NBI == 2 && sizeof(T) == 4 ? 2 : 1;
@@ -455,10 +472,16 @@ __device__ __forceinline__ void gather_t(const FHdr &H, const KParams &P, const 
     for (int w = tid; w < total; w += GS) {
         const int o = fdiv(w, vb, vmag), v = w - o * vb;
         const int *rp = rk + (size_t)o * NBI;
-        const double *xv = x + (size_t)v * P.n_cs;
         T val[NBI];
+        if constexpr (ST) {
+            const T *xv = static_cast<const T *>(src) + v;
 #pragma unroll
-        for (int i = 0; i < NBI; i++) val[i] = (T)__ldg(xv + rp[i]);
+            for (int i = 0; i < NBI; i++) val[i] = __ldg(xv + (size_t)rp[i] * stride);
+        } else {
+            const double *xv = static_cast<const double *>(src) + (size_t)v * stride;
+#pragma unroll
+            for (int i = 0; i < NBI; i++) val[i] = (T)__ldg(xv + rp[i]);
+        }
         T *dst = X + (size_t)w * NBI;
 #pragma unroll
         for (int i = 0; i < NBI; i += ZW) {
@@ -470,29 +493,44 @@ __device__ __forceinline__ void gather_t(const FHdr &H, const KParams &P, const 
     }
 }
 
-template <typename T, int GS>
-__device__ void gather_rt(const FHdr &H, const KParams &P, const double *__restrict__ x,
-                          const int *__restrict__ rk, T *X, int vb, int tid)
+template <typename T, int GS, bool ST>
+__device__ void gather_rt(const FHdr &H, const void *__restrict__ src, size_t stride, const int *__restrict__ rk,
+                          T *X, int vb, int tid)
 {
     const int NBI = H.NBI, total = H.NBo * vb;
     const unsigned vmag = rmag((unsigned)vb);
     for (int w = tid; w < total; w += GS) {
         const int o = fdiv(w, vb, vmag), v = w - o * vb;
-        for (int i = 0; i < NBI; i++)
-            X[(size_t)w * NBI + i] = (T)__ldg(x + (size_t)v * P.n_cs + rk[(size_t)o * NBI + i]);
+        for (int i = 0; i < NBI; i++) {
+            const size_t r = (size_t)rk[(size_t)o * NBI + i];
+            X[(size_t)w * NBI + i] = ST ? __ldg(static_cast<const T *>(src) + r * stride + v)
+                                        : (T)__ldg(static_cast<const double *>(src) + (size_t)v * stride + r);
+        }
     }
 }
 
-template <typename T, int GS>
-__device__ void gather(const FHdr &H, const KParams &P, const double *x, const int *rk, T *X, int vb, int tid)
+template <typename T, int GS, bool ST>
+__device__ void gather_s(const FHdr &H, const void *src, size_t stride, const int *rk, T *X, int vb, int tid)
 {
     switch (H.NBI) {
-        case 1: gather_t<T, 1, GS>(H, P, x, rk, X, vb, tid); return;
-        case 2: gather_t<T, 2, GS>(H, P, x, rk, X, vb, tid); return;
-        case 4: gather_t<T, 4, GS>(H, P, x, rk, X, vb, tid); return;
-        case 8: gather_t<T, 8, GS>(H, P, x, rk, X, vb, tid); return;
-        default: gather_rt<T, GS>(H, P, x, rk, X, vb, tid); return;
+        case 1: gather_t<T, 1, GS, ST>(H, src, stride, rk, X, vb, tid); return;
+        case 2: gather_t<T, 2, GS, ST>(H, src, stride, rk, X, vb, tid); return;
+        case 4: gather_t<T, 4, GS, ST>(H, src, stride, rk, X, vb, tid); return;
+        case 8: gather_t<T, 8, GS, ST>(H, src, stride, rk, X, vb, tid); return;
+        default: gather_rt<T, GS, ST>(H, src, stride, rk, X, vb, tid); return;
     }
+}
+
+// The chunk's vectors v0 .. v0 + vb - 1: from the problem's entry-major copy
+// when it has one, else from x.
+template <typename T, int GS>
+__device__ void gather(const FHdr &H, const KParams &P, const double *x, int nvec, int v0, const int *rk, T *X,
+                       int vb, int tid)
+{
+    if (P.xs)
+        gather_s<T, GS, true>(H, static_cast<const T *>(P.xs) + v0, (size_t)xs_stride(P.xs_nvec), rk, X, vb, tid);
+    else
+        gather_s<T, GS, false>(H, x + (size_t)v0 * P.n_cs, (size_t)P.n_cs, rk, X, vb, tid);
 }
 
 // Final step of a chunk, fused: y = F + (c0 X when the term has no grid) +
@@ -548,7 +586,21 @@ __device__ void combine_add(const FHdr &H, const KParams &P, const int *__restri
     }
     gsync<GS>();
     const int n = H.NB * vb;
-    const unsigned vmag = rmag((unsigned)vb), nbimag = rmag((unsigned)NBI);
+    const unsigned nbimag = rmag((unsigned)NBI);
+    if (GS % vb == 0) {
+        // each thread keeps one vector (and its accumulator unit) for the whole pass
+        const int v = tid % vb, step = GS / vb;
+        const int E = fx::Acc<T>::unit(maxbits[v0 + v]);
+        unsigned long long *av = acc + (size_t)(v0 + v) * fx::Acc<T>::words;
+        const T *dv = dst + (size_t)v * NBI;
+        for (int oi = tid / vb; oi < H.NB; oi += step) {  // oi = o * NBI + i
+            const int o = fdiv(oi, NBI, nbimag), i = oi - o * NBI;
+            fx::Acc<T>::add_unit(av + (size_t)rk[oi] * nvec * fx::Acc<T>::words, dv[(size_t)o * Pl + i], H.coef, E,
+                                 P.err);
+        }
+        return;
+    }
+    const unsigned vmag = rmag((unsigned)vb);
     for (int w = tid; w < n; w += GS) {
         const int oi = fdiv(w, vb, vmag), v = w - oi * vb;  // oi = o * NBI + i
         const int o = fdiv(oi, NBI, nbimag), i = oi - o * NBI;
@@ -568,7 +620,7 @@ template <typename T, int GS>
 __device__ __forceinline__ void fast_term(const KParams &P, const double *__restrict__ x,
                                           unsigned long long *accp, const long long *__restrict__ maxbits,
                                           int nvec, int p, int work_cap, unsigned char *base, FHdr &H,
-                                          const int tid)
+                                          const int tid, const KParams &PA, int pa)
 {
     constexpr int U = vunit<T>();
     const size_t rb = sizeof(T);
@@ -589,10 +641,26 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
             l2_prefetch_bulk(reinterpret_cast<const unsigned char *>(FTab<T>::mt(P)) + b0, (unsigned)(b1 - b0));
         }
     }
+    // Look-ahead: the group that will take processing position pa (of problem
+    // *PA) about one residency later gets that term's record, image, compact
+    // indices and the start of its inner-block table fetched into L2 now; its
+    // offsets are read here and the prefetches issued after the prologue.
+    // One thread: the first of warp 1 in the block form, lane 0 in the warp form.
+    const bool la = SG_LOOKAHEAD && pa >= 0 && tid == (GS == 32 ? 0 : 32);
+    unsigned la_d0 = 0, la_d1 = 0;
+    long long la_i0 = 0, la_i1 = 0, la_r0 = 0, la_r1 = 0, la_m0 = 0, la_m1 = 0;
+    if (la) {
+        la_d0 = PA.fast.desc_off[pa]; la_d1 = PA.fast.desc_off[pa + 1];
+        la_i0 = PA.fast.img_off[pa]; la_i1 = PA.fast.img_off[pa + 1];
+        la_r0 = PA.fast.rank_start[pa]; la_r1 = PA.fast.rank_start[pa + 1];
+        la_m0 = PA.fast.mt_off[pa]; la_m1 = PA.fast.mt_off[pa + 1];
+    }
     // the term's image (B, B^T W, H1 per position, then its G tables) and its
     // compact indices (M^B) are copied as they lie while warp 0 decodes the
     // record (into a scratch at the end of the work area)
     int *rks = reinterpret_cast<int *>(work);
+    const int64_t rec_off = record_scratch_offset((int64_t)work_cap * rb, P.fast.desccap);
+    bool rfit;
     {
         const long long i0 = P.fast.img_off[p];
         const int isz = (int)(P.fast.img_off[p + 1] - i0);
@@ -601,19 +669,25 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
             for (int e = tid; e < isz; e += GS) mats[e] = img[e];
         const long long r0 = P.fast.rank_start[p];
         const int nr = (int)(P.fast.rank_start[p + 1] - r0);
-        if (ranks_elems(nr, U) <= work_cap)
+        // the indices must stay clear of the record scratch (the planner keeps
+        // them apart; a term that breaks this is refused below)
+        rfit = 4 * (int64_t)nr <= rec_off;
+        if (rfit)
             for (int e = tid; e < nr; e += GS) rks[e] = __ldg(P.fast.ranks + r0 + e);
     }
     if (tid < 32) {
-        load_record(P, p,
-                    reinterpret_cast<int4 *>(reinterpret_cast<unsigned char *>(work) +
-                                             record_scratch_offset((int64_t)work_cap * rb, P.fast.desccap)),
-                    H);
+        load_record(P, p, reinterpret_cast<int4 *>(reinterpret_cast<unsigned char *>(work) + rec_off), H);
         derive_layout<T>(P, nvec, work_cap, H);
     }
     gsync<GS>();
-    if (H.bad) {
-        if (tid == 0 && P.err) atomicCAS(P.err, 0, 110 + H.bad);
+    if (la) {
+        l2_prefetch_span(PA.fast.desc, 16 * (size_t)la_d0, 16 * (size_t)la_d1, ~(size_t)0);
+        l2_prefetch_span(FTab<T>::img(PA), (size_t)la_i0 * rb, (size_t)la_i1 * rb, ~(size_t)0);
+        l2_prefetch_span(PA.fast.ranks, 4 * (size_t)la_r0, 4 * (size_t)la_r1, ~(size_t)0);
+        l2_prefetch_span(FTab<T>::mt(PA), (size_t)la_m0 * rb, (size_t)la_m1 * rb, (size_t)kMtPrefetchBytes);
+    }
+    if (H.bad || !rfit) {
+        if (tid == 0 && P.err) atomicCAS(P.err, 0, 110 + (rfit ? H.bad : 3));
         return;
     }
     const int m = H.m, R = H.R, NB = H.NB, NBI = H.NBI;
@@ -630,7 +704,7 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
         T *Y = X + pad_elems((int64_t)NB * vb, U);
         T *A = sliced ? Y + pad_elems((int64_t)NB * vb, U) : Y;
         T *Bf = A + pad_elems((int64_t)NBI * H.NGs * vb, U);
-        gather<T, GS>(H, P, x + (size_t)v0 * P.n_cs, rk, X, vb, tid);
+        gather<T, GS>(H, P, x, nvec, v0, rk, X, vb, tid);
         gsync<GS>();
         const T *F = nullptr;
         if (H.grid) {
@@ -735,7 +809,7 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
 template <typename T, int GS>
 __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? SG_F32_MINBLOCKS : SG_F64_MINBLOCKS)
     k_apply_fast(const KParams P, const double *__restrict__ x, const long long *__restrict__ maxbits, int nvec,
-                 int p0, int pcount, int pstride, int work_cap)
+                 int p0, int pcount, int pstride, int work_cap, int ahead)
 {
     constexpr int NG = kFT / GS;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -743,8 +817,9 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? SG_F32_MINBLOCKS : SG_F6
     const int grp = threadIdx.x / GS, tid = threadIdx.x % GS;
     const int pidx = blockIdx.x * NG + grp;
     if (pidx >= pcount) return;
+    const int qa = ahead > 0 && pidx + ahead < pcount ? p0 + (pidx + ahead) * pstride : -1;
     fast_term<T, GS>(P, x, P.acc, maxbits, nvec, p0 + pidx * pstride, work_cap,
-                     smraw + (size_t)grp * part_bytes(P, sizeof(T), work_cap), Hs[grp], tid);
+                     smraw + (size_t)grp * part_bytes(P, sizeof(T), work_cap), Hs[grp], tid, P, qa);
 }
 
 // Many problems in one launch: work item i = (problem, processing position);
@@ -757,7 +832,7 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? SG_F32_MINBLOCKS : SG_F6
     k_apply_fast_batch(const KParams *__restrict__ kps, const int2 *__restrict__ items, int count,
                        const double *__restrict__ x, unsigned long long *acc,
                        const long long *__restrict__ maxbits, const long long *__restrict__ cs_prefix, int nvec,
-                       int part)
+                       int part, int ahead)
 {
     constexpr int NG = kFT / GS;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -768,8 +843,10 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? SG_F32_MINBLOCKS : SG_F6
     const int2 it = items[pidx];
     const KParams &P = kps[it.x];
     const size_t off = (size_t)nvec * (size_t)cs_prefix[it.x];
+    const int2 ia = ahead > 0 && pidx + ahead < count ? items[pidx + ahead] : make_int2(it.x, -1);
     fast_term<T, GS>(P, x + off, acc + off * fx::Acc<T>::words, maxbits + (size_t)it.x * nvec, nvec, it.y,
-                     GS == kFT ? P.fast.work_cta : P.fast.work_warp, smraw + (size_t)grp * part, Hs[grp], tid);
+                     GS == kFT ? P.fast.work_cta : P.fast.work_warp, smraw + (size_t)grp * part, Hs[grp], tid,
+                     kps[ia.x], ia.y);
 }
 
 // Sets a kernel's dynamic shared-memory limit to the most the device allows
@@ -789,6 +866,41 @@ cudaError_t set_smem_limit(K kernel, size_t need)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
 }
 
+// Term groups of kernel `kernel` resident on the whole device at `smem` bytes
+// of dynamic shared memory per block: the look-ahead distance of its
+// prefetches.  Answers are kept (a small table shared by all host threads)
+// and first asked when the kernels are configured, so that a launch inside a
+// stream capture normally finds its answer there.
+struct ResidentEntry {
+    const void *k;
+    size_t smem;
+    int dev, groups;
+};
+inline std::mutex g_resident_mu;
+inline ResidentEntry g_resident[16];
+inline int g_resident_next = 0;
+
+template <typename K>
+int resident_groups(K kernel, size_t smem, int groups_per_block)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    const void *kp = reinterpret_cast<const void *>(kernel);
+    {
+        std::lock_guard<std::mutex> lk(g_resident_mu);
+        for (const ResidentEntry &c : g_resident)
+            if (c.k == kp && c.smem == smem && c.dev == dev) return c.groups;
+    }
+    int nb = 0, nsm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kFT, smem) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    std::lock_guard<std::mutex> lk(g_resident_mu);
+    g_resident[g_resident_next] = ResidentEntry{kp, smem, dev, nb * nsm * groups_per_block};
+    g_resident_next = (g_resident_next + 1) % 16;
+    return nb * nsm * groups_per_block;
+}
+
 template <typename T>
 cudaError_t launch_t(const KParams &kp, const FastLaunch &a)
 {
@@ -798,9 +910,15 @@ cudaError_t launch_t(const KParams &kp, const FastLaunch &a)
     if (a.configure) {
         cudaError_t e = set_smem_limit(k_apply_fast<T, kFT>, smem_cta);
         if (e == cudaSuccess) e = set_smem_limit(k_apply_fast<T, 32>, smem_warp);
+        if (e == cudaSuccess) {
+            resident_groups(k_apply_fast<T, kFT>, smem_cta, 1);
+            resident_groups(k_apply_fast<T, 32>, smem_warp, kFT / 32);
+        }
         return e;
     }
     const int nbig = kp.fast.n_big, nrest = (int)kp.n_terms - nbig;
+    const int ahead_cta = nbig > 0 ? resident_groups(k_apply_fast<T, kFT>, smem_cta, 1) : 0;
+    const int ahead_warp = nrest > 0 ? resident_groups(k_apply_fast<T, 32>, smem_warp, kFT / 32) : 0;
     if (kp.nparts > 1) {
         // one part of a term-sharded apply: positions p = part (mod nparts) of each form
         const int G = kp.nparts, r = kp.part;
@@ -809,19 +927,19 @@ cudaError_t launch_t(const KParams &kp, const FastLaunch &a)
         const int cw = (int)kp.n_terms > p1 ? ((int)kp.n_terms - p1 + G - 1) / G : 0;
         if (cb > 0)
             k_apply_fast<T, kFT><<<(unsigned)cb, kFT, smem_cta, a.stream>>>(kp, a.x, a.maxbits, a.nvec, r, cb, G,
-                                                                          kp.fast.work_cta);
+                                                                          kp.fast.work_cta, ahead_cta);
         if (cw > 0)
             k_apply_fast<T, 32><<<(unsigned)((cw + kFT / 32 - 1) / (kFT / 32)), kFT, smem_warp, a.stream>>>(
-                kp, a.x, a.maxbits, a.nvec, p1, cw, G, kp.fast.work_warp);
+                kp, a.x, a.maxbits, a.nvec, p1, cw, G, kp.fast.work_warp, ahead_warp);
         return cudaGetLastError();
     }
     if (nbig > 0)
         k_apply_fast<T, kFT><<<(unsigned)nbig, kFT, smem_cta, a.stream>>>(kp, a.x, a.maxbits, a.nvec, 0, nbig, 1,
-                                                                        kp.fast.work_cta);
+                                                                        kp.fast.work_cta, ahead_cta);
     if (nrest > 0) {
         const unsigned blocks = (unsigned)((nrest + kFT / 32 - 1) / (kFT / 32));
         k_apply_fast<T, 32><<<blocks, kFT, smem_warp, a.stream>>>(kp, a.x, a.maxbits, a.nvec, nbig, nrest, 1,
-                                                                kp.fast.work_warp);
+                                                                kp.fast.work_warp, ahead_warp);
     }
     return cudaGetLastError();
 }
@@ -832,15 +950,21 @@ cudaError_t batch_t(const FastBatchLaunch &a)
     constexpr int NG = kFT / 32;
     if (a.configure) {
         cudaError_t e = set_smem_limit(k_apply_fast_batch<T, kFT>, (size_t)a.part[0]);
-        if (e != cudaSuccess) return e;
-        return set_smem_limit(k_apply_fast_batch<T, 32>, (size_t)NG * a.part[1]);
+        if (e == cudaSuccess) e = set_smem_limit(k_apply_fast_batch<T, 32>, (size_t)NG * a.part[1]);
+        if (e == cudaSuccess) {
+            resident_groups(k_apply_fast_batch<T, kFT>, (size_t)a.part[0], 1);
+            resident_groups(k_apply_fast_batch<T, 32>, (size_t)NG * a.part[1], NG);
+        }
+        return e;
     }
     if (a.count[0] > 0)
         k_apply_fast_batch<T, kFT><<<(unsigned)a.count[0], kFT, (size_t)a.part[0], a.stream>>>(
-            a.kps, a.items[0], a.count[0], a.x, a.acc, a.maxbits, a.cs_prefix, a.nvec, a.part[0]);
+            a.kps, a.items[0], a.count[0], a.x, a.acc, a.maxbits, a.cs_prefix, a.nvec, a.part[0],
+            resident_groups(k_apply_fast_batch<T, kFT>, (size_t)a.part[0], 1));
     if (a.count[1] > 0)
         k_apply_fast_batch<T, 32><<<(unsigned)((a.count[1] + NG - 1) / NG), kFT, (size_t)NG * a.part[1], a.stream>>>(
-            a.kps, a.items[1], a.count[1], a.x, a.acc, a.maxbits, a.cs_prefix, a.nvec, a.part[1]);
+            a.kps, a.items[1], a.count[1], a.x, a.acc, a.maxbits, a.cs_prefix, a.nvec, a.part[1],
+            resident_groups(k_apply_fast_batch<T, 32>, (size_t)NG * a.part[1], NG));
     return cudaGetLastError();
 }
 

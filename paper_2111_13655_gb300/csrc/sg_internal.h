@@ -88,6 +88,11 @@ inline int fast_rmax(int nb1) { return nb1 == 2 ? 3 : nb1 == 3 ? 2 : 0; }
 // Sizes shared by the host planner and the fast kernels.
 // Padding of a buffer of n elements to a multiple of u elements (16 bytes).
 __host__ __device__ inline int64_t pad_elems(int64_t n, int u) { return (n + u - 1) / u * u; }
+#ifndef SG_STAGE_X
+#define SG_STAGE_X 1  // the fast path gathers from an entry-major copy of x
+#endif
+// Row length (elements) of the entry-major input copy for nvec vectors.
+__host__ __device__ inline int xs_stride(int nvec) { return (nvec + 3) & ~3; }
 // Elements (of a type with u per 16 bytes) that hold a term's NB int32
 // compact indices, padded to 16 bytes.
 __host__ __device__ inline int64_t ranks_elems(int64_t NB, int u) { return pad_elems((NB * u + 3) / 4, u); }
@@ -201,6 +206,12 @@ struct KParams {
     const int *harm_mono;    // [D] monomial holding the harmonic part of mode i (-1: not split)
     const double *esplit;    // [n_cs] sum over split modes of omega_i s_i^2 (k_i + 1/2)
     unsigned long long *acc; // [n_cs][nvec][acc_words] fixed-point accumulators (entry-major)
+    // Entry-major copy of the input vectors in the contraction type, made at
+    // the start of each apply: xs[r * xs_stride(xs_nvec) + v] = x_v[r] (the
+    // vectors of one compact entry adjacent).  Holds up to xs_nvec vectors;
+    // nullptr: the term kernels read x itself.
+    const void *xs;
+    int xs_nvec;
     FastParams fast;
     // capacities of the per-CTA shared-memory areas (elements)
     int cap;       // each of the two grid ping-pong buffers
@@ -292,6 +303,11 @@ cudaError_t launch_apply_terms(const KParams &kp, bool fp32, const double *x, co
 // (zeroed first), and y = (accumulated integer) * 2^E + esplit * x, which also
 // clears kp.acc.
 cudaError_t launch_maxabs(const KParams &kp, const double *x, int nvec, long long *maxbits, cudaStream_t stream);
+// kp.xs = the input vectors entry-major in the contraction type (kp.xs set, nvec <= kp.xs_nvec; rows of
+// xs_stride(kp.xs_nvec) elements); for a batch, every problem's rows from cs_prefix[j].
+cudaError_t launch_stage_x(const KParams &kp, bool fp32, const double *x, int nvec, cudaStream_t stream);
+cudaError_t launch_stage_x_batch(bool fp32, const double *x, const long long *cs_prefix, int nprob, int64_t max_ncs,
+                                 int nvec, int xs_nvec, void *xs, cudaStream_t stream);
 cudaError_t launch_finalize(const KParams &kp, bool fp32, const double *x, double *y, int nvec,
                             const long long *maxbits, cudaStream_t stream);
 cudaError_t launch_maxabs_batch(const double *x, const long long *cs_prefix, int nprob, int64_t max_ncs, int nvec,
@@ -359,6 +375,7 @@ struct sg_ctx {
     // apply workspace: fixed-point accumulators and per-vector scale exponents
     unsigned long long *acc = nullptr;
     long long *maxbits = nullptr;
+    void *xs = nullptr;       // entry-major input copy (fast path), acc_nvec vectors
     int acc_nvec = 0;
     int plan_version = 0;     // incremented whenever sg_tune installs a plan
     std::string last_error;
