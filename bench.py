@@ -37,10 +37,11 @@ sys.path.insert(0, ROOT)
 METRIC = "Smolyak H|psi> applications/s and % roofline at D=12 L=10; mixed vs FP64; p50/p99"
 UNIT = "applications/s"
 WORKLOAD = "chained Henon-Heiles D=12 L=10 nb=l+1 nq=l+2 (N_cs=646646, 646646 terms)"
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# dominant term kernel at the benchmark workload, per precision, from the ncu
-# captures summarised in profiles/; None until the current kernel is captured.
-TRAFFIC_BYTES = {"mixed": None, "fp64": None}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the term kernel
+# k_apply_fast per apply (its block-form and warp-form launches) at the
+# benchmark workload, per precision, from the one-pass ncu capture of the full
+# workload summarised in profiles/; None when the kernel has changed since.
+TRAFFIC_BYTES = {"mixed": 9_009_755_648, "fp64": 23_425_165_568}
 # FP32 lanes per SM (the unit count of the derived FP32 peak)
 FP32_LANES_PER_SM = 128
 # kernels of one sg_apply_H at this workload: k_maxabs, k_stage_x (entry-major
