@@ -41,7 +41,11 @@ WORKLOAD = "chained Henon-Heiles D=12 L=10 nb=l+1 nq=l+2 (N_cs=646646, 646646 te
 # k_apply_fast per apply (its block-form and warp-form launches) at the
 # benchmark workload, per precision, from the one-pass ncu capture of the full
 # workload summarised in profiles/; None when the kernel has changed since.
-TRAFFIC_BYTES = {"mixed": 9_009_755_648, "fp64": 23_425_165_568}
+TRAFFIC_BYTES = {"mixed": 9_009_755_648, "fp64": 23_425_165_568, "df64": None}
+# FP32 instructions of one double-float multiply-add (csrc/sg_df.cuh df_fma:
+# one multiply, three FMAs, two_sum 6, two additions, fast_two_sum 3): the
+# double-float arm's roofline counts these against the FP32 issue rate
+DF_INSTR_PER_FMA = 15
 # FP32 lanes per SM (the unit count of the derived FP32 peak)
 FP32_LANES_PER_SM = 128
 # kernels of one sg_apply_H at this workload: k_maxabs, k_stage_x (entry-major
@@ -519,7 +523,7 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--L", type=int, default=10, help="Smolyak level of the D=12 workload (10: the benchmark)")
-    ap.add_argument("--precisions", default="mixed,fp64")
+    ap.add_argument("--precisions", default="mixed,fp64,df64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--peak-seconds", type=float, default=1.0, help="0: skip the peak measurement")
     ap.add_argument("--sharding", default="replicas", choices=["replicas", "terms"],
@@ -588,21 +592,34 @@ def main():
         lv, _ = sg.sg_term_levels(ctx)
         f_alg = algorithmic_flops_per_vector(lv) * nvec
         ms = total_ms / steps
-        peak = peaks["fp32"] if prec == "mixed" else peaks["fp64"]
-        achieved = f_alg / (statistics.mean(times) * 1e-3) / 1e12
-        frac = achieved / peak if peak else None
         units = nvec * steps if args.sharding == "terms" and world > 1 else None
+        if prec == "df64":
+            # double-float: F_alg / 2 multiply-adds of DF_INSTR_PER_FMA FP32
+            # instructions each, against the FP32 issue rate (fma rate / 2)
+            instr = f_alg / 2 * DF_INSTR_PER_FMA
+            peak = peaks["fp32"] / 2 if peaks["fp32"] else None
+            achieved = instr / (statistics.mean(times) * 1e-3) / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32-instructions/s",
+                    "frac": achieved / peak if peak else None, "traffic": TRAFFIC_BYTES[prec],
+                    "flops_per_launch": f_alg, "fp32_instructions_per_launch": instr,
+                    "peak_source": "measured",
+                    "peak_note": "half the measured FP32 fma rate (one instruction per lane per cycle); "
+                                 + str(peaks["note_fp32"])}
+        else:
+            peak = peaks["fp32"] if prec == "mixed" else peaks["fp64"]
+            achieved = f_alg / (statistics.mean(times) * 1e-3) / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak if peak else None,
+                    "traffic": TRAFFIC_BYTES[prec],
+                    "flops_per_launch": f_alg,
+                    "peak_source": "measured",
+                    "peak_note": peaks["note_fp32" if prec == "mixed" else "note_fp64"],
+                    "peak_derived": peaks["derived_fp32"] if prec == "mixed" else None}
         results[prec] = {
             "value": (units / (total_ms * 1e-3) if units else replica_throughput(world, nvec * steps, total_ms * 1e-3)),
             "ms_per_step": ms, "steps": steps,
             "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": frac,
-                         "traffic": TRAFFIC_BYTES[prec],
-                         "flops_per_launch": f_alg,
-                         "peak_source": "measured",
-                         "peak_note": peaks["note_fp32" if prec == "mixed" else "note_fp64"],
-                         "peak_derived": peaks["derived_fp32"] if prec == "mixed" else None},
+            "roofline": roof,
             "clocks": clk.summary(),
         }
         if prec == "mixed" and not args.no_e2e:
@@ -633,6 +650,7 @@ def main():
     if rank == 0:
         m = results.get("mixed") or next(iter(results.values()))
         f = results.get("fp64")
+        d = results.get("df64")
         line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": m["steps"],
                 "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
                 "scaling": "strong" if args.sharding == "terms" and world > 1 else "weak", "vs_baseline": None,
@@ -643,6 +661,10 @@ def main():
                 "fp64": ({"value": f["value"], "unit": UNIT, "ms_per_step": f["ms_per_step"], "steps": f["steps"],
                           "latency_ms": f["latency_ms"], "roofline": f["roofline"], "clocks": f["clocks"]}
                          if f else None),
+                "df64": ({"value": d["value"], "unit": UNIT, "ms_per_step": d["ms_per_step"], "steps": d["steps"],
+                          "precision": "double-float contractions (pairs of FP32, ~48 bits), FP64 accumulation",
+                          "latency_ms": d["latency_ms"], "roofline": d["roofline"], "clocks": d["clocks"]}
+                         if d else None),
                 "peaks": {k: v for k, v in peaks.items() if k != "clocks"} if peaks else None,
                 "cpu_baseline": cpu, "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)

@@ -57,7 +57,7 @@ typedef enum {
     SG_EUNSUPPORTED = 7  /* valid request outside this build's limits (see below)     */
 } sg_status;
 
-typedef enum { SG_FP64 = 0, SG_MIXED = 1 } sg_precision;
+typedef enum { SG_FP64 = 0, SG_MIXED = 1, SG_DF64 = 2 } sg_precision;
 
 typedef enum { SG_LANCZOS = 0, SG_DAVIDSON = 1 } sg_eig_method;
 
@@ -96,13 +96,20 @@ typedef struct {
  *   basis  D host structs; grids: D host structs.
  *   H      Hamiltonian; all arrays are host memory, copied (caller keeps ownership).
  *   prec   SG_FP64: every step in FP64.  SG_MIXED: per-term contractions and
- *          the grid multiply in FP32, accumulation of the compact result in FP64.
+ *          the grid multiply in FP32, accumulation of the compact result in
+ *          FP64 (exact fixed point).  SG_DF64: the contractions in double-float
+ *          arithmetic (each value an unevaluated sum of two FP32 numbers,
+ *          about 48 significant bits, on the FP32 pipes), accumulation as for
+ *          SG_FP64; FP64-class results (relative error about 1e-14 against
+ *          1e-16), for problems on the fast path only (V with monomials of one
+ *          mode or of two neighbouring modes of a chain; else
+ *          SG_EUNSUPPORTED); not accepted by sg_batch_create or the server.
  *   out    receives the context (owned by the caller, release with sg_destroy).
  * Setup runs on the host plus synchronous uploads on the current device.
  * The context keeps on the device M^B (4 bytes per term basis function), the
- * per-term records and 1D tables, and, when every monomial of V touches at most
- * two modes, the coupling potential at every grid point of every term (4 bytes
- * per point for SG_MIXED, 8 for SG_FP64; about 5.1 / 10.2 GB at D=12 L=10,
+ * per-term records, images and 1D tables, and, on the fast path, the
+ * inner-block tables of every term with a grid (4 bytes per value for
+ * SG_MIXED, 8 for SG_FP64 and SG_DF64; 6.65 / 13.1 GB at D=12 L=10,
  * nq = l+2).  sg_size reports the total.
  * Limits of this build (SG_EUNSUPPORTED): nb(L), nq(L) <= 32, N_cs < 2^31,
  * at most 256 monomials with at most 8 factors each, powers <= 16.
@@ -213,7 +220,8 @@ sg_status sg_apply_H_noalloc(sg_ctx *ctx, const double *x, double *y, int nvec, 
  * monomials over three or more modes) get one launch each.
  *
  * sg_batch_create -- n (1..65535) contexts made by sg_create on the current
- *   device, all of one precision (else SG_EINVAL).  The batch borrows their
+ *   device, all of one precision (else SG_EINVAL; SG_DF64 contexts:
+ *   SG_EUNSUPPORTED).  The batch borrows their
  *   device tables: destroy it before any of them.  The contexts' own
  *   workspaces are not used, so sg_apply_H on a member stays valid.
  * sg_batch_size -- total N_cs and terms over the problems; kernel launches

@@ -38,7 +38,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libsmolyak.so")
 
 SG_OK, SG_EINVAL, SG_ENOMEM, SG_ECUDA, SG_ENOCONV, SG_ETIMEOUT, SG_EBUDGET, SG_EUNSUPPORTED = range(8)
-SG_FP64, SG_MIXED = 0, 1
+SG_FP64, SG_MIXED, SG_DF64 = 0, 1, 2
 SG_LANCZOS, SG_DAVIDSON = 0, 1
 _STATUS = {0: "SG_OK", 1: "SG_EINVAL", 2: "SG_ENOMEM", 3: "SG_ECUDA", 4: "SG_ENOCONV",
            5: "SG_ETIMEOUT", 6: "SG_EBUDGET", 7: "SG_EUNSUPPORTED"}
@@ -205,6 +205,8 @@ def _precision(precision) -> int:
         return SG_FP64
     if precision in (SG_MIXED, "mixed", "MIXED", "fp32"):
         return SG_MIXED
+    if precision in (SG_DF64, "df64", "DF64"):
+        return SG_DF64
     raise ValueError(f"unknown precision {precision!r}")
 
 

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsmolyak.so")
 # the four fast-path instantiation units take the longest and go first
-SOURCES = ["sg_fast_f32.cu", "sg_fast_f64.cu", "sg_fast_batch_f32.cu", "sg_fast_batch_f64.cu",
+SOURCES = ["sg_fast_f32.cu", "sg_fast_f64.cu", "sg_fast_df.cu", "sg_fast_batch_f32.cu", "sg_fast_batch_f64.cu",
            "sg_setup.cpp", "sg_api.cpp", "sg_apply.cu", "sg_apply_fast.cu", "sg_solvers.cu", "sg_solvers_api.cpp",
            "sg_apply_noalloc.cu", "sg_batch.cpp", "sg_server.cu", "sg_server_api.cpp",
            "sg_tune.cpp", "sg_peak.cu"]

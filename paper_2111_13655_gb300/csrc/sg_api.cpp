@@ -6,6 +6,7 @@
 #include <new>
 #include <string>
 
+#include "sg_df.cuh"
 #include "sg_internal.h"
 
 namespace {
@@ -21,6 +22,17 @@ sg_status fail(sg_ctx *ctx, sg_status st, const std::string &msg)
 sg_status cuda_fail(sg_ctx *ctx, cudaError_t e, const char *where)
 {
     return fail(ctx, SG_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// FP64 values as double-float pairs (hi = fl32(d), lo = fl32(d - hi))
+std::vector<float2> df_pairs(const std::vector<double> &v)
+{
+    std::vector<float2> out(v.size());
+    for (size_t i = 0; i < v.size(); i++) {
+        const sg::df2 d(v[i]);
+        out[i] = make_float2(d.hi, d.lo);
+    }
+    return out;
 }
 
 template <typename T>
@@ -107,7 +119,7 @@ sg_status plan(int D, int L, const sg_basis *basis, const sg_grid *grids,
     if (D > kMaxD) return fail(nullptr, SG_EUNSUPPORTED, "D > 32");
     if (L < 0) return fail(nullptr, SG_EINVAL, "L must be >= 0");
     if (!basis || !grids || !H || !H->omega) return fail(nullptr, SG_EINVAL, "NULL basis/grids/H/omega");
-    if (prec != SG_FP64 && prec != SG_MIXED) return fail(nullptr, SG_EINVAL, "unknown precision");
+    if (prec != SG_FP64 && prec != SG_MIXED && prec != SG_DF64) return fail(nullptr, SG_EINVAL, "unknown precision");
     for (int i = 0; i < D; i++) {
         const sg_basis &b = basis[i];
         const sg_grid &g = grids[i];
@@ -249,7 +261,8 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
                     (st = upload(ctx, T.frank_start, &kp.fast.rank_start)) != SG_OK ||
                     (ctx->fp32 ? (st = upload(ctx, std::vector<float>(T.fimg.begin(), T.fimg.end()),
                                               &kp.fast.imgf)) != SG_OK
-                               : (st = upload(ctx, T.fimg, &kp.fast.imgd)) != SG_OK)))) {
+                     : p.prec == SG_DF64 ? (st = upload(ctx, df_pairs(T.fimg), &kp.fast.imgx)) != SG_OK
+                                         : (st = upload(ctx, T.fimg, &kp.fast.imgd)) != SG_OK)))) {
         g_create_error = ctx->last_error;
         free_all(ctx);
         delete ctx;
@@ -257,8 +270,16 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
     }
     kp.err = const_cast<int *>(errp);
     ctx->has_device = true;
+    if (p.prec == SG_DF64 && !T.fast) {
+        st = fail(nullptr, SG_EUNSUPPORTED,
+                  "SG_DF64 needs the fast path (a potential with one- and two-mode monomials of a chain)");
+        free_all(ctx);
+        delete ctx;
+        return st;
+    }
     if (T.fast) {
         kp.fast.enabled = 1;
+        kp.fast.df = p.prec == SG_DF64;
         kp.fast.nb1 = T.nb1;
         kp.fast.nq1 = T.nq1;
         kp.fast.npairs = (int)T.pair_modes.size() / 2;
@@ -297,6 +318,7 @@ sg_status sg_create(int D, int L, const sg_basis *basis, const sg_grid *grids,
         ctx->allocations.push_back(vp);
         ctx->bytes_device += (int64_t)nvt * (ctx->fp32 ? 4 : 8);
         if (ctx->fp32) kp.fast.mtabf = static_cast<const float *>(vp);
+        else if (kp.fast.df) kp.fast.mtabx = static_cast<const float2 *>(vp);
         else kp.fast.mtabd = static_cast<const double *>(vp);
         e = launch_build_ranks(kp, static_cast<int *>(rp), 0);
         if (e == cudaSuccess) e = launch_build_mtab(kp, ctx->fp32, 0);

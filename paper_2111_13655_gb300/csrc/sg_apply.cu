@@ -407,17 +407,15 @@ __device__ __forceinline__ void stage_rows(const double *__restrict__ x, long lo
                                            T *__restrict__ xs, long long r0, long long rstep)
 {
     constexpr int U = 16 / (int)sizeof(T);
+    struct alignas(16) Unit { T v[U]; };
     const int w = xs_stride(nvec);
     for (long long r = r0; r < n; r += rstep) {
         T *row = xs + (size_t)r * stride;
         for (int v0 = 0; v0 < w; v0 += U) {
-            T t[U];
+            Unit t;
 #pragma unroll
-            for (int e = 0; e < U; e++) t[e] = v0 + e < nvec ? (T)x[(size_t)(v0 + e) * n + r] : T(0);
-            if constexpr (U == 4)
-                *reinterpret_cast<float4 *>(row + v0) = make_float4(t[0], t[1], t[2], t[3]);
-            else
-                *reinterpret_cast<double2 *>(row + v0) = make_double2(t[0], t[1]);
+            for (int e = 0; e < U; e++) t.v[e] = v0 + e < nvec ? (T)x[(size_t)(v0 + e) * n + r] : T(0);
+            *reinterpret_cast<Unit *>(row + v0) = t;
         }
     }
 }
@@ -604,6 +602,7 @@ cudaError_t launch_stage_x(const KParams &kp, bool fp32, const double *x, int nv
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((kp.n_cs + 255) / 256, 152 * 16));
     void *xs = const_cast<void *>(kp.xs);
     if (fp32) k_stage_x<float><<<blocks, 256, 0, stream>>>(x, kp.n_cs, nvec, stride, static_cast<float *>(xs));
+    else if (kp.fast.df) k_stage_x<df2><<<blocks, 256, 0, stream>>>(x, kp.n_cs, nvec, stride, static_cast<df2 *>(xs));
     else k_stage_x<double><<<blocks, 256, 0, stream>>>(x, kp.n_cs, nvec, stride, static_cast<double *>(xs));
     return cudaGetLastError();
 }
@@ -664,13 +663,15 @@ cudaError_t launch_maxabs_batch(const double *x, const long long *cs_prefix, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_batch(const KParams *kps, const long long *cs_prefix, int nprob, int64_t total_cs,
+cudaError_t launch_finalize_batch(const KParams *kps, const long long *cs_prefix, int nprob, int64_t max_ncs,
                                   const double *x, double *y, unsigned long long *acc, const long long *maxbits,
                                   int nvec, bool fp32, cudaStream_t stream)
 {
-    // blocks per problem: enough for the average problem, at least one
-    const size_t per = (size_t)nvec * (size_t)total_cs / (size_t)std::max(1, nprob);
-    const unsigned bx = (unsigned)std::max<size_t>(1, std::min<size_t>((per + 255) / 256, 64));
+    // blocks per problem: enough for the largest problem, within about 16 blocks per SM in all
+    // (at least 64 per problem)
+    const size_t per = (size_t)nvec * (size_t)max_ncs;
+    const size_t cap = std::max<size_t>(64, (152 * 16 + (size_t)nprob - 1) / (size_t)std::max(1, nprob));
+    const unsigned bx = (unsigned)std::max<size_t>(1, std::min<size_t>((per + 255) / 256, cap));
     k_finalize_batch<<<dim3(bx, (unsigned)nprob), 256, 0, stream>>>(kps, cs_prefix, x, y, acc, maxbits, nvec,
                                                                     fp32 ? 1 : 0);
     return cudaGetLastError();

@@ -155,6 +155,15 @@ cudaError_t launch_build_mtab(const KParams &kp, bool fp32, cudaStream_t stream)
     const unsigned nb = (unsigned)kp.n_terms;
     float *mf = const_cast<float *>(kp.fast.mtabf);
     double *md = const_cast<double *>(kp.fast.mtabd);
+    if (kp.fast.df) {
+        df2 *mx = reinterpret_cast<df2 *>(const_cast<float2 *>(kp.fast.mtabx));
+        switch (fast_inner_nb(kp.fast.nb1)) {
+            case 2: k_build_mtab<df2, 2><<<nb, kFT, smem, stream>>>(kp, mx); break;
+            case 3: k_build_mtab<df2, 3><<<nb, kFT, smem, stream>>>(kp, mx); break;
+            default: k_build_mtab<df2, 1><<<nb, kFT, smem, stream>>>(kp, mx); break;
+        }
+        return cudaGetLastError();
+    }
     // inner positions are level-1 modes of a uniform size nb1 (2 or 3); none otherwise
     switch (fast_inner_nb(kp.fast.nb1)) {
         case 2:
@@ -221,7 +230,7 @@ cudaError_t launch_build_ranks(const KParams &kp, int *ranks, cudaStream_t strea
 cudaError_t configure_fast_kernels(const KParams &kp, bool fp32)
 {
     FastLaunch a{nullptr, 0, nullptr, 0, true};
-    return fp32 ? fast_launch_f32(kp, a) : fast_launch_f64(kp, a);
+    return fp32 ? fast_launch_f32(kp, a) : kp.fast.df ? fast_launch_df(kp, a) : fast_launch_f64(kp, a);
 }
 
 cudaError_t launch_apply_fast(const KParams &kp, bool fp32, const double *x, int nvec,
@@ -229,7 +238,7 @@ cudaError_t launch_apply_fast(const KParams &kp, bool fp32, const double *x, int
 {
     if (kp.n_terms == 0) return cudaSuccess;
     FastLaunch a{x, nvec, maxbits, stream, false};
-    return fp32 ? fast_launch_f32(kp, a) : fast_launch_f64(kp, a);
+    return fp32 ? fast_launch_f32(kp, a) : kp.fast.df ? fast_launch_df(kp, a) : fast_launch_f64(kp, a);
 }
 
 }  // namespace sg

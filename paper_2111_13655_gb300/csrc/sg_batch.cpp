@@ -16,6 +16,13 @@
 #ifndef SG_BATCH_ORDER
 #define SG_BATCH_ORDER 0
 #endif
+// A fast-path problem with at least this many block-form terms fills the GPU
+// for several waves by itself: it runs as its own launches (parameters in the
+// kernel's parameter bank, as in sg_apply_H) inside the batch's sequence, and
+// only the smaller problems share the packed launches.
+#ifndef SG_BATCH_SOLO_TERMS
+#define SG_BATCH_SOLO_TERMS 16384
+#endif
 
 struct sg_batch {
     std::vector<sg_ctx *> ctxs;
@@ -32,6 +39,7 @@ struct sg_batch {
     };
     std::vector<Group> groups;
     std::vector<int> generic;          // problems outside the fast path: one launch each
+    std::vector<int> solo;             // large fast-path problems: their own launches
     std::vector<void *> allocations;
     std::vector<sg::KParams> h_kps;    // host copy of d_kps (the input-copy pointers change with the workspace)
     unsigned long long *acc = nullptr;
@@ -105,6 +113,7 @@ extern "C" sg_status sg_batch_create(sg_ctx *const *ctxs, int n, sg_batch **out)
     for (int j = 0; j < n; j++) {
         sg_ctx *c = ctxs[j];
         if (!c || !c->has_device) { delete b; return SG_EINVAL; }
+        if (c->kp.fast.df) { delete b; return SG_EUNSUPPORTED; }  // double-float contexts are applied one by one
         if (j > 0 && (c->device != b->device || c->fp32 != b->fp32)) { delete b; return SG_EINVAL; }
         b->device = c->device;
         b->fp32 = c->fp32;
@@ -131,8 +140,9 @@ extern "C" sg_status sg_batch_create(sg_ctx *const *ctxs, int n, sg_batch **out)
     std::map<int, std::vector<int>> by_variant;
     for (int j = 0; j < n; j++) {
         const sg::KParams &kp = ctxs[j]->kp;
-        if (kp.fast.enabled) by_variant[0].push_back(j);
-        else b->generic.push_back(j);
+        if (!kp.fast.enabled) b->generic.push_back(j);
+        else if (kp.fast.n_big >= SG_BATCH_SOLO_TERMS) b->solo.push_back(j);
+        else by_variant[0].push_back(j);
     }
     sg_status st;
     b->h_kps = kps;
@@ -191,8 +201,13 @@ extern "C" sg_status sg_batch_size(const sg_batch *b, int64_t *n_cs_total, int64
     if (n_cs_total) *n_cs_total = b->cs_prefix.back();
     if (n_terms_total) *n_terms_total = b->n_terms;
     if (launches_per_apply) {
-        int l = 2 + (SG_STAGE_X && !b->groups.empty());  // max|x|, finalisation, the input copies
+        // max|x|, finalisation, the input copies
+        int l = 2 + (SG_STAGE_X && (!b->groups.empty() || !b->solo.empty()));
         for (const auto &G : b->groups) l += (G.g.count[0] > 0) + (G.g.count[1] > 0);
+        for (int j : b->solo) {
+            const sg::KParams &kp = b->ctxs[j]->kp;
+            l += (kp.fast.n_big > 0) + (kp.n_terms > kp.fast.n_big);
+        }
         for (int j : b->generic) {
             const sg::KParams &kp = b->ctxs[j]->kp;
             l += kp.n_terms > 0;
@@ -236,7 +251,7 @@ extern "C" sg_status sg_apply_H_batch(sg_batch *b, const double *x, double *y, i
             (e = cudaMalloc(&b->maxbits, sizeof(long long) * (size_t)nprob * nvec)) != cudaSuccess)
             return bfail(b, SG_ENOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
 #if SG_STAGE_X
-        if (!b->groups.empty()) {
+        if (!b->groups.empty() || !b->solo.empty()) {
             // the fast-path problems gather from entry-major copies, problem j's rows from cs_prefix[j]
             const size_t rb = b->fp32 ? 4 : 8, stride = (size_t)sg::xs_stride(nvec);
             if ((e = cudaMalloc(&b->xs, (size_t)b->cs_prefix.back() * stride * rb)) != cudaSuccess)
@@ -295,6 +310,14 @@ sg_status enqueue_apply(sg_batch *b, const double *x, double *y, int nvec, cudaS
     if (b->xs && (e = sg::launch_stage_x_batch(b->fp32, x, b->d_cs_prefix, nprob, b->max_ncs, nvec, b->acc_nvec,
                                                b->xs, s)) != cudaSuccess)
         return bfail(b, SG_ECUDA, std::string("input copy launch: ") + cudaGetErrorString(e));
+    for (int j : b->solo) {
+        sg::KParams kp = b->h_kps[j];  // with the batch's input copy of problem j
+        const size_t off = (size_t)nvec * (size_t)b->cs_prefix[j];
+        kp.acc = b->acc + off * sg::acc_words(b->fp32);
+        if (!kp.xs || nvec > kp.xs_nvec) kp.xs = nullptr;
+        if ((e = sg::launch_apply_fast(kp, b->fp32, x + off, nvec, b->maxbits + (size_t)j * nvec, s)) != cudaSuccess)
+            return bfail(b, SG_ECUDA, std::string("term launch: ") + cudaGetErrorString(e));
+    }
     for (const auto &G : b->groups)
         if ((e = sg::launch_fast_batch(G.kp_any, b->fp32, G.g, x, b->acc, b->maxbits, b->d_cs_prefix, nvec, s)) !=
             cudaSuccess)
@@ -308,7 +331,7 @@ sg_status enqueue_apply(sg_batch *b, const double *x, double *y, int nvec, cudaS
             cudaSuccess)
             return bfail(b, SG_ECUDA, std::string("term launch: ") + cudaGetErrorString(e));
     }
-    if ((e = sg::launch_finalize_batch(b->d_kps, b->d_cs_prefix, nprob, b->cs_prefix.back(), x, y, b->acc,
+    if ((e = sg::launch_finalize_batch(b->d_kps, b->d_cs_prefix, nprob, b->max_ncs, x, y, b->acc,
                                        b->maxbits, nvec, b->fp32, s)) != cudaSuccess)
         return bfail(b, SG_ECUDA, std::string("finalise launch: ") + cudaGetErrorString(e));
     return SG_OK;

@@ -46,7 +46,7 @@
 
 namespace sg {
 
-// One problem per launch (sg_fast_f32.cu, sg_fast_f64.cu).
+// One problem per launch (sg_fast_f32.cu, sg_fast_f64.cu, sg_fast_df.cu).
 struct FastLaunch {
     const double *x;
     int nvec;
@@ -56,6 +56,7 @@ struct FastLaunch {
 };
 cudaError_t fast_launch_f32(const KParams &kp, const FastLaunch &a);
 cudaError_t fast_launch_f64(const KParams &kp, const FastLaunch &a);
+cudaError_t fast_launch_df(const KParams &kp, const FastLaunch &a);
 
 // Many problems of one precision per launch (sg_fast_batch_f32.cu,
 // sg_fast_batch_f64.cu).  [0]: block-form items, [1]: warp-form items.
@@ -115,6 +116,7 @@ __device__ __forceinline__ int fdiv(int x, int d, unsigned mag)
 
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ df2 fma_t(df2 a, df2 b, df2 c) { return df_fma(a, b, c); }
 
 // Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a multiple of 16)
 static __device__ __forceinline__ void l2_prefetch_bulk(const void *p, unsigned bytes)
@@ -146,6 +148,10 @@ template <> struct FTab<float> {
     static __device__ const float *mt(const KParams &P) { return P.fast.mtabf; }
     static __device__ const float *img(const KParams &P) { return P.fast.imgf; }
 };
+template <> struct FTab<df2> {
+    static __device__ const df2 *mt(const KParams &P) { return reinterpret_cast<const df2 *>(P.fast.mtabx); }
+    static __device__ const df2 *img(const KParams &P) { return reinterpret_cast<const df2 *>(P.fast.imgx); }
+};
 
 // W consecutive elements of T moved as one access (W * sizeof(T) <= 16 bytes)
 template <typename T, int W>
@@ -172,6 +178,20 @@ template <> struct Ldg<float, 4> {
     {
         const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
         return {{t.x, t.y, t.z, t.w}};
+    }
+};
+template <> struct Ldg<df2, 1> {
+    static __device__ __forceinline__ VecT<df2, 1> f(const df2 *p)
+    {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        return {{df2(t.x, t.y)}};
+    }
+};
+template <> struct Ldg<df2, 2> {
+    static __device__ __forceinline__ VecT<df2, 2> f(const df2 *p)
+    {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        return {{df2(t.x, t.y), df2(t.z, t.w)}};
     }
 };
 template <> struct Ldg<double, 1> {
@@ -476,7 +496,7 @@ __device__ __forceinline__ void gather_t(const FHdr &H, const void *__restrict__
         if constexpr (ST) {
             const T *xv = static_cast<const T *>(src) + v;
 #pragma unroll
-            for (int i = 0; i < NBI; i++) val[i] = __ldg(xv + (size_t)rp[i] * stride);
+            for (int i = 0; i < NBI; i++) val[i] = Ldg<T, 1>::f(xv + (size_t)rp[i] * stride).v[0];
         } else {
             const double *xv = static_cast<const double *>(src) + (size_t)v * stride;
 #pragma unroll
@@ -503,7 +523,7 @@ __device__ void gather_rt(const FHdr &H, const void *__restrict__ src, size_t st
         const int o = fdiv(w, vb, vmag), v = w - o * vb;
         for (int i = 0; i < NBI; i++) {
             const size_t r = (size_t)rk[(size_t)o * NBI + i];
-            X[(size_t)w * NBI + i] = ST ? __ldg(static_cast<const T *>(src) + r * stride + v)
+            X[(size_t)w * NBI + i] = ST ? Ldg<T, 1>::f(static_cast<const T *>(src) + r * stride + v).v[0]
                                         : (T)__ldg(static_cast<const double *>(src) + (size_t)v * stride + r);
         }
     }

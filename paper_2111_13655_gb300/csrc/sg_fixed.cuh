@@ -4,6 +4,7 @@
 // exact and associative, so the sum does not depend on the order of additions.
 #pragma once
 
+#include "sg_df.cuh"
 #include "sg_internal.h"
 
 namespace sg {
@@ -119,6 +120,21 @@ template <> struct Acc<double> {
         fx_add_real(a, r, coef, E, err);
     }
     static __device__ __forceinline__ void add(unsigned long long *a, double r, int coef, long long mb, int *err)
+    {
+        add_unit(a, r, coef, unit(mb), err);
+    }
+};
+// Double-float contributions: the FP64 accumulator format; the high and low
+// parts are added as two exact contributions (integer arithmetic only).
+template <> struct Acc<df2> {
+    static constexpr int words = kAccDigits;
+    static __device__ __forceinline__ int unit(long long mb) { return lsb_exponent(mb); }
+    static __device__ __forceinline__ void add_unit(unsigned long long *a, df2 r, int coef, int E, int *err)
+    {
+        fx_add_real(a, r.hi, coef, E, err);
+        fx_add_real(a, r.lo, coef, E, err);
+    }
+    static __device__ __forceinline__ void add(unsigned long long *a, df2 r, int coef, long long mb, int *err)
     {
         add_unit(a, r, coef, unit(mb), err);
     }

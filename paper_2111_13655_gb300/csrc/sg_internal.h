@@ -182,10 +182,16 @@ struct FastParams {
     const double *mtabd;       // FP64 contexts
     const float *mtabf;        // FP32 contexts
     const long long *mt_off;   // [n_terms + 1] starts, in elements (16-byte aligned; 0-size without a grid)
+    // double-float contexts (SG_DF64): contractions in pairs of FP32 numbers
+    // (hi, lo), FP64 accumulation; images and inner-block tables as (hi, lo)
+    int df;
+    const float2 *imgx;
+    const float2 *mtabx;
 };
 
-// Everything a kernel needs, passed by value.
-struct KParams {
+// Everything a kernel needs, passed by value (a multiple of 16 bytes, so
+// that a kernel can copy it in 16-byte units).
+struct alignas(16) KParams {
     int D, L, Dpad;
     int nmono, pmax, kw;
     int n_cs;
@@ -312,7 +318,7 @@ cudaError_t launch_finalize(const KParams &kp, bool fp32, const double *x, doubl
                             const long long *maxbits, cudaStream_t stream);
 cudaError_t launch_maxabs_batch(const double *x, const long long *cs_prefix, int nprob, int64_t max_ncs, int nvec,
                                 long long *maxbits, cudaStream_t stream);
-cudaError_t launch_finalize_batch(const KParams *kps, const long long *cs_prefix, int nprob, int64_t total_cs,
+cudaError_t launch_finalize_batch(const KParams *kps, const long long *cs_prefix, int nprob, int64_t max_ncs,
                                   const double *x, double *y, unsigned long long *acc, const long long *maxbits,
                                   int nvec, bool fp32, cudaStream_t stream);
 // Propagation server (sg_server_api.cpp, sg_server.cu): device state of one

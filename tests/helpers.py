@@ -23,12 +23,23 @@ error is the largest: the element-wise measure is looser than the norm-wise
 one.  Measured on GB300 (mixed vs the oracle): element-wise 1.1e-8 (D=2 L=6),
 2.0e-7 (D=6 L=8), 3.0e-7 (D=12 L=5), 1.4e-7 (general polynomial); norm-wise
 at most 1.2e-7.  MIXED_ELEM_TOL = 5e-6 keeps a margin above 15 over them.
+Double-float mode (SG_DF64: each contraction value a pair of FP32 numbers,
+about 48 significant bits, exact fixed-point sum): every term's result
+carries a relative rounding of a few u_df = 2^-48 per operation (against
+2^-53 in FP64; tests/test_df_arith.py pins the operations' bounds), 32 times
+FP64's, and the compact functions shared by many terms collect it with the
+weights |D_l| as in mixed mode.  Norm-wise the FP64 bound 1e-12 holds (measured
+on GB300: 9.7e-16 at D=12 L=5, 3.7e-14 at D=12 L=10 against the FP64 path);
+element-wise the measure reaches 1.0e-14 at D=12 L=5 and 1.6e-12 at D=12
+L=10, so DF64_ELEM_TOL = 1e-11 (a margin of six over the largest).
 """
 import numpy as np
 
 FP64_TOL = 1e-12
 MIXED_TOL = 5e-6
 MIXED_ELEM_TOL = 5e-6
+DF64_TOL = 1e-12
+DF64_ELEM_TOL = 1e-11
 
 
 def literal_elem_tol(p):
@@ -50,10 +61,12 @@ def elem_rel(y, r):
 
 
 def assert_parity(y, r, precision, what=""):
-    """Both measures within the tolerances of `precision` ("fp64" or "mixed")."""
+    """Both measures within the tolerances of `precision` ("fp64", "df64" or "mixed")."""
     n, e = norm_rel(y, r), elem_rel(y, r)
     if precision == "fp64":
         assert n <= FP64_TOL and e <= FP64_TOL, f"{what}: norm-wise {n:.3e}, element-wise {e:.3e}"
+    elif precision == "df64":
+        assert n <= DF64_TOL and e <= DF64_ELEM_TOL, f"{what}: norm-wise {n:.3e}, element-wise {e:.3e}"
     else:
         assert n <= MIXED_TOL and e <= MIXED_ELEM_TOL, f"{what}: norm-wise {n:.3e}, element-wise {e:.3e}"
     return n, e
