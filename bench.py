@@ -43,9 +43,9 @@ WORKLOAD = "chained Henon-Heiles D=12 L=10 nb=l+1 nq=l+2 (N_cs=646646, 646646 te
 # workload summarised in profiles/; None when the kernel has changed since.
 TRAFFIC_BYTES = {"mixed": 9_009_755_648, "fp64": 23_425_165_568, "df64": None}
 # FP32 instructions of one double-float multiply-add (csrc/sg_df.cuh df_fma:
-# one multiply, three FMAs, two_sum 6, two additions, fast_two_sum 3): the
-# double-float arm's roofline counts these against the FP32 issue rate
-DF_INSTR_PER_FMA = 15
+# one multiply, three FMAs, two_sum 6, two additions): the double-float arm's
+# roofline counts these against the FP32 issue rate
+DF_INSTR_PER_FMA = 12
 # FP32 lanes per SM (the unit count of the derived FP32 peak)
 FP32_LANES_PER_SM = 128
 # kernels of one sg_apply_H at this workload: k_maxabs, k_stage_x (entry-major

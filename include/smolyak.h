@@ -254,7 +254,8 @@ void sg_batch_destroy(sg_batch *b);
  *   - the block/warp split (1, 2, 4): terms that fit a quarter of a block's
  *     shared memory with that many vectors per chunk run one per warp;
  *   - the shared-memory budget of a block, in KB (52, 70, 104 for SG_MIXED;
- *     70, 104 for SG_FP64): more vectors per chunk, fewer resident blocks.
+ *     70, 104 for SG_FP64 and SG_DF64): more vectors per chunk, fewer
+ *     resident blocks.
  * Only the term records, the split and the work-area capacities change;
  * results change by rounding only.  Synchronous; allocates and frees
  * 2 * nvec * N_cs doubles of scratch.  No other work may use the context
@@ -293,7 +294,8 @@ sg_status sg_tune_plan(const sg_ctx *ctx, int *slice_vt, int *warp_vt, int *smem
  * A request's results are bitwise the same alone and in any mix (its applies,
  * updates and logged sums do not depend on the other requests).
  *
- * sg_server_create -- precision of every request's contexts; hbm_budget_bytes:
+ * sg_server_create -- precision of every request's contexts (SG_FP64 or
+ *   SG_MIXED; else SG_EINVAL); hbm_budget_bytes:
  *   the planned device memory of the active requests never exceeds it
  *   (context tables, M^B, batch items, four state vectors, batch and context
  *   workspaces, logs).  Transient set-up buffers of an admission (the

@@ -17,11 +17,10 @@
 //   df_fma(x, y, c)     c + x * y as one step of a compensated dot product:
 //                       the product as in df_mul, its high part added to c's
 //                       high part by two_sum, the two low parts and the
-//                       rounding error summed in FP32, renormalised.  The
-//                       error is about u^2 (|x y| + |c|) plus u |x y + c|
-//                       times the FP32 rounding of the low-part sum, i.e. the
-//                       sum is as accurate as if computed with 2^-48 and
-//                       rounded to a double-float.
+//                       rounding error summed in FP32 (12 FP32 instructions;
+//                       not renormalised unless SG_DF_RENORM).  The error is
+//                       within a few u^2 (|x y| + |c|): the sum is as
+//                       accurate as if computed with 2^-48 and rounded.
 // From double: hi = fl32(d), lo = fl32(d - hi); hi + lo equals d to 2^-48
 // relative (d - hi is exact in FP64).
 #pragma once
@@ -42,6 +41,11 @@
 #endif
 #ifndef __align__
 #define __align__(n) alignas(n)
+#endif
+
+// 1: renormalise after every multiply-add (three more FP32 instructions)
+#ifndef SG_DF_RENORM
+#define SG_DF_RENORM 0
 #endif
 
 namespace sg {
@@ -131,9 +135,17 @@ __host__ __device__ inline df2 df_fma(df2 x, df2 y, df2 c)
     float s, t;
     dfops::two_sum(c.hi, p, s, t);  // s + t = c.hi + p exactly
     t = dfops::add(t, dfops::add(e, c.lo));
+#if SG_DF_RENORM
     df2 r;
     dfops::fast_two_sum(s, t, r.hi, r.lo);
     return r;
+#else
+    // not renormalised: (s, t) holds the same value, with t above ulp(s) / 2
+    // by at most a few FP32 roundings; every consumer (the next multiply-add,
+    // a product, the exact fixed-point conversion of hi and lo) takes it as
+    // the sum hi + lo
+    return df2(s, t);
+#endif
 }
 
 __host__ __device__ inline df2 operator*(df2 x, df2 y) { return df_mul(x, y); }

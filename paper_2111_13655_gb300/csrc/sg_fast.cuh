@@ -138,17 +138,7 @@ static __device__ __forceinline__ void l2_prefetch_span(const void *base, size_t
 #ifndef SG_LOOKAHEAD
 #define SG_LOOKAHEAD 1
 #endif
-// work items of the transfer and inner-block loops unrolled per thread (0: the compiler's choice)
-#ifndef SG_PASS_UNROLL
-#define SG_PASS_UNROLL 0
-#endif
-#if SG_PASS_UNROLL > 0
-#define SG_PRAGMA_(x) _Pragma(#x)
-#define SG_PRAGMA(x) SG_PRAGMA_(x)
-#define SG_PASS_UNROLL_PRAGMA SG_PRAGMA(unroll SG_PASS_UNROLL)
-#else
-#define SG_PASS_UNROLL_PRAGMA
-#endif
+
 
 template <typename T> struct FTab;
 template <> struct FTab<double> {
@@ -309,7 +299,6 @@ __device__ __forceinline__ void fwd_pass_t(const T *__restrict__ in, T *__restri
 #pragma unroll
     for (int i = 0; i < NO * NI; i++) mr[i] = M[i];
     const int total = C * PW, cpw = C * PW;
-    SG_PASS_UNROLL_PRAGMA
     for (int w = tid; w < total; w += GS) {
         const int c = fdiv(w, PW, pwmag), pw = w - c * PW;
         VecT<T, W> xv[NI];
@@ -339,7 +328,6 @@ __device__ __forceinline__ void bwd_pass_t(const T *__restrict__ in, T *__restri
 #pragma unroll
     for (int i = 0; i < NO * NI; i++) mr[i] = M[i];
     const int total = C * PW, cpw = C * PW;
-    SG_PASS_UNROLL_PRAGMA
     for (int w = tid; w < total; w += GS) {
         const int c = fdiv(w, PW, pwmag), pw = w - c * PW;
         const T *ip = in + (size_t)((c * NI) * PW + pw) * W;
@@ -429,7 +417,6 @@ __device__ void reg_phase(const T *__restrict__ tab, T *Z, int NGs, int vb, int 
     constexpr int ZW = (NBI * (int)sizeof(T)) % 16 == 0 ? U : NBI == 2 && sizeof(T) == 4 ? 2 : 1;
     const int total = NGs * vb;
     const unsigned vmag = rmag((unsigned)vb);
-    SG_PASS_UNROLL_PRAGMA
     for (int w = tid; w < total; w += GS) {
         const int g = fdiv(w, vb, vmag);
         T mm[NEU * UE];

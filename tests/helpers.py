@@ -29,9 +29,9 @@ carries a relative rounding of a few u_df = 2^-48 per operation (against
 2^-53 in FP64; tests/test_df_arith.py pins the operations' bounds), 32 times
 FP64's, and the compact functions shared by many terms collect it with the
 weights |D_l| as in mixed mode.  Norm-wise the FP64 bound 1e-12 holds (measured
-on GB300: 9.7e-16 at D=12 L=5, 3.7e-14 at D=12 L=10 against the FP64 path);
-element-wise the measure reaches 1.0e-14 at D=12 L=5 and 1.6e-12 at D=12
-L=10, so DF64_ELEM_TOL = 1e-11 (a margin of six over the largest).
+on GB300 against the exact closed form: 1.3e-15 at D=12 L=5, 8.7e-14 at
+D=12 L=10); element-wise the measure reaches 1.7e-14 at D=12 L=5 and 3.6e-12
+at D=12 L=10, so DF64_ELEM_TOL = 1e-11 (a margin near three over the largest).
 """
 import numpy as np
 
