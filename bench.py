@@ -41,7 +41,7 @@ WORKLOAD = "chained Henon-Heiles D=12 L=10 nb=l+1 nq=l+2 (N_cs=646646, 646646 te
 # k_apply_fast per apply (its block-form and warp-form launches) at the
 # benchmark workload, per precision, from the one-pass ncu capture of the full
 # workload summarised in profiles/; None when the kernel has changed since.
-TRAFFIC_BYTES = {"mixed": 9_009_755_648, "fp64": 23_425_165_568, "df64": None}
+TRAFFIC_BYTES = {"mixed": 9_009_755_648, "fp64": 23_425_165_568, "df64": 23_315_786_496}
 # FP32 instructions of one double-float multiply-add (csrc/sg_df.cuh df_fma:
 # one multiply, three FMAs, two_sum 6, two additions): the double-float arm's
 # roofline counts these against the FP32 issue rate

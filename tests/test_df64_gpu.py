@@ -99,9 +99,22 @@ def test_df64_eigenvalues_match_the_oracle_spectrum():
     assert np.max(np.abs(ev - ref)) <= 1e-10
 
 
+def test_df64_tuned_plan_keeps_parity():
+    """sg_tune re-plans a double-float context (slicing, split, budget); the
+    tuned applies stay within the tolerances and repeat bitwise."""
+    p = synth.workload_C3(L=6)
+    x = synth.random_vectors(orc.n_compact(p), 4, 31)
+    y_ref = galerkin.apply_H(p, x)
+    with sg.sg_create(p, "df64") as ctx:
+        sg.sg_tune(ctx, 4)
+        y = apply(ctx, x)
+        assert np.array_equal(apply(ctx, x), y)
+    assert_parity(y, y_ref, "df64", "D=12 L=6 tuned")
+
+
 def test_df64_refusals():
     """Problems off the fast path (a monomial of three modes) and batches are
-    refused with SG_EUNSUPPORTED."""
+    refused with SG_EUNSUPPORTED, a double-float server with SG_EINVAL."""
     p3 = synth.polynomial_problem(3, 3, [1.0, 1.0, 1.0], [(0.1, [(0, 1), (1, 1), (2, 1)])])
     with pytest.raises(sg.SgError) as ei:
         sg.sg_create(p3, "df64")
@@ -110,3 +123,6 @@ def test_df64_refusals():
         with pytest.raises(sg.SgError) as ei:
             sg.sg_batch_create([ctx])
         assert ei.value.status == sg.SG_EUNSUPPORTED
+    with pytest.raises(sg.SgError) as ei:
+        sg.Server("df64")
+    assert ei.value.status == sg.SG_EINVAL
