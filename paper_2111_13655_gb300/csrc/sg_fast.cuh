@@ -545,8 +545,8 @@ __device__ void gather_s(const FHdr &H, const void *src, size_t stride, const in
 // The chunk's vectors v0 .. v0 + vb - 1: from the problem's entry-major copy
 // when it has one, else from x.
 template <typename T, int GS>
-__device__ void gather(const FHdr &H, const KParams &P, const double *x, int nvec, int v0, const int *rk, T *X,
-                       int vb, int tid)
+__device__ void gather(const FHdr &H, const KParams &P, const double *x, int v0, const int *rk, T *X, int vb,
+                       int tid)
 {
     if (P.xs)
         gather_s<T, GS, true>(H, static_cast<const T *>(P.xs) + v0, (size_t)xs_stride(P.xs_nvec), rk, X, vb, tid);
@@ -725,7 +725,7 @@ __device__ __forceinline__ void fast_term(const KParams &P, const double *__rest
         T *Y = X + pad_elems((int64_t)NB * vb, U);
         T *A = sliced ? Y + pad_elems((int64_t)NB * vb, U) : Y;
         T *Bf = A + pad_elems((int64_t)NBI * H.NGs * vb, U);
-        gather<T, GS>(H, P, x, nvec, v0, rk, X, vb, tid);
+        gather<T, GS>(H, P, x, v0, rk, X, vb, tid);
         gsync<GS>();
         const T *F = nullptr;
         if (H.grid) {
