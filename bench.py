@@ -524,6 +524,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--L", type=int, default=10, help="Smolyak level of the D=12 workload (10: the benchmark)")
     ap.add_argument("--precisions", default="mixed,fp64,df64")
+    ap.add_argument("--tune", action=argparse.BooleanOptionalAction, default=True,
+                    help="run sg_tune on each arm's context before timing (--no-tune: the default plan)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--peak-seconds", type=float, default=1.0, help="0: skip the peak measurement")
     ap.add_argument("--sharding", default="replicas", choices=["replicas", "terms"],
@@ -570,6 +572,12 @@ def main():
     results = {}
     for prec in args.precisions.split(","):
         ctx = sg.sg_create(p, prec)
+        tuned = args.tune and not (args.sharding == "terms" and world > 1)
+        if tuned:
+            # the library's own autotuner picks the schedule for these applies
+            # (slicing target, block/warp split, shared-memory budget) by timing
+            sg.sg_tune(ctx, nvec)
+        plan = dict(sg.sg_tune_plan(ctx), tuned=bool(tuned))
         n = ctx.n_cs
         # replicas: independent inputs per rank; term sharding: one problem, the same x everywhere
         x = synth.random_vectors(n, nvec, 11 + (0 if args.sharding == "terms" else rank))
@@ -621,6 +629,7 @@ def main():
             "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
             "roofline": roof,
             "clocks": clk.summary(),
+            "plan": plan,
         }
         if prec == "mixed" and not args.no_e2e:
             # end to end through the host-buffer entry point: H2D + apply + D2H per step
@@ -657,13 +666,15 @@ def main():
                 "dtype": "f32" if "mixed" in results else "f64",
                 "data": "synthetic", "config": bench_config(args, world),
                 "latency_ms": m["latency_ms"], "roofline": m["roofline"], "clocks": m["clocks"],
-                "e2e": m.get("e2e"), "gpu_launches": LAUNCHES_PER_APPLY * m["steps"],
+                "e2e": m.get("e2e"), "gpu_launches": LAUNCHES_PER_APPLY * m["steps"], "plan": m.get("plan"),
                 "fp64": ({"value": f["value"], "unit": UNIT, "ms_per_step": f["ms_per_step"], "steps": f["steps"],
-                          "latency_ms": f["latency_ms"], "roofline": f["roofline"], "clocks": f["clocks"]}
+                          "latency_ms": f["latency_ms"], "roofline": f["roofline"], "clocks": f["clocks"],
+                          "plan": f.get("plan")}
                          if f else None),
                 "df64": ({"value": d["value"], "unit": UNIT, "ms_per_step": d["ms_per_step"], "steps": d["steps"],
                           "precision": "double-float contractions (pairs of FP32, ~48 bits), FP64 accumulation",
-                          "latency_ms": d["latency_ms"], "roofline": d["roofline"], "clocks": d["clocks"]}
+                          "latency_ms": d["latency_ms"], "roofline": d["roofline"], "clocks": d["clocks"],
+                          "plan": d.get("plan")}
                          if d else None),
                 "peaks": {k: v for k, v in peaks.items() if k != "clocks"} if peaks else None,
                 "cpu_baseline": cpu, "batched": batched, "serving": serving}
