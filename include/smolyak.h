@@ -141,6 +141,13 @@ sg_status sg_size(const sg_ctx *ctx, int64_t *n_cs, int64_t *n_terms, int64_t *n
  *          y is overwritten; x and y must not overlap.
  *   nvec   >= 1.  A complex vector is passed as two real vectors.
  * Enqueued on `stream`; the result is ready when the stream reaches it.
+ * The first call with a larger nvec than before synchronises `stream` and
+ * allocates the context's workspace for that many vectors: the fixed-point
+ * accumulators (1 word per element for SG_MIXED, 4 otherwise) and, on the
+ * fast path, an entry-major copy of x in the contraction type (rows of nvec
+ * rounded up to 4 values), which every apply rewrites before its terms
+ * gather from it.  Calls on one context must be ordered (one stream, or
+ * synchronised streams): they share that workspace.
  */
 sg_status sg_apply_H(sg_ctx *ctx, const double *x, double *y, int nvec, void *stream);
 
