@@ -141,3 +141,7 @@ def test_plan_reports_the_device_bytes_of_sg_create():
         assert lower <= b <= lower + 3 * 10 ** 9, (prec, b, lower)
         sizes[prec] = b
     assert sizes["fp64"] > sizes["mixed"]
+    # the double-float mode holds its tables as (hi, lo) FP32 pairs: the FP64 sizes
+    ctx = sg.sg_plan(p, "df64")
+    assert sg.sg_size(ctx)["bytes_device"] == sizes["fp64"]
+    sg.sg_destroy(ctx)
