@@ -1,9 +1,10 @@
 // Device code of the fast path of the Smolyak operator action (sm_103a):
 // potentials whose monomials touch at most two modes (the Henon-Heiles family
 // of Sec. 4, Eq. (18)).  Included by the units that instantiate it:
-// sg_fast_f32.cu / sg_fast_f64.cu (one problem per launch),
-// sg_fast_batch_f32.cu / sg_fast_batch_f64.cu (many problems per launch) and
-// sg_apply_fast.cu (the per-context set-up kernels).
+// sg_fast_f32.cu / sg_fast_f64.cu / sg_fast_df.cu (one problem per launch;
+// T = float, double or the double-float pair df2), sg_fast_batch_f32.cu /
+// sg_fast_batch_f64.cu (many problems per launch) and sg_apply_fast.cu (the
+// per-context set-up kernels).
 //
 // One thread block (or, for small terms, one warp) per Smolyak term, terms
 // ordered most-expensive first.  With the grid operator split as described in
@@ -35,6 +36,13 @@
 //     reverse order, ending on the canonical basis order.
 // The basis part of the outer positions is fused with the exact fixed-point
 // compress-add of D_l * y_l (sg_fixed.cuh).
+//
+// Per term, before the first chunk: the term's image (its 1D matrices and
+// pair tables) and its slice of M^B are copied into shared memory while one
+// warp decodes the record; one thread issues L2 prefetches of the data of the
+// term one residency ahead.  Each chunk gathers its vectors from the
+// entry-major copy of x made at the start of the apply (k_stage_x), where the
+// vectors of one compact entry are adjacent.
 #pragma once
 
 #include <algorithm>
