@@ -39,9 +39,10 @@ UNIT = "applications/s"
 WORKLOAD = "chained Henon-Heiles D=12 L=10 nb=l+1 nq=l+2 (N_cs=646646, 646646 terms)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the term kernel
 # k_apply_fast per apply (its block-form and warp-form launches) at the
-# benchmark workload, per precision, from the one-pass ncu capture of the full
-# workload summarised in profiles/; None when the kernel has changed since.
-TRAFFIC_BYTES = {"mixed": 9_009_755_648, "fp64": 23_425_165_568, "df64": 23_315_786_496}
+# benchmark workload with the plan sg_tune keeps, per precision, from the
+# one-pass ncu capture of the full workload summarised in profiles/; None when
+# the kernel has changed since.
+TRAFFIC_BYTES = {"mixed": 8_849_153_280, "fp64": 23_382_741_248, "df64": 23_298_306_560}
 # FP32 instructions of one double-float multiply-add (csrc/sg_df.cuh df_fma:
 # one multiply, three FMAs, two_sum 6, two additions): the double-float arm's
 # roofline counts these against the FP32 issue rate
