@@ -140,10 +140,12 @@ __host__ __device__ inline df2 df_fma(df2 x, df2 y, df2 c)
     dfops::fast_two_sum(s, t, r.hi, r.lo);
     return r;
 #else
-    // not renormalised: (s, t) holds the same value, with t above ulp(s) / 2
-    // by at most a few FP32 roundings; every consumer (the next multiply-add,
-    // a product, the exact fixed-point conversion of hi and lo) takes it as
-    // the sum hi + lo
+    // not renormalised: (s, t) holds the same value, t possibly above
+    // ulp(s) / 2; every consumer takes it as the sum hi + lo (the next
+    // multiply-add exactly so, the exact fixed-point conversion of hi and lo
+    // too, and a product with an extra error of u |x| |t|: a few u^2 |x s|
+    // unless s came from a cancellation, where it is u^2 of the cancelled
+    // terms as in a compensated dot product)
     return df2(s, t);
 #endif
 }

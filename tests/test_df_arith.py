@@ -8,6 +8,8 @@ and every result is compared with the exact rational value:
   * the split of a double into hi + lo is within 2^-48 of it;
   * df_mul: within 8u^2 of the exact product of the two double-floats
     (u = 2^-24);
+  * df_mul with a second factor left unrenormalised by df_fma: the same
+    plus u |x| |y_lo|;
   * df_fma: within 8u^2 (|x y| + |c|) of c + x y, cancellation included;
   * a dot product of six terms by df_fma: within 6 * 8u^2 sum |x_k y_k|.
 """
@@ -125,6 +127,24 @@ def test_product(run):
     for (x, y), (hi, lo) in zip(xs, res):
         exact = F(*x) * F(*y)
         assert abs(F(hi, lo) - exact) <= 8 * U * U * abs(exact)
+
+
+def test_product_of_an_unrenormalised_accumulator(run):
+    """df_fma leaves its result unrenormalised (lo can exceed ulp(hi)/2; here
+    |lo| <= 2^-20 |hi|).  A product taking it rounds the cross term x_hi y_lo
+    to FP32: its error gains u |x| |y_lo| over the normalised bound (which is
+    about u^2 |x y| again when lo is a few roundings of hi)."""
+    rng = np.random.default_rng(6)
+    xs = []
+    for _ in range(400):
+        x = df_of(rng)
+        hi = f32(float(rng.standard_normal()))
+        lo = f32(hi * float(rng.uniform(-1, 1)) * 2.0 ** -20)
+        xs.append((x, (hi, lo)))
+    res = run([f"m {x[0].hex()} {x[1].hex()} {y[0].hex()} {y[1].hex()}" for x, y in xs])
+    for (x, y), (hi, lo) in zip(xs, res):
+        exact = F(*x) * F(*y)
+        assert abs(F(hi, lo) - exact) <= 8 * U * U * abs(exact) + 2 * U * abs(F(*x)) * abs(Fraction(y[1]))
 
 
 def test_fused_multiply_add_with_cancellation(run):
